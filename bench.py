@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the step-truncation RK4 TT solver (Burgers-Hopf, GB300).
+
+One step = one full RK4 step of the hot path: 4 operator applies, 8 TT
+roundings (right-to-left Householder orthogonalisation + left-to-right
+truncated SVD) and 4 TT sums, on the d=32, n=128, rank<=64 workload, in the
+"saturated" state (every interior rank at the cap 64: a seeded TT with random
+orthonormal cores), complex float64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas (one per
+GPU, launched by torchrun); value = steps of all ranks / max time over ranks.
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TT RK4 steps/s (d=32,n=128,r≤64) mixed vs FP64 @≤1e-6 err; roofline %"
+FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12  # 152 SMs x 2 DFMA/clk x 2.07 GHz
+# relative cost of one RK4 step in units of one rounding at rank 6r:
+# 4 roundings at 6r, 3 at 2r, 1 at 5r (cost ~ K^3 per core)
+STEP_PER_KROUND = (4 * 216 + 3 * 8 + 125) / 216.0
+
+
+def workload():
+    import synthetic
+    w = synthetic.C3
+    return w
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# --------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                smax.append(float(s[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, s[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle arm ----
+def oracle_sample_seconds(d_sample: int = 8):
+    """One operator apply + rounding at rank 6r (the first RK4 stage) by the
+    CPU oracle on a d_sample-core slice of the saturated workload.  Returns
+    (seconds, extrapolated seconds per full RK4 step at d=32)."""
+    from oracle import model, tt
+    import synthetic
+    w = workload()
+    cores, _ = synthetic.saturated_tt_cores(d_sample, w.n, w.cap, seed=0)
+    m0, C0 = model.cell_moments(w.d, w.alpha, w.beta, w.sigma, w.ell)
+    L = model.default_L(C0)
+    W = model.mpo_blocks(d_sample, w.n, L, w.nu)
+    bond = model.mpo_bond_dims(d_sample)
+    t0 = time.perf_counter()
+    y = tt.apply_mpo(cores, W, bond)
+    tt.round_tt(y, w.tol, w.cap)
+    sec = time.perf_counter() - t0
+    per_step = sec * (w.d - 1) / (d_sample - 1) * STEP_PER_KROUND
+    return sec, per_step
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    w = workload()
+    for _ in range(args.warmup):
+        oracle_sample_seconds()
+    per = []
+    for _ in range(args.steps):
+        per.append(oracle_sample_seconds()[1])
+    step_s = sum(per) / len(per)
+    value = 1.0 / step_s
+    sample = ("one operator apply + rank-6r rounding (first RK4 stage) on an 8-core slice "
+              "(d=8, n=128, r=64) of the saturated state; step time extrapolated by "
+              f"(d-1)/7 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")
+    return {"metric": METRIC, "value": value, "unit": "steps/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w),
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def config_dict(w):
+    return {"workload": f"saturated TT, d={w.d}, n={w.n}, rank cap {w.cap} (all interior ranks at the cap), "
+                        f"tol {w.tol:g}, dt {w.dt:g}, nu {w.nu}, FP64 complex",
+            "d": w.d, "n": w.n, "rank_cap": w.cap, "tol": w.tol, "dt": w.dt, "precision": "fp64",
+            "state": "seeded random orthonormal cores (seed 0)",
+            "l2": "working set (~20 GB) larger than L2; no flush needed",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- our arm ----
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2403_04946_gb300 import binding
+    from oracle import model  # noqa: F401  (used only for the CPU baseline leg)
+    import synthetic
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    w = workload()
+    ctx0 = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=1.0,
+                           stream=stream.cuda_stream)
+    m0, C0 = ctx0.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
+    ctx0.close()
+    L = float(np.sqrt(36.8 / np.min(np.diag(C0))))
+    ctx = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L,
+                          stream=stream.cuda_stream)
+    cores, ranks = synthetic.saturated_tt_cores(w.d, w.n, w.cap, seed=0)
+    t = ctx.tt_from_host(cores, max_rank=w.cap)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.hopf_step(t, w.dt, 1)
+    ctx.hopf_profile_read(reset=True)
+    ctx.hopf_profile_enable(True)
+
+    gpu_id = "0"
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.hopf_step(t, w.dt, 1)
+    e1.record(stream)
+    barrier()
+    clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    prof = ctx.hopf_profile_read(reset=True)
+    ctx.hopf_profile_enable(False)
+    tmax = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    elapsed = float(tmax.item())
+
+    # end to end through the C ABI: pinned host state in, step, state out
+    ranks_np = np.asarray(ranks, dtype=np.int32)
+    _, flat = binding.cores_to_flat(cores)
+    host_in = torch.from_numpy(flat.copy()).pin_memory()
+    nd = flat.size
+    host_out = torch.empty(nd, dtype=torch.float64).pin_memory()
+    import ctypes
+    pin_in = ctypes.cast(host_in.data_ptr(), ctypes.POINTER(ctypes.c_double))
+    pin_out = ctypes.cast(host_out.data_ptr(), ctypes.POINTER(ctypes.c_double))
+    k_e2e = max(1, args.steps)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ctx.tt_set_from_host(t, ranks=ranks_np, flat=pin_in)
+        ctx.hopf_step(t, w.dt, 1)
+        ctx.tt_to_host_into(t, pin_out, ctx.tt_size(t))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    out_bytes = ctx.tt_size(t) * 8
+
+    result = None
+    if rank == 0:
+        value = world * args.steps / elapsed
+        # roofline of the dominant kernel class
+        dom = max(prof, key=lambda k: prof[k]["ms"])
+        pd = prof[dom]
+        launch_s = pd["ms"] / 1e3 / max(pd["timed_launches"], 1)
+        peaks = read_peaks()
+        if pd["flops"] > 0:
+            achieved = pd["flops"] / max(pd["timed_launches"], 1) / launch_s / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "FP64 FMA: 152 SMs x 4 FLOP/clk x 2.07 GHz (derived, no measured FP64 peak)",
+                    "traffic": None}
+        else:
+            achieved = pd["bytes"] / max(pd["timed_launches"], 1) / launch_s / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                    "traffic": None}
+        total_ms = sum(v["ms"] for v in prof.values())
+        shares = {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if v["ms"] > 0}
+        apply_gbs = (prof["apply"]["bytes"] / (prof["apply"]["ms"] / 1e3) / 1e9) if prof["apply"]["ms"] > 0 else None
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            sec, per_step = oracle_sample_seconds()
+            cpu = {"value": 1.0 / per_step, "unit": "steps/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": ("one operator apply + rank-6r rounding (first RK4 stage) on an 8-core slice "
+                              f"(d=8, n=128, r=64) of the saturated state, {sec:.1f} s; step time extrapolated by "
+                              f"(d-1)/7 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")}
+        result = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w),
+            "roofline": roof,
+            "kernel_shares": shares,
+            "apply_gbs": apply_gbs,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s",
+                    "h2d_bytes_per_step": int(nd * 8), "d2h_bytes_per_step": int(out_bytes)},
+            "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "clocks": clocks.summary(),
+        }
+    ctx.tt_free(t)
+    ctx.close()
+    return result
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

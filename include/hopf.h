@@ -1,0 +1,226 @@
+/*
+ * hopf.h -- C ABI of the GB300 (sm_103a) tensor-train solver for the
+ * Burgers-Hopf characteristic-function PDE of Rodgers & Venturi, "Tensor
+ * approximation of functional differential equations" (arXiv 2403.04946).
+ *
+ * What is solved.  Phi(a,t) = E[exp(i a . u(t))] for the d cell averages u of
+ * the periodic Burgers solution (Sec. 5, Eq. burgers-rxn with alpha = 0 and
+ * Eq. BHfde), projected on d cell-indicator functions (Eq. sense) so that it
+ * obeys a linear PDE of the form of Eq. (hyper1):
+ *     dPhi/dt = sum_k a_k sum_j [ (i/2) D1[k,j] d^2Phi/da_j^2
+ *                                 + nu D2[k,j] dPhi/da_j ],
+ * D1, D2 the periodic second-order difference matrices in x (text under
+ * Eq. pdf-burgers).  Each a_j lives on a_i = (i - n/2) da, da = 2L/n,
+ * i = 0..n-1; slot 0 (a = -L) is held at zero and a = +L is a zero ghost.
+ * Phi is held in tensor-train format (App. A, "Tensor train decomposition")
+ * and advanced by step-truncation RK4 (Eq. discrete-flow-trunc-intro).
+ *
+ * Conventions shared by every call.
+ *  - Complex numbers are pairs of doubles (re, im), interleaved.
+ *  - A TT core C_k has shape r_{k-1} x n x r_k with r_0 = r_d = 1 and is
+ *    stored column-major, C[i,j,k] = v[i + a j + a b k] (App. A, the
+ *    vectorisation under the flattening maps H and V).  Host arrays hold the
+ *    d cores back to back in that layout.
+ *  - All device work is ordered on the stream given to hopf_create (a
+ *    cudaStream_t, e.g. PyTorch's current stream; NULL = legacy default
+ *    stream).  Calls that return host data synchronise that stream.
+ *  - The library allocates and owns all device memory it uses (contexts,
+ *    tensors, workspaces) and frees it in hopf_destroy / tt_free.  Host
+ *    arrays passed in are read during the call only; host output arrays
+ *    are caller-owned and written before the call returns.
+ *  - Every call returns a hopf_status; nothing aborts.  On an error the
+ *    context keeps a message (hopf_last_error) and tensors passed in are
+ *    left in a valid state (their contents are unspecified after a failed
+ *    device step).  A context must not be used from two threads at once.
+ *  - Device waits inside the library's cooperative kernels are bounded (a
+ *    few seconds of wall time); expiry returns HOPF_ETIMEOUT.
+ */
+#ifndef HOPF_H
+#define HOPF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hopf_ctx hopf_ctx; /* stream, model parameters, workspaces */
+typedef struct hopf_tt hopf_tt;   /* one TT on the device: cores + ranks   */
+
+typedef enum {
+  HOPF_OK = 0,
+  HOPF_EINVAL = 1,   /* bad argument (message in hopf_last_error)          */
+  HOPF_ENOMEM = 2,   /* device or host allocation failed                   */
+  HOPF_ECUDA = 3,    /* a CUDA call failed                                 */
+  HOPF_ENUMERIC = 4, /* NaN/Inf met, or the Jacobi SVD did not converge    */
+  HOPF_ETIMEOUT = 5, /* a bounded device-side wait expired                 */
+  HOPF_ERANKCAP = 6  /* informational: the rank cap bound, so the error   */
+                     /* exceeds the tolerance by the discarded norm        */
+} hopf_status;
+
+enum { HOPF_FP64 = 0, HOPF_MIXED = 1 };
+
+typedef struct {
+  int d;          /* number of cells / tensor modes, d >= 3               */
+  int n;          /* grid points per mode, n >= 4, even                   */
+  double nu;      /* viscosity                                            */
+  double L;       /* half-width of the a-box; <= 0: set by                */
+                  /* hopf_init_gaussian to sqrt(36.8 / min_k C0_kk)       */
+  double tol;     /* relative rounding tolerance used by hopf_step        */
+  int rank_cap;   /* rank cap used by hopf_step                           */
+  int precision;  /* HOPF_FP64 (HOPF_MIXED is rejected with HOPF_EINVAL)  */
+  int nonlinear;  /* 1: full Burgers generator; 0: drop the (i/2) D1 term */
+} hopf_params;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context bound to `stream` (cudaStream_t or NULL) on the current
+ * device.  `p` is copied.  Errors: HOPF_EINVAL (d < 3, n < 4 or odd,
+ * rank_cap < 1, tol < 0, precision not HOPF_FP64), HOPF_ENOMEM, HOPF_ECUDA. */
+hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out);
+void hopf_destroy(hopf_ctx* ctx);
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
+const char* hopf_last_error(const hopf_ctx* ctx);
+/* Sets / reads the a-box half-width L (must be > 0). */
+hopf_status hopf_set_L(hopf_ctx* ctx, double L);
+hopf_status hopf_get_L(const hopf_ctx* ctx, double* L);
+
+/* ---- model set-up -------------------------------------------------------- */
+
+/* Projection of the Gaussian initial state on the cell-indicator basis
+ * (Eq. sense): m0_k = (1/h) int_{I_k} mu, C0_jk = (1/h^2) int int K, with
+ * mu(x) = sum_{m=1}^{nmodes} alpha[m-1] cos(m x) + beta[m-1] sin(m x) and
+ * the periodic squared-exponential kernel
+ * K(x,y) = sigma^2 exp(-2 sin^2((x-y)/2) / ell^2), by 12-point tensor
+ * Gauss-Legendre quadrature per cell, computed on the device.
+ * m0: host [d]; C0: host [d*d] (symmetric).  Errors: HOPF_EINVAL. */
+hopf_status hopf_cell_moments(hopf_ctx* ctx, int nmodes, const double* alpha,
+                              const double* beta, double sigma, double ell,
+                              double* m0, double* C0);
+
+/* ---- tensors ------------------------------------------------------------- */
+
+/* Uploads a TT: ranks[d+1] (ranks[0] = ranks[d] = 1, each <= max_rank),
+ * cores as described above (2 * sum_k r_{k-1} n r_k doubles).  `max_rank`
+ * (>= every rank) fixes the device capacity of every core.  The TT has the
+ * context's d and n.  Errors: HOPF_EINVAL, HOPF_ENOMEM, HOPF_ECUDA. */
+hopf_status tt_from_host(hopf_ctx* ctx, const int* ranks, const double* cores,
+                         int max_rank, hopf_tt** out);
+/* Allocates an empty TT (all ranks 1, cores zero) with capacity max_rank. */
+hopf_status tt_create(hopf_ctx* ctx, int max_rank, hopf_tt** out);
+/* Copies ranks[d+1] to the host. */
+hopf_status tt_get_ranks(const hopf_tt* t, int* ranks);
+/* Number of doubles tt_to_host writes: 2 * sum_k r_{k-1} n r_k. */
+hopf_status tt_size(const hopf_tt* t, size_t* ndoubles);
+/* Downloads the cores (layout above) into `cores` (capacity `cap_doubles`).
+ * Errors: HOPF_EINVAL if the capacity is too small. */
+hopf_status tt_to_host(const hopf_tt* t, double* cores, size_t cap_doubles);
+/* dst <- src (dst capacity must hold src's ranks). */
+hopf_status tt_copy(hopf_ctx* ctx, const hopf_tt* src, hopf_tt* dst);
+void tt_free(hopf_tt* t);
+
+/* ---- the hot path (Sec. 4.1 and App. A) ---------------------------------- */
+
+/* Builds the TT of Phi0(a) = exp(i a.m0 - a^T C0 a / 2), zero on the
+ * boundary slot, rounded to the context's tol and rank_cap.  m0: host [d],
+ * C0: host [d*d] (column-major, symmetric positive definite).  If the
+ * context's L <= 0 it is set first to sqrt(36.8 / min_k C0_kk).  Diagonal
+ * C0 gives the exact rank-1 product for any d; a correlated C0 is built by
+ * rounding the full grid, which needs n^d <= 2^26 (else HOPF_EINVAL).
+ * *out is allocated with capacity rank_cap. */
+hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0,
+                               const double* C0, hopf_tt** out);
+
+/* out <- G(in): the generator applied core by core as a matrix product
+ * operator of bond dimension 6 (Eq. hyper1 for 1-D Burgers; rank growth
+ * under operator application, Sec. 4.1): out ranks are 6 r_k (interior).
+ * `out` must have capacity >= 6 * max rank of `in`; it is not rounded. */
+hopf_status hopf_apply_op(hopf_ctx* ctx, const hopf_tt* in, hopf_tt* out);
+
+/* In-place TT rounding (App. A, Alg. 2 in its mirrored form with the
+ * factor-then-SVD structure of Alg. 4): right-to-left Householder LQ sweep
+ * (Alg. 1 mirrored), then left-to-right truncated SVDs of the small
+ * triangular factors with per-SVD tolerance tol * ||f||_F / sqrt(d-1); each
+ * rank is the smallest rho >= 1 whose discarded tail norm is <= that
+ * tolerance, then capped at rank_cap.  forced_ranks: NULL, or host [d+1]
+ * ranks to use instead of the tolerance rule (ranks replay).
+ * discarded_norm (may be NULL): sqrt(sum of squared discarded tails), a
+ * bound on ||g - f||_F.  Returns HOPF_ERANKCAP (result valid) when the cap
+ * overrode the tolerance rule. */
+hopf_status tt_round(hopf_ctx* ctx, hopf_tt* inout, double tol, int rank_cap,
+                     const int* forced_ranks, double* discarded_norm);
+
+/* out <- sum_t coef[t] * term[t] by block concatenation (App. A, TT sum and
+ * scalar multiplication).  coef: host [2*nterms] complex.  `out` must not
+ * alias a term and needs capacity >= sum of the terms' ranks. */
+hopf_status tt_sum(hopf_ctx* ctx, int nterms, const hopf_tt* const* terms,
+                   const double* coef, hopf_tt* out);
+
+/* nsteps step-truncation RK4 steps (Eq. discrete-flow-trunc-intro with the
+ * classical RK4 increment): K_s = T[G Y_s], Y_2 = T[f + dt/2 K_1],
+ * Y_3 = T[f + dt/2 K_2], Y_4 = T[f + dt K_3],
+ * f <- T[f + dt/6 (K_1 + 2 K_2 + 2 K_3 + K_4)], every T at the context's
+ * tol and rank_cap.  `inout` needs capacity >= rank_cap.
+ * discarded_norm_sum (may be NULL): sum of the 8 * nsteps discarded norms.
+ * rank_log (may be NULL): host [8 * nsteps * (d+1)] ints receiving the ranks
+ * after every rounding (for ranks replay).  forced_log (may be NULL): host
+ * ranks to replay, same layout.  Returns HOPF_ERANKCAP if the cap bound. */
+hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* inout, double dt, int nsteps,
+                      double* discarded_norm_sum, int* rank_log,
+                      const int* forced_log);
+
+/* Mean and covariance of u from central differences of Phi at a = 0
+ * (Sec. 1: moments are functional derivatives of Phi at theta = 0):
+ * mean_k = Re[-i (Phi(+da e_k) - Phi(-da e_k)) / (2 da)],
+ * E[u_j u_k] = -(mixed central difference) for j != k, -(second difference)
+ * for j == k, cov = E[u u^T] - mean mean^T.  mean: host [d]; cov: host
+ * [d*d]; imag_resid (may be NULL): host [1], the largest imaginary part met
+ * (diagnostic; exactly zero for a Hermitian-symmetric Phi). */
+hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean,
+                              double* cov, double* imag_resid);
+
+/* Phi at npts grid multi-indices idx (host [npts*d], row-major, each in
+ * [0, n)).  vals: host [2*npts] complex. */
+hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts,
+                             const int* idx, double* vals);
+
+/* ||t||_F (by orthogonalisation, computed on the device). */
+hopf_status tt_norm(hopf_ctx* ctx, const hopf_tt* t, double* norm);
+
+/* Overwrites t with host cores (same layout and rules as tt_from_host; the
+ * ranks must fit t's capacity).  No device allocation. */
+hopf_status tt_set_from_host(hopf_tt* t, const int* ranks, const double* cores);
+
+/* ---- instrumentation ----------------------------------------------------- */
+
+/* Kernel classes of the profile record. */
+enum {
+  HOPF_K_QR = 0,      /* Householder QR panels + trailing updates           */
+  HOPF_K_APPLYQ = 1,  /* application of Householder Q factors               */
+  HOPF_K_SVD = 2,     /* one-sided Jacobi SVD                               */
+  HOPF_K_APPLY = 3,   /* operator apply (MPO x TT)                          */
+  HOPF_K_GEMM = 4,    /* small dense products (merges, projections)         */
+  HOPF_K_SUM = 5,     /* TT sums, copies, transposes                        */
+  HOPF_K_SMALL = 6,   /* rank selection, gathers, norms, set-up             */
+  HOPF_K_NCLASS = 8
+};
+typedef struct {
+  double ms[HOPF_K_NCLASS];        /* device time (CUDA events around each */
+                                   /* launch on the context's stream)      */
+  double flops[HOPF_K_NCLASS];     /* algorithmic real FLOPs               */
+  double bytes[HOPF_K_NCLASS];     /* algorithmic DRAM bytes (apply, sums) */
+  long long launches[HOPF_K_NCLASS]; /* kernels launched                   */
+  long long timed_launches[HOPF_K_NCLASS]; /* launches covered by ms      */
+} hopf_profile;
+
+/* Turns per-launch event timing on or off (launch counting is always on).
+ * Timing adds two event records per launch on the context's stream. */
+hopf_status hopf_profile_enable(hopf_ctx* ctx, int on);
+/* Copies the accumulated record into *out (synchronises the stream);
+ * reset != 0 zeroes it afterwards. */
+hopf_status hopf_profile_read(hopf_ctx* ctx, hopf_profile* out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOPF_H */

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of the C ABI in include/hopf.h.
+
+Argument marshalling only: every numerical step runs in the CUDA library
+libhopf.so.  The names follow the C calls (hopf_create, hopf_init_gaussian,
+hopf_apply_op, tt_round, hopf_step, hopf_eval_moments, ...).  There is no CPU
+fallback: if the library is missing or cannot be loaded, ``load`` raises.
+
+Cores cross the boundary as numpy complex128 arrays of shape (r_{k-1}, n, r_k)
+in the paper's column-major layout C[i,j,k] = v[i + a j + a b k] (App. A).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhopf.so")
+
+HOPF_OK, HOPF_EINVAL, HOPF_ENOMEM, HOPF_ECUDA, HOPF_ENUMERIC, HOPF_ETIMEOUT, HOPF_ERANKCAP = range(7)
+STATUS_NAMES = ["HOPF_OK", "HOPF_EINVAL", "HOPF_ENOMEM", "HOPF_ECUDA", "HOPF_ENUMERIC",
+                "HOPF_ETIMEOUT", "HOPF_ERANKCAP"]
+HOPF_FP64, HOPF_MIXED = 0, 1
+
+# Every symbol include/hopf.h declares, with (restype, argtypes).
+_vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+_pi, _pd = C.POINTER(C.c_int), C.POINTER(C.c_double)
+SIGNATURES = {
+    "hopf_create": (_i, [_vp, _vp, C.POINTER(_vp)]),
+    "hopf_destroy": (None, [_vp]),
+    "hopf_last_error": (C.c_char_p, [_vp]),
+    "hopf_set_L": (_i, [_vp, _d]),
+    "hopf_get_L": (_i, [_vp, _pd]),
+    "hopf_cell_moments": (_i, [_vp, _i, _pd, _pd, _d, _d, _pd, _pd]),
+    "tt_from_host": (_i, [_vp, _pi, _pd, _i, C.POINTER(_vp)]),
+    "tt_create": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "tt_get_ranks": (_i, [_vp, _pi]),
+    "tt_size": (_i, [_vp, C.POINTER(_sz)]),
+    "tt_to_host": (_i, [_vp, _pd, _sz]),
+    "tt_copy": (_i, [_vp, _vp, _vp]),
+    "tt_free": (None, [_vp]),
+    "hopf_init_gaussian": (_i, [_vp, _pd, _pd, C.POINTER(_vp)]),
+    "hopf_apply_op": (_i, [_vp, _vp, _vp]),
+    "tt_round": (_i, [_vp, _vp, _d, _i, _pi, _pd]),
+    "tt_sum": (_i, [_vp, _i, C.POINTER(_vp), _pd, _vp]),
+    "hopf_step": (_i, [_vp, _vp, _d, _i, _pd, _pi, _pi]),
+    "hopf_eval_moments": (_i, [_vp, _vp, _pd, _pd, _pd]),
+    "hopf_eval_points": (_i, [_vp, _vp, _i, _pi, _pd]),
+    "tt_norm": (_i, [_vp, _vp, _pd]),
+    "tt_set_from_host": (_i, [_vp, _pi, _pd]),
+    "hopf_profile_enable": (_i, [_vp, _i]),
+    "hopf_profile_read": (_i, [_vp, _vp, _i]),
+}
+
+KERNEL_CLASSES = ["qr", "apply_q", "svd", "apply", "gemm", "sum", "small", "unused"]
+
+
+class HopfProfile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("flops", C.c_double * 8), ("bytes", C.c_double * 8),
+                ("launches", C.c_longlong * 8), ("timed_launches", C.c_longlong * 8)]
+
+
+class HopfParams(C.Structure):
+    _fields_ = [("d", C.c_int), ("n", C.c_int), ("nu", C.c_double), ("L", C.c_double),
+                ("tol", C.c_double), ("rank_cap", C.c_int), ("precision", C.c_int),
+                ("nonlinear", C.c_int)]
+
+
+class HopfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhopf.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_pd)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(_pi)
+
+
+def cores_to_flat(cores):
+    """List of (r_{k-1}, n, r_k) complex arrays -> (ranks, interleaved doubles)."""
+    ranks = [1] + [int(c.shape[2]) for c in cores]
+    flat = np.concatenate([np.asarray(c, dtype=np.complex128).reshape(-1, order="F") for c in cores])
+    return np.asarray(ranks, dtype=np.int32), np.ascontiguousarray(flat).view(np.float64)
+
+
+def flat_to_cores(flat, ranks, n):
+    z = np.ascontiguousarray(flat).view(np.complex128)
+    out, off = [], 0
+    for k in range(len(ranks) - 1):
+        ne = ranks[k] * n * ranks[k + 1]
+        out.append(np.asfortranarray(z[off:off + ne].reshape((ranks[k], n, ranks[k + 1]), order="F")))
+        off += ne
+    return out
+
+
+@dataclass
+class Context:
+    """Owns one hopf_ctx; TT handles are plain ints (void*)."""
+
+    d: int
+    n: int
+    nu: float
+    tol: float
+    rank_cap: int
+    L: float = 0.0
+    nonlinear: bool = True
+    stream: int | None = None
+
+    def __post_init__(self):
+        self.lib = load()
+        p = HopfParams(self.d, self.n, self.nu, self.L, self.tol, self.rank_cap, HOPF_FP64,
+                       1 if self.nonlinear else 0)
+        h = C.c_void_p()
+        st = self.lib.hopf_create(C.byref(p), C.c_void_p(self.stream) if self.stream else None, C.byref(h))
+        if st != HOPF_OK:
+            raise HopfError(st, "hopf_create failed")
+        self.h = h
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, st, allow=(HOPF_OK,)):
+        if st not in allow:
+            raise HopfError(st, self.lib.hopf_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hopf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls ----------------------------------------------------------------
+    def hopf_set_L(self, L):
+        self._check(self.lib.hopf_set_L(self.h, float(L)))
+
+    def hopf_get_L(self):
+        v = C.c_double()
+        self._check(self.lib.hopf_get_L(self.h, C.byref(v)))
+        return v.value
+
+    def hopf_cell_moments(self, alpha, beta, sigma, ell):
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        m0 = np.zeros(self.d)
+        C0 = np.zeros(self.d * self.d)
+        self._check(self.lib.hopf_cell_moments(self.h, len(a), _dptr(a), _dptr(b), float(sigma), float(ell),
+                                               _dptr(m0), _dptr(C0)))
+        return m0, C0.reshape(self.d, self.d, order="F")
+
+    def tt_from_host(self, cores, max_rank=None):
+        ranks, flat = cores_to_flat(cores)
+        max_rank = int(max_rank or max(ranks))
+        h = C.c_void_p()
+        self._check(self.lib.tt_from_host(self.h, _iptr(ranks), _dptr(flat), max_rank, C.byref(h)))
+        return h
+
+    def tt_create(self, max_rank):
+        h = C.c_void_p()
+        self._check(self.lib.tt_create(self.h, int(max_rank), C.byref(h)))
+        return h
+
+    def tt_get_ranks(self, t):
+        r = np.zeros(self.d + 1, dtype=np.int32)
+        self._check(self.lib.tt_get_ranks(t, _iptr(r)))
+        return [int(x) for x in r]
+
+    def tt_to_host(self, t):
+        nd = C.c_size_t()
+        self._check(self.lib.tt_size(t, C.byref(nd)))
+        buf = np.zeros(nd.value, dtype=np.float64)
+        self._check(self.lib.tt_to_host(t, _dptr(buf), nd.value))
+        return flat_to_cores(buf, self.tt_get_ranks(t), self.n)
+
+    def tt_copy(self, src, dst):
+        self._check(self.lib.tt_copy(self.h, src, dst))
+
+    def tt_free(self, t):
+        self.lib.tt_free(t)
+
+    def hopf_init_gaussian(self, m0, C0):
+        m = np.ascontiguousarray(m0, dtype=np.float64)
+        c = np.asfortranarray(C0, dtype=np.float64).reshape(-1, order="F").copy()
+        h = C.c_void_p()
+        self._check(self.lib.hopf_init_gaussian(self.h, _dptr(m), _dptr(c), C.byref(h)),
+                    allow=(HOPF_OK, HOPF_ERANKCAP))
+        return h
+
+    def hopf_apply_op(self, t_in, t_out):
+        self._check(self.lib.hopf_apply_op(self.h, t_in, t_out))
+
+    def tt_round(self, t, tol, cap, forced_ranks=None):
+        f = None if forced_ranks is None else np.ascontiguousarray(forced_ranks, dtype=np.int32)
+        disc = C.c_double()
+        st = self._check(self.lib.tt_round(self.h, t, float(tol), int(cap), None if f is None else _iptr(f),
+                                           C.byref(disc)), allow=(HOPF_OK, HOPF_ERANKCAP))
+        return disc.value, st
+
+    def tt_sum(self, terms, coefs, out):
+        arr = (C.c_void_p * len(terms))(*[t.value if isinstance(t, C.c_void_p) else t for t in terms])
+        cf = np.zeros(2 * len(coefs))
+        cf[0::2] = np.real(coefs)
+        cf[1::2] = np.imag(coefs)
+        self._check(self.lib.tt_sum(self.h, len(terms), arr, _dptr(cf), out))
+
+    def hopf_step(self, t, dt, nsteps, record=False, replay=None):
+        disc = C.c_double()
+        log = np.zeros(8 * nsteps * (self.d + 1), dtype=np.int32) if record else None
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.int32).reshape(-1)
+        st = self._check(self.lib.hopf_step(self.h, t, float(dt), int(nsteps), C.byref(disc),
+                                            None if log is None else _iptr(log),
+                                            None if rep is None else _iptr(rep)),
+                         allow=(HOPF_OK, HOPF_ERANKCAP))
+        out = {"discarded": disc.value, "status": st}
+        if record:
+            out["ranks"] = log.reshape(8 * nsteps, self.d + 1)
+        return out
+
+    def hopf_eval_moments(self, t):
+        mean = np.zeros(self.d)
+        cov = np.zeros(self.d * self.d)
+        ir = C.c_double()
+        self._check(self.lib.hopf_eval_moments(self.h, t, _dptr(mean), _dptr(cov), C.byref(ir)))
+        return mean, cov.reshape(self.d, self.d, order="F"), ir.value
+
+    def hopf_eval_points(self, t, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        vals = np.zeros(2 * idx.shape[0])
+        self._check(self.lib.hopf_eval_points(self.h, t, idx.shape[0], _iptr(idx), _dptr(vals)))
+        return vals.view(np.complex128)
+
+    def tt_set_from_host(self, t, cores=None, ranks=None, flat=None):
+        """Overwrite t from host cores, or from (ranks, flat doubles) already
+        staged (e.g. in pinned memory: flat may be a ctypes pointer)."""
+        if cores is not None:
+            ranks, flat = cores_to_flat(cores)
+        ranks = np.ascontiguousarray(ranks, dtype=np.int32)
+        ptr = flat if isinstance(flat, C.POINTER(C.c_double)) else _dptr(flat)
+        self._check(self.lib.tt_set_from_host(t, _iptr(ranks), ptr))
+
+    def tt_to_host_into(self, t, ptr, ndoubles):
+        """Download into a caller buffer (ctypes double pointer)."""
+        self._check(self.lib.tt_to_host(t, ptr, int(ndoubles)))
+
+    def tt_size(self, t):
+        nd = C.c_size_t()
+        self._check(self.lib.tt_size(t, C.byref(nd)))
+        return nd.value
+
+    def hopf_profile_enable(self, on=True):
+        self._check(self.lib.hopf_profile_enable(self.h, 1 if on else 0))
+
+    def hopf_profile_read(self, reset=True):
+        p = HopfProfile()
+        self._check(self.lib.hopf_profile_read(self.h, C.byref(p), 1 if reset else 0))
+        return {name: {"ms": p.ms[i], "flops": p.flops[i], "bytes": p.bytes[i],
+                       "launches": int(p.launches[i]), "timed_launches": int(p.timed_launches[i])}
+                for i, name in enumerate(KERNEL_CLASSES)}
+
+    def tt_norm(self, t):
+        v = C.c_double()
+        self._check(self.lib.tt_norm(self.h, t, C.byref(v)))
+        return v.value

@@ -1,0 +1,129 @@
+// Shared device helpers: complex float64 arithmetic on double2, block
+// reductions, and a bounded grid-wide barrier for cooperative launches.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+typedef double2 cplx;
+
+#define HD __host__ __device__ __forceinline__
+#define DV __device__ __forceinline__
+
+HD cplx mk(double re, double im) { return make_double2(re, im); }
+HD cplx cadd(cplx a, cplx b) { return mk(a.x + b.x, a.y + b.y); }
+HD cplx csub(cplx a, cplx b) { return mk(a.x - b.x, a.y - b.y); }
+HD cplx cscale(cplx a, double s) { return mk(a.x * s, a.y * s); }
+HD cplx cconj(cplx a) { return mk(a.x, -a.y); }
+HD cplx cmul(cplx a, cplx b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// conj(a) * b
+HD cplx cmulc(cplx a, cplx b) { return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+HD double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+// acc + a * b
+DV cplx cfma(cplx a, cplx b, cplx acc) {
+  return mk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc + conj(a) * b
+DV cplx cfmac(cplx a, cplx b, cplx acc) {
+  return mk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+HD cplx cinv(cplx a) {
+  double s = 1.0 / (a.x * a.x + a.y * a.y);
+  return mk(a.x * s, -a.y * s);
+}
+
+// Sum over a warp (all 32 lanes active).
+DV double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+DV cplx warp_sum(cplx v) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  return v;
+}
+
+// Deterministic block sum; `red` needs blockDim.x/32 slots.  Every thread
+// gets the result.
+template <typename T>
+DV T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T s = red[0];
+  for (int i = 1; i < nw; ++i) s = s + red[i];
+  __syncthreads();
+  return s;
+}
+template <>
+DV cplx block_sum<cplx>(cplx v, cplx* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  cplx s = red[0];
+  for (int i = 1; i < nw; ++i) s = cadd(s, red[i]);
+  __syncthreads();
+  return s;
+}
+
+DV uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier state (device memory, zeroed before the first launch).
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;  // nonzero after a wait expired
+  int pad;
+};
+
+// Barrier across all CTAs of a cooperative launch (co-residency guaranteed
+// by cudaLaunchCooperativeKernel).  Every wait is bounded: after
+// `timeout_ns` of wall time the CTA records the expiry in bar->err and
+// leaves; callers check grid_failed() and return early.
+constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
+
+DV void grid_sync(GridBar* bar) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &bar->gen;
+    volatile int* verr = &bar->err;
+    if (*verr == 0) {
+      const unsigned int g = *vgen;
+      __threadfence();
+      const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+      const unsigned int arrived = atomicAdd(&bar->count, 1u);
+      if (arrived == nb - 1) {
+        atomicExch(&bar->count, 0u);
+        __threadfence();
+        atomicAdd(&bar->gen, 1u);
+      } else {
+        const uint64_t t0 = global_ns();
+        unsigned int spins = 0;
+        while (*vgen == g) {
+          if (((++spins) & 255u) == 0u) {
+            if (*verr != 0) break;
+            if (global_ns() - t0 > kBarrierTimeoutNs) {
+              atomicExch(&bar->err, 1);
+              break;
+            }
+          }
+          __nanosleep(64);
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+DV bool grid_failed(const GridBar* bar) {
+  return *((volatile const int*)&bar->err) != 0;
+}

@@ -1,0 +1,1095 @@
+// C ABI of the solver (include/hopf.h): contexts, tensors, and the host
+// orchestration of the hot path.  All arithmetic runs in the kernels of
+// qr.cu, svd.cu and tt.cu; the host keeps the TT ranks, launches kernels with
+// exact dimensions, and reads back one small record per truncation (the rank
+// chosen for the next core depends on the singular values just computed).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hopf.h"
+#include "kernels.h"
+
+// cplx (double2) comes from common.cuh
+
+struct hopf_tt {
+  hopf_ctx* ctx = nullptr;
+  int d = 0, n = 0, cap_rank = 0;
+  std::vector<size_t> core_cap;  // capacity (elements) of each core buffer
+  std::vector<cplx*> cores;
+  std::vector<int> ranks;        // host copy, authoritative
+  cplx** d_ptrs = nullptr;       // device copy of `cores`
+  int* d_ranks = nullptr;        // device copy of `ranks`
+};
+
+struct RoundWs {
+  size_t elems = 0;  // capacity of each big buffer (elements)
+  int d = 0;
+  int kcap = 0;      // largest rank the workspace serves
+  std::vector<cplx*> B;   // per-core QR buffers (phase 1)
+  cplx* W1 = nullptr;     // phase-2 scratch
+  cplx* tau = nullptr;    // d * kcap
+  cplx* T = nullptr;      // d * tstride
+  size_t tstride = 0;
+  cplx* tau2 = nullptr;   // kcap
+  cplx* T2 = nullptr;     // tstride
+  cplx* Rb = nullptr;     // kcap * kcap
+  cplx* Mb = nullptr;     // kcap * kcap
+  cplx* Jb = nullptr;     // kcap * kcap
+  cplx* Ub = nullptr;     // kcap * kcap
+  cplx* Sb = nullptr;     // kcap * kcap
+  double* sig = nullptr;  // 2 * kcap + 2
+  int* perm = nullptr;    // kcap
+};
+
+struct hopf_ctx {
+  hopf_params p{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double L = 0.0;
+  // operator tables
+  cplx* d_coef = nullptr;             // 5 ops x 3 x n
+  unsigned char* d_blocks = nullptr;  // 3 site kinds x 36
+  double* d_agrid = nullptr;          // n
+  std::vector<double> agrid;
+  // cooperative-kernel workspace
+  hk::CoopWs coop{};
+  int coop_kcap = 0;
+  // small device scalars and pinned mirrors
+  double* d_dbl = nullptr;  // [16]
+  int* d_int = nullptr;     // [16]
+  double* h_dbl = nullptr;  // pinned [16]
+  int* h_int = nullptr;     // pinned [16]
+  RoundWs rw;
+  // hopf_step workspace
+  hopf_tt* big = nullptr;
+  hopf_tt* kst[4] = {nullptr, nullptr, nullptr, nullptr};
+  hopf_tt* ytmp = nullptr;
+  hk::SumTerm* d_terms = nullptr;  // [16]
+  std::vector<void*> extra;        // other device allocations to free
+  // launch instrumentation
+  struct ProfRec {
+    int cls, slot;
+    double flops, bytes;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // 2 per slot
+  std::vector<ProfRec> prof_recs;
+  hopf_profile prof{};
+};
+
+// ---------------------------------------------------------------------------
+namespace {
+
+hopf_status fail(hopf_ctx* c, hopf_status st, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return st;
+}
+
+#define CK(expr)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      if (e_ == cudaErrorMemoryAllocation) {                                        \
+        cudaGetLastError();                                                         \
+        return fail(ctx, HOPF_ENOMEM, "%s: %s", #expr, cudaGetErrorString(e_));     \
+      }                                                                             \
+      return fail(ctx, HOPF_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));        \
+    }                                                                               \
+  } while (0)
+
+#define TRY(expr)                        \
+  do {                                   \
+    hopf_status s_ = (expr);             \
+    if (s_ != HOPF_OK) return s_;        \
+  } while (0)
+
+// ---- launch instrumentation ----------------------------------------------------
+constexpr int kProfSlots = 4096;
+
+hopf_status prof_flush(hopf_ctx* ctx) {
+  if (ctx->prof_recs.empty()) return HOPF_OK;
+  CK(cudaEventSynchronize(ctx->prof_ev[2 * ctx->prof_recs.back().slot + 1]));
+  for (const auto& r : ctx->prof_recs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * r.slot], ctx->prof_ev[2 * r.slot + 1]));
+    ctx->prof.ms[r.cls] += ms;
+    ctx->prof.timed_launches[r.cls] += 1;
+  }
+  ctx->prof_recs.clear();
+  return HOPF_OK;
+}
+
+int prof_begin(hopf_ctx* ctx) {
+  if (!ctx->prof_on) return -1;
+  if ((int)ctx->prof_recs.size() >= kProfSlots && prof_flush(ctx) != HOPF_OK) return -1;
+  const int slot = (int)ctx->prof_recs.size();
+  if (cudaEventRecord(ctx->prof_ev[2 * slot], ctx->stream) != cudaSuccess) return -1;
+  return slot;
+}
+
+void prof_end(hopf_ctx* ctx, int slot, int cls, double flops, double bytes, int nlaunch) {
+  ctx->prof.launches[cls] += nlaunch;
+  ctx->prof.flops[cls] += flops;
+  ctx->prof.bytes[cls] += bytes;
+  if (slot < 0) return;
+  if (cudaEventRecord(ctx->prof_ev[2 * slot + 1], ctx->stream) != cudaSuccess) return;
+  ctx->prof_recs.push_back({cls, slot, flops, bytes});
+}
+
+// Launch `expr` (a kernel launcher returning cudaError_t) as one profiled
+// unit of class `cls` with algorithmic flops/bytes and `nl` kernels.
+#define LAUNCH(cls, flops, bytes, nl, expr)                 \
+  do {                                                      \
+    const int ps_ = prof_begin(ctx);                        \
+    CK(expr);                                               \
+    prof_end(ctx, ps_, (cls), (flops), (bytes), (nl));      \
+  } while (0)
+
+// Algorithmic real FLOPs (complex = 4 real multiplies + adds per MAC pair):
+// Householder QR of m x k (LAPACK count for the complex case).
+double qr_flops(double m, double k) {
+  return (m >= k) ? 8.0 * m * k * k - 8.0 * k * k * k / 3.0 : 8.0 * k * m * m - 8.0 * m * m * m / 3.0;
+}
+// Q (m x m, p reflectors) applied to an m x q block.
+double applyq_flops(double m, double q, double p) { return 16.0 * m * q * p - 8.0 * q * p * p; }
+// C = A R^H with R upper trapezoidal N x K: sum_j (K - j) MACs per row.
+double arh_flops(double M, double K, double N) {
+  const double Nn = std::min(N, K);
+  return 8.0 * M * (Nn * K - Nn * (Nn - 1) / 2.0);
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// ---- per-mode operator coefficients ------------------------------------------
+// (op x)[i] = lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1] on a_i = (i - n/2) da,
+// slot 0 with zero row and column for A, D, S (and so for P, Q, Z).
+hopf_status build_ops(hopf_ctx* ctx) {
+  const int n = ctx->p.n, d = ctx->p.d;
+  const double L = ctx->L;
+  const double da = 2.0 * L / n;
+  const double h = 2.0 * M_PI / d;
+  ctx->agrid.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) ctx->agrid[i] = (i - n / 2) * da;
+  std::vector<cplx> coef((size_t)5 * 3 * n, cplx{0.0, 0.0});
+  auto set = [&](int op, int which, int i, cplx v) { coef[(size_t)op * 3 * n + (size_t)which * n + i] = v; };
+  const cplx cS = ctx->p.nonlinear ? cplx{0.0, 1.0 / (4.0 * h)} : cplx{0.0, 0.0};
+  const double e = ctx->p.nu / (h * h);
+  for (int i = 0; i < n; ++i) {
+    // identity keeps every slot
+    set(hk::OP_I, 1, i, cplx{1.0, 0.0});
+    if (i == 0) continue;
+    const double a = ctx->agrid[i];
+    set(hk::OP_A, 1, i, cplx{a, 0.0});
+    // D: -1/(2da) on the left (column >= 1), +1/(2da) on the right (column < n)
+    const double dlo = (i >= 2) ? -1.0 / (2 * da) : 0.0;
+    const double dup = (i + 1 < n) ? 1.0 / (2 * da) : 0.0;
+    // S: (1, -2, 1)/da^2
+    const double slo = (i >= 2) ? 1.0 / (da * da) : 0.0;
+    const double sdi = -2.0 / (da * da);
+    const double sup = (i + 1 < n) ? 1.0 / (da * da) : 0.0;
+    // P = cS + eD, Q = -cS + eD (c purely imaginary)
+    set(hk::OP_P, 0, i, cplx{e * dlo, cS.y * slo});
+    set(hk::OP_P, 1, i, cplx{0.0, cS.y * sdi});
+    set(hk::OP_P, 2, i, cplx{e * dup, cS.y * sup});
+    set(hk::OP_Q, 0, i, cplx{e * dlo, -cS.y * slo});
+    set(hk::OP_Q, 1, i, cplx{0.0, -cS.y * sdi});
+    set(hk::OP_Q, 2, i, cplx{e * dup, -cS.y * sup});
+    // Z = -2e A D
+    set(hk::OP_Z, 0, i, cplx{-2.0 * e * a * dlo, 0.0});
+    set(hk::OP_Z, 2, i, cplx{-2.0 * e * a * dup, 0.0});
+  }
+  hopf_ctx* c = ctx;
+  (void)c;
+  CK(cudaMemcpyAsync(ctx->d_coef, coef.data(), coef.size() * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_agrid, ctx->agrid.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HOPF_OK;
+}
+
+// MPO block tables: kind 0 first site (row), 1 interior, 2 last site (column).
+void mpo_tables(unsigned char out[3][36]) {
+  for (int k = 0; k < 3; ++k)
+    for (int e = 0; e < 36; ++e) out[k][e] = hk::OP_NONE;
+  using namespace hk;
+  // bond states: 0 idle, 1 A placed (P pending), 2 Q placed (A pending), 3 done,
+  // 4 wrap P at site 1 (A pending at d), 5 wrap A at site 1 (Q pending at d)
+  const unsigned char first[6] = {OP_I, OP_A, OP_Q, OP_Z, OP_P, OP_A};
+  for (int b = 0; b < 6; ++b) out[0][b] = first[b];  // Al = 1, Ar = 6
+  auto I6 = [&](int a, int b, unsigned char op) { out[1][a * 6 + b] = op; };
+  I6(0, 0, OP_I); I6(0, 1, OP_A); I6(0, 2, OP_Q); I6(0, 3, OP_Z);
+  I6(1, 3, OP_P); I6(2, 3, OP_A); I6(3, 3, OP_I); I6(4, 4, OP_I); I6(5, 5, OP_I);
+  const unsigned char last[6] = {OP_Z, OP_P, OP_A, OP_I, OP_A, OP_Q};
+  for (int a = 0; a < 6; ++a) out[2][a] = last[a];  // Al = 6, Ar = 1
+}
+
+hopf_status coop_reserve(hopf_ctx* ctx, int kcap) {
+  if (kcap <= ctx->coop_kcap) return HOPF_OK;
+  kcap = std::max(kcap, 64);
+  hk::CoopWs& w = ctx->coop;
+  cudaFree(w.pc);
+  cudaFree(w.wfin);
+  w.pc = nullptr;
+  w.wfin = nullptr;
+  const int G = hk::dev_info().sm_count;
+  w.pc_elems = (size_t)G * 32 * (size_t)(kcap + 64);
+  w.wfin_elems = (size_t)32 * (size_t)(kcap + 64);
+  CK(dalloc(&w.pc, w.pc_elems));
+  CK(dalloc(&w.wfin, w.wfin_elems));
+  ctx->coop_kcap = kcap;
+  return HOPF_OK;
+}
+
+hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
+  size_t need = 0;
+  for (size_t c : t->core_cap) need = std::max(need, c);
+  const int kcap = t->cap_rank;
+  RoundWs& w = ctx->rw;
+  if (w.elems >= need && w.kcap >= kcap && w.d >= t->d) return HOPF_OK;
+  for (cplx* b : w.B) cudaFree(b);
+  cudaFree(w.W1); cudaFree(w.tau); cudaFree(w.T); cudaFree(w.tau2); cudaFree(w.T2);
+  cudaFree(w.Rb); cudaFree(w.Mb); cudaFree(w.Jb); cudaFree(w.Ub); cudaFree(w.Sb);
+  cudaFree(w.sig); cudaFree(w.perm);
+  w = RoundWs{};
+  const size_t elems = std::max(need, w.elems);
+  const int d = t->d;
+  const int K = std::max(kcap, t->n);  // ranks may reach n at the ends
+  w.B.assign(d, nullptr);
+  for (int c = 0; c < d; ++c) CK(dalloc(&w.B[c], elems));
+  CK(dalloc(&w.W1, elems));
+  w.tstride = (size_t)(K / 8 + 2) * 32 * 32;
+  CK(dalloc(&w.tau, (size_t)d * K));
+  CK(dalloc(&w.T, (size_t)d * w.tstride));
+  CK(dalloc(&w.tau2, (size_t)K));
+  CK(dalloc(&w.T2, w.tstride));
+  CK(dalloc(&w.Rb, (size_t)K * K));
+  CK(dalloc(&w.Mb, (size_t)K * K));
+  CK(dalloc(&w.Jb, (size_t)K * K));
+  CK(dalloc(&w.Ub, (size_t)K * K));
+  CK(dalloc(&w.Sb, (size_t)K * K));
+  CK(dalloc(&w.sig, (size_t)2 * K + 2));
+  CK(dalloc(&w.perm, (size_t)K));
+  w.elems = elems;
+  w.d = d;
+  w.kcap = K;
+  return coop_reserve(ctx, K);
+}
+
+hopf_status tt_alloc(hopf_ctx* ctx, int cap_rank, hopf_tt** out) {
+  hopf_tt* t = new (std::nothrow) hopf_tt();
+  if (!t) return fail(ctx, HOPF_ENOMEM, "host allocation failed");
+  t->ctx = ctx;
+  t->d = ctx->p.d;
+  t->n = ctx->p.n;
+  t->cap_rank = cap_rank;
+  t->core_cap.resize(t->d);
+  t->cores.assign(t->d, nullptr);
+  t->ranks.assign(t->d + 1, 1);
+  auto cleanup = [&]() {
+    for (cplx* c : t->cores) cudaFree(c);
+    cudaFree(t->d_ptrs);
+    cudaFree(t->d_ranks);
+    delete t;
+  };
+  for (int k = 0; k < t->d; ++k) {
+    const size_t rl = (k == 0) ? 1 : (size_t)cap_rank;
+    const size_t rr = (k == t->d - 1) ? 1 : (size_t)cap_rank;
+    t->core_cap[k] = rl * t->n * rr;
+    cudaError_t e = dalloc(&t->cores[k], t->core_cap[k]);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return fail(ctx, HOPF_ENOMEM, "tensor allocation (%zu bytes per core): %s",
+                  t->core_cap[k] * sizeof(cplx), cudaGetErrorString(e));
+    }
+  }
+  if (dalloc(&t->d_ptrs, t->d) != cudaSuccess || dalloc(&t->d_ranks, t->d + 1) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, HOPF_ENOMEM, "tensor metadata allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(t->d_ptrs, t->cores.data(), t->d * sizeof(cplx*), cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, HOPF_ECUDA, "%s", cudaGetErrorString(e));
+  }
+  *out = t;
+  return HOPF_OK;
+}
+
+hopf_status sync_meta(hopf_ctx* ctx, hopf_tt* t) {
+  CK(cudaMemcpyAsync(t->d_ranks, t->ranks.data(), (t->d + 1) * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  return HOPF_OK;
+}
+
+size_t core_elems(const hopf_tt* t, int k) { return (size_t)t->ranks[k] * t->n * t->ranks[k + 1]; }
+
+hopf_status check_fit(hopf_ctx* ctx, const hopf_tt* t, const std::vector<int>& r) {
+  for (int k = 0; k < t->d; ++k)
+    if ((size_t)r[k] * t->n * r[k + 1] > t->core_cap[k])
+      return fail(ctx, HOPF_EINVAL, "core %d of size %d x %d x %d exceeds the tensor's capacity (max rank %d)",
+                  k, r[k], t->n, r[k + 1], t->cap_rank);
+  return HOPF_OK;
+}
+
+hopf_status read_small(hopf_ctx* ctx, int nint, int ndbl) {
+  if (nint) CK(cudaMemcpyAsync(ctx->h_int, ctx->d_int, nint * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (ndbl) CK(cudaMemcpyAsync(ctx->h_dbl, ctx->d_dbl, ndbl * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HOPF_OK;
+}
+
+hopf_status check_barrier(hopf_ctx* ctx) {
+  GridBar hb;
+  CK(cudaMemcpyAsync(&hb, ctx->coop.bar, sizeof(GridBar), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hb.err) {
+    cudaMemsetAsync(ctx->coop.bar, 0, sizeof(GridBar), ctx->stream);
+    return fail(ctx, HOPF_ETIMEOUT, "a grid barrier wait expired");
+  }
+  return HOPF_OK;
+}
+
+// Phase 1 of the rounding: right-to-left Householder LQ sweep (App. A,
+// Alg. 1 mirrored).  Reads the cores of t (unchanged), leaves B_c = the
+// factored H(Y_c)^H with its reflectors for c >= 1 and B_0 = V(Y_0 L_1)
+// explicitly; p[c] = rank after orthogonalisation at bond c.  Returns
+// ||f||_F^2 in ctx->d_dbl[0].
+hopf_status orth_sweep(hopf_ctx* ctx, const hopf_tt* t, std::vector<int>& p, std::vector<int>& nbv) {
+  RoundWs& w = ctx->rw;
+  const int d = t->d, n = t->n;
+  const std::vector<int>& r = t->ranks;
+  p.assign(d + 1, 1);
+  nbv.assign(d, 32);
+  // B_{d-1} = H(X_{d-1})^H: X_{d-1} is r[d-1] x n (x 1)
+  LAUNCH(HOPF_K_SUM, 0, 32.0 * r[d - 1] * n, 1, hk::conj_transpose(t->cores[d - 1], r[d - 1], r[d - 1], n, w.B[d - 1], n, ctx->stream));
+  for (int c = d - 1; c >= 1; --c) {
+    const int m = n * p[c + 1], k = r[c];
+    LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1, hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream));
+    p[c] = std::min(m, k);
+    // merge L_c = R_c^H into core c-1
+    const int rl = r[c - 1];
+    if (c - 1 >= 1) {
+      LAUNCH(HOPF_K_GEMM, arh_flops((double)rl * n, k, p[c]), 0, 1, hk::gemm_a_rh(t->cores[c - 1], rl * n, rl * n, k, w.B[c], m, p[c], w.B[c - 1], n * p[c], 1, rl, n, ctx->stream));
+    } else {
+      LAUNCH(HOPF_K_GEMM, arh_flops(n, k, p[1]), 0, 1, hk::gemm_a_rh(t->cores[0], n, n, k, w.B[1], m, p[1], w.B[0], n, 0, 1, n, ctx->stream));
+    }
+  }
+  LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::frob2(w.B[0], n, n, p[1], ctx->d_dbl, ctx->stream));
+  return HOPF_OK;
+}
+
+hopf_status round_impl(hopf_ctx* ctx, hopf_tt* t, double tol, int cap, const int* forced,
+                       double* disc_out, bool* capped) {
+  const int d = t->d, n = t->n;
+  TRY(round_reserve(ctx, t));
+  RoundWs& w = ctx->rw;
+  std::vector<int> p, nbv;
+  TRY(orth_sweep(ctx, t, p, nbv));
+  TRY(read_small(ctx, 0, 1));
+  TRY(check_barrier(ctx));
+  const double nrm2 = ctx->h_dbl[0];
+  if (!std::isfinite(nrm2)) return fail(ctx, HOPF_ENUMERIC, "non-finite norm in rounding");
+  const double eps_hat = tol * std::sqrt(nrm2) / std::sqrt((double)(d - 1));
+  ctx->h_dbl[1] = eps_hat;
+  CK(cudaMemcpyAsync(ctx->d_dbl + 1, ctx->h_dbl + 1, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+
+  std::vector<int> rho(d + 1, 1);
+  double disc2 = 0.0;
+  bool cap_hit = false;
+  for (int c = 0; c <= d - 2; ++c) {
+    cplx* Z;
+    const int Mrows = rho[c] * n, cols = p[c + 1];
+    if (c == 0) {
+      Z = w.B[0];
+    } else {
+      const int mc = n * p[c + 1];
+      LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::init_sh_pad(w.Sb, rho[c], rho[c], p[c], t->cores[c], mc, mc, ctx->stream));
+      LAUNCH(HOPF_K_APPLYQ, applyq_flops(mc, rho[c], p[c]), 0, 1, hk::ormqr(w.B[c], mc, mc, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c],
+                   t->cores[c], mc, rho[c], ctx->coop, ctx->stream));
+      LAUNCH(HOPF_K_SUM, 0, 32.0 * mc * rho[c], 1, hk::conj_transpose(t->cores[c], mc, mc, rho[c], w.W1, rho[c], ctx->stream));
+      Z = w.W1;
+    }
+    int nb2 = 32;
+    LAUNCH(HOPF_K_QR, qr_flops(Mrows, cols), 0, 1, hk::geqrf(Z, Mrows, Mrows, cols, w.tau2, w.T2, &nb2, ctx->coop, ctx->stream));
+    const int pp = std::min(Mrows, cols);
+    LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::extract_r(Z, Mrows, pp, cols, w.Rb, pp, ctx->stream));
+    const int forced_c = forced ? forced[c + 1] : 0;
+    const bool case1 = (pp >= cols);
+    const int nsv = case1 ? cols : pp;
+    if (forced && (forced_c < 1 || forced_c > nsv))
+      return fail(ctx, HOPF_EINVAL, "forced rank %d at bond %d outside [1, %d]", forced_c, c + 1, nsv);
+    // Jacobi leaves out pairs far below the truncation tolerance (theta);
+    // if the rank kept reaches below theta, finish the SVD exactly so that
+    // every kept singular vector is orthogonal to all others.
+    for (int pass = 0; pass < 2; ++pass) {
+      const double* eh = (pass == 0) ? ctx->d_dbl + 1 : nullptr;
+      if (case1) {
+        if (pass == 0)
+          CK(cudaMemcpyAsync(w.Mb, w.Rb, (size_t)pp * cols * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
+        LAUNCH(HOPF_K_SVD, 0, 0, 1, hk::jacobi_svd(w.Mb, pp, pp, cols, nullptr, 1, 0, eh, 0, ctx->coop, ctx->stream));
+        LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::rank_select(w.Mb, pp, pp, cols, ctx->d_dbl + 1, cap, forced_c, w.sig, w.perm, ctx->d_int, ctx->d_dbl + 2, ctx->stream));
+      } else {
+        if (pass == 0) LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::conj_transpose(w.Rb, pp, pp, cols, w.Mb, cols, ctx->stream));
+        LAUNCH(HOPF_K_SVD, 0, 0, pass == 0 ? 2 : 1,
+               hk::jacobi_svd(w.Mb, cols, cols, pp, w.Jb, pp, 1, eh, pass == 0, ctx->coop, ctx->stream));
+        LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::rank_select(w.Mb, cols, cols, pp, ctx->d_dbl + 1, cap, forced_c, w.sig, w.perm, ctx->d_int, ctx->d_dbl + 2, ctx->stream));
+      }
+      CK(cudaMemcpyAsync(ctx->d_int + 2, ctx->coop.counters + 63, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+      TRY(read_small(ctx, 3, 5));
+      TRY(check_barrier(ctx));
+      if (ctx->h_int[2] < 0) return fail(ctx, HOPF_ENUMERIC, "Jacobi SVD did not converge at bond %d", c + 1);
+      const double theta = std::max(1e-3 * eps_hat, 64.0 * 2.220446049250313e-16 * std::sqrt(ctx->h_dbl[4]));
+      if (pass == 0 && !(ctx->h_dbl[3] > theta)) continue;  // smallest kept sigma below theta
+      break;
+    }
+    const int rnew = ctx->h_int[0];
+    const int rtol = ctx->h_int[1];
+    const double delta = ctx->h_dbl[2];
+    if (!std::isfinite(delta)) return fail(ctx, HOPF_ENUMERIC, "non-finite singular values at bond %d", c + 1);
+    if (!forced && rtol > cap) cap_hit = true;
+    // the new core must fit the tensor's capacity
+    if ((size_t)rho[c] * n * rnew > t->core_cap[c])
+      return fail(ctx, HOPF_EINVAL, "rank %d at bond %d exceeds the tensor's capacity", rnew, c + 1);
+    rho[c + 1] = rnew;
+    disc2 += delta * delta;
+    // new core c = Q [U_rho; 0]
+    if (case1) {
+      LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::gather_u(w.Mb, pp, pp, w.perm, w.sig, 1, rnew, t->cores[c], Mrows, Mrows, w.Ub, pp, ctx->stream));
+    } else {
+      LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::gather_u(w.Jb, pp, pp, w.perm, w.sig, 0, rnew, t->cores[c], Mrows, Mrows, w.Ub, pp, ctx->stream));
+    }
+    LAUNCH(HOPF_K_APPLYQ, applyq_flops(Mrows, rnew, pp), 0, 1, hk::ormqr(Z, Mrows, Mrows, pp, w.tau2, w.T2, nb2, t->cores[c], Mrows, rnew, ctx->coop, ctx->stream));
+    // S = U_rho^H R (rho x cols)
+    LAUNCH(HOPF_K_GEMM, 8.0 * rnew * pp * cols, 0, 1, hk::gemm_uh_r(w.Ub, pp, rnew, pp, w.Rb, pp, cols, w.Sb, rnew, ctx->stream));
+  }
+  // last core: C = Q_{B,d-1} [S^H; 0] (n x rho), core = C^H
+  {
+    const int c = d - 1;
+    LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::init_sh_pad(w.Sb, rho[c], rho[c], p[c], w.W1, n, n, ctx->stream));
+    LAUNCH(HOPF_K_APPLYQ, applyq_flops(n, rho[c], p[c]), 0, 1, hk::ormqr(w.B[c], n, n, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c], w.W1, n, rho[c],
+                 ctx->coop, ctx->stream));
+    LAUNCH(HOPF_K_SUM, 0, 32.0 * n * rho[c], 1, hk::conj_transpose(w.W1, n, n, rho[c], t->cores[c], rho[c], ctx->stream));
+  }
+  rho[d] = 1;
+  t->ranks = rho;
+  TRY(sync_meta(ctx, t));
+  if (disc_out) *disc_out = std::sqrt(disc2);
+  if (capped) *capped = cap_hit;
+  return HOPF_OK;
+}
+
+hopf_status apply_impl(hopf_ctx* ctx, const hopf_tt* in, hopf_tt* out) {
+  const int d = in->d, n = in->n;
+  std::vector<int> r(d + 1, 1);
+  for (int k = 1; k < d; ++k) r[k] = 6 * in->ranks[k];
+  TRY(check_fit(ctx, out, r));
+  hk::OpTable ops{ctx->d_coef, n};
+  for (int k = 0; k < d; ++k) {
+    const int kind = (k == 0) ? 0 : (k == d - 1 ? 2 : 1);
+    const int Al = (k == 0) ? 1 : 6, Ar = (k == d - 1) ? 1 : 6;
+    const double rd = (double)in->ranks[k] * n * in->ranks[k + 1];
+    LAUNCH(HOPF_K_APPLY, 0, 16.0 * rd * (1.0 + (double)Al * Ar), 1,
+           hk::apply_core(in->cores[k], in->ranks[k], n, in->ranks[k + 1], out->cores[k], Al, Ar,
+                          ctx->d_blocks + 36 * kind, ops, ctx->stream));
+  }
+  out->ranks = r;
+  return sync_meta(ctx, out);
+}
+
+hopf_status sum_impl(hopf_ctx* ctx, int nterms, const hopf_tt* const* terms, const double* coef,
+                     hopf_tt* out) {
+  const int d = out->d, n = out->n;
+  if (nterms < 1 || nterms > 16) return fail(ctx, HOPF_EINVAL, "tt_sum takes 1..16 terms");
+  std::vector<int> r(d + 1, 1);
+  for (int t = 0; t < nterms; ++t) {
+    if (!terms[t] || terms[t]->d != d || terms[t]->n != n) return fail(ctx, HOPF_EINVAL, "tt_sum: term %d has another shape", t);
+    if (terms[t] == out) return fail(ctx, HOPF_EINVAL, "tt_sum: output aliases term %d", t);
+  }
+  for (int k = 1; k < d; ++k) {
+    int s = 0;
+    for (int t = 0; t < nterms; ++t) s += terms[t]->ranks[k];
+    r[k] = s;
+  }
+  TRY(check_fit(ctx, out, r));
+  std::vector<hk::SumTerm> host((size_t)nterms * d);
+  for (int k = 0; k < d; ++k)
+    for (int t = 0; t < nterms; ++t) {
+      hk::SumTerm& s = host[(size_t)k * nterms + t];
+      s.p = terms[t]->cores[k];
+      s.ra = terms[t]->ranks[k];
+      s.rc = terms[t]->ranks[k + 1];
+      s.coef = cplx{coef[2 * t], coef[2 * t + 1]};
+    }
+  // pageable source: the copy is staged before the call returns, and stream
+  // order keeps earlier sums' kernels ahead of this overwrite
+  hk::SumTerm* dt = ctx->d_terms;
+  CK(cudaMemcpyAsync(dt, host.data(), host.size() * sizeof(hk::SumTerm), cudaMemcpyHostToDevice, ctx->stream));
+  for (int k = 0; k < d; ++k) {
+    const int kind = (k == 0) ? 0 : (k == d - 1 ? 2 : 1);
+    double in_elems = 0.0;
+    for (int t = 0; t < nterms; ++t) in_elems += (double)terms[t]->ranks[k] * n * terms[t]->ranks[k + 1];
+    LAUNCH(HOPF_K_SUM, 0, 16.0 * (in_elems + (double)r[k] * n * r[k + 1]), 1,
+           hk::sum_core(dt + (size_t)k * nterms, nterms, kind, n, out->cores[k], r[k], r[k + 1], ctx->stream));
+  }
+  out->ranks = r;
+  return sync_meta(ctx, out);
+}
+
+hopf_status copy_impl(hopf_ctx* ctx, const hopf_tt* src, hopf_tt* dst) {
+  TRY(check_fit(ctx, dst, src->ranks));
+  for (int k = 0; k < src->d; ++k)
+    CK(cudaMemcpyAsync(dst->cores[k], src->cores[k], core_elems(src, k) * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
+  dst->ranks = src->ranks;
+  return sync_meta(ctx, dst);
+}
+
+hopf_status ensure_step_ws(hopf_ctx* ctx, int cap) {
+  if (ctx->big && ctx->big->cap_rank >= 6 * cap && ctx->kst[0]->cap_rank >= cap) return HOPF_OK;
+  if (ctx->big) tt_free(ctx->big);
+  for (auto& k : ctx->kst)
+    if (k) tt_free(k);
+  if (ctx->ytmp) tt_free(ctx->ytmp);
+  ctx->big = ctx->ytmp = nullptr;
+  for (auto& k : ctx->kst) k = nullptr;
+  TRY(tt_alloc(ctx, 6 * cap, &ctx->big));
+  for (auto& k : ctx->kst) TRY(tt_alloc(ctx, cap, &k));
+  TRY(tt_alloc(ctx, cap, &ctx->ytmp));
+  return HOPF_OK;
+}
+
+std::vector<double> gauss_legendre01(int q) {
+  // nodes by Newton's method on P_q, then mapped to [0, 1]
+  std::vector<double> out(2 * q);
+  for (int i = 0; i < q; ++i) {
+    double x = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= q; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = q * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= q; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = q * (x * p1 - p0) / (x * x - 1.0);
+    out[i] = 0.5 * (x + 1.0);
+    out[q + i] = 1.0 / ((1.0 - x * x) * dp * dp);  // weight on [-1,1] halved
+  }
+  return out;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out) {
+  if (!p || !out) return HOPF_EINVAL;
+  *out = nullptr;
+  if (p->d < 3 || p->d > 64 || p->n < 4 || (p->n & 1) || p->rank_cap < 1 || !(p->tol >= 0.0) ||
+      p->precision != HOPF_FP64 || !(p->nu >= 0.0))
+    return HOPF_EINVAL;
+  hopf_ctx* ctx = new (std::nothrow) hopf_ctx();
+  if (!ctx) return HOPF_ENOMEM;
+  ctx->p = *p;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->L = p->L;
+  auto bad = [&](hopf_status st) {
+    hopf_destroy(ctx);
+    return st;
+  };
+  if (dalloc(&ctx->d_coef, (size_t)15 * p->n) != cudaSuccess || dalloc(&ctx->d_blocks, 3 * 36) != cudaSuccess ||
+      dalloc(&ctx->d_agrid, p->n) != cudaSuccess || dalloc(&ctx->d_dbl, 16) != cudaSuccess ||
+      dalloc(&ctx->d_int, 16) != cudaSuccess || dalloc(&ctx->coop.bar, 1) != cudaSuccess ||
+      dalloc(&ctx->coop.pr, 1024) != cudaSuccess || dalloc(&ctx->coop.scal, 8) != cudaSuccess ||
+      dalloc(&ctx->coop.counters, 64) != cudaSuccess || dalloc(&ctx->d_terms, 16 * 64) != cudaSuccess)
+    return bad(HOPF_ENOMEM);
+  if (cudaMallocHost((void**)&ctx->h_dbl, 16 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_int, 16 * sizeof(int)) != cudaSuccess)
+    return bad(HOPF_ENOMEM);
+  if (cudaMemsetAsync(ctx->coop.bar, 0, sizeof(GridBar), ctx->stream) != cudaSuccess) return bad(HOPF_ECUDA);
+  unsigned char tab[3][36];
+  mpo_tables(tab);
+  if (cudaMemcpyAsync(ctx->d_blocks, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    return bad(HOPF_ECUDA);
+  if (ctx->L > 0.0 && build_ops(ctx) != HOPF_OK) return bad(HOPF_ECUDA);
+  if (coop_reserve(ctx, 64) != HOPF_OK) return bad(HOPF_ENOMEM);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bad(HOPF_ECUDA);
+  *out = ctx;
+  return HOPF_OK;
+}
+
+void tt_free(hopf_tt* t) {
+  if (!t) return;
+  for (cplx* c : t->cores) cudaFree(c);
+  cudaFree(t->d_ptrs);
+  cudaFree(t->d_ranks);
+  delete t;
+}
+
+void hopf_destroy(hopf_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  tt_free(ctx->big);
+  for (auto k : ctx->kst) tt_free(k);
+  tt_free(ctx->ytmp);
+  RoundWs& w = ctx->rw;
+  for (cplx* b : w.B) cudaFree(b);
+  cudaFree(w.W1); cudaFree(w.tau); cudaFree(w.T); cudaFree(w.tau2); cudaFree(w.T2);
+  cudaFree(w.Rb); cudaFree(w.Mb); cudaFree(w.Jb); cudaFree(w.Ub); cudaFree(w.Sb);
+  cudaFree(w.sig); cudaFree(w.perm);
+  cudaFree(ctx->coop.bar); cudaFree(ctx->coop.pr); cudaFree(ctx->coop.pc);
+  cudaFree(ctx->coop.wfin); cudaFree(ctx->coop.scal); cudaFree(ctx->coop.counters);
+  cudaFree(ctx->d_coef); cudaFree(ctx->d_blocks); cudaFree(ctx->d_agrid);
+  cudaFree(ctx->d_dbl); cudaFree(ctx->d_int); cudaFree(ctx->d_terms);
+  for (void* p : ctx->extra) cudaFree(p);
+  for (auto e : ctx->prof_ev) cudaEventDestroy(e);
+  if (ctx->h_dbl) cudaFreeHost(ctx->h_dbl);
+  if (ctx->h_int) cudaFreeHost(ctx->h_int);
+  delete ctx;
+}
+
+const char* hopf_last_error(const hopf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+hopf_status hopf_set_L(hopf_ctx* ctx, double L) {
+  if (!ctx) return HOPF_EINVAL;
+  if (!(L > 0.0) || !std::isfinite(L)) return fail(ctx, HOPF_EINVAL, "L must be positive");
+  ctx->L = L;
+  return build_ops(ctx);
+}
+
+hopf_status hopf_get_L(const hopf_ctx* ctx, double* L) {
+  if (!ctx || !L) return HOPF_EINVAL;
+  *L = ctx->L;
+  return HOPF_OK;
+}
+
+hopf_status hopf_cell_moments(hopf_ctx* ctx, int nmodes, const double* alpha, const double* beta,
+                              double sigma, double ell, double* m0, double* C0) {
+  if (!ctx) return HOPF_EINVAL;
+  if (nmodes < 0 || nmodes > 64 || (nmodes && (!alpha || !beta)) || !m0 || !C0 || !(ell > 0.0) || !(sigma >= 0.0))
+    return fail(ctx, HOPF_EINVAL, "hopf_cell_moments: bad arguments");
+  const int d = ctx->p.d, q = 12;
+  std::vector<double> host(2 * 64 + 2 * q, 0.0);
+  for (int i = 0; i < nmodes; ++i) {
+    host[i] = alpha[i];
+    host[64 + i] = beta[i];
+  }
+  const std::vector<double> gl = gauss_legendre01(q);
+  std::copy(gl.begin(), gl.end(), host.begin() + 128);
+  double* dbuf = nullptr;
+  CK(dalloc(&dbuf, host.size() + d + (size_t)d * d));
+  CK(cudaMemcpyAsync(dbuf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  double* dm0 = dbuf + host.size();
+  double* dC0 = dm0 + d;
+  cudaError_t e = hk::cell_moments(d, nmodes, dbuf, dbuf + 64, sigma, ell, dbuf + 128, q, dm0, dC0, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m0, dm0, d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(C0, dC0, (size_t)d * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dbuf);
+  if (e != cudaSuccess) return fail(ctx, HOPF_ECUDA, "hopf_cell_moments: %s", cudaGetErrorString(e));
+  for (int j = 0; j < d; ++j)
+    for (int k = j + 1; k < d; ++k) {
+      const double s = 0.5 * (C0[j + d * k] + C0[k + d * j]);
+      C0[j + d * k] = C0[k + d * j] = s;
+    }
+  return HOPF_OK;
+}
+
+hopf_status tt_create(hopf_ctx* ctx, int max_rank, hopf_tt** out) {
+  if (!ctx || !out || max_rank < 1) return ctx ? fail(ctx, HOPF_EINVAL, "tt_create: bad arguments") : HOPF_EINVAL;
+  TRY(tt_alloc(ctx, max_rank, out));
+  hopf_tt* t = *out;
+  for (int k = 0; k < t->d; ++k) CK(cudaMemsetAsync(t->cores[k], 0, t->core_cap[k] * sizeof(cplx), ctx->stream));
+  return sync_meta(ctx, t);
+}
+
+hopf_status tt_from_host(hopf_ctx* ctx, const int* ranks, const double* cores, int max_rank, hopf_tt** out) {
+  if (!ctx || !ranks || !cores || !out) return ctx ? fail(ctx, HOPF_EINVAL, "tt_from_host: null argument") : HOPF_EINVAL;
+  const int d = ctx->p.d, n = ctx->p.n;
+  if (ranks[0] != 1 || ranks[d] != 1) return fail(ctx, HOPF_EINVAL, "boundary ranks must be 1");
+  for (int k = 0; k <= d; ++k)
+    if (ranks[k] < 1 || ranks[k] > max_rank) return fail(ctx, HOPF_EINVAL, "rank %d = %d outside [1, max_rank=%d]", k, ranks[k], max_rank);
+  hopf_tt* t = nullptr;
+  TRY(tt_alloc(ctx, max_rank, &t));
+  size_t off = 0;
+  for (int k = 0; k < d; ++k) {
+    const size_t ne = (size_t)ranks[k] * n * ranks[k + 1];
+    cudaError_t e = cudaMemcpyAsync(t->cores[k], cores + 2 * off, ne * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+      tt_free(t);
+      return fail(ctx, HOPF_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    off += ne;
+  }
+  t->ranks.assign(ranks, ranks + d + 1);
+  hopf_status st = sync_meta(ctx, t);
+  if (st == HOPF_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, HOPF_ECUDA, "upload failed");
+  if (st != HOPF_OK) {
+    tt_free(t);
+    return st;
+  }
+  *out = t;
+  return HOPF_OK;
+}
+
+hopf_status tt_get_ranks(const hopf_tt* t, int* ranks) {
+  if (!t || !ranks) return HOPF_EINVAL;
+  std::copy(t->ranks.begin(), t->ranks.end(), ranks);
+  return HOPF_OK;
+}
+
+hopf_status tt_size(const hopf_tt* t, size_t* nd) {
+  if (!t || !nd) return HOPF_EINVAL;
+  size_t s = 0;
+  for (int k = 0; k < t->d; ++k) s += core_elems(t, k);
+  *nd = 2 * s;
+  return HOPF_OK;
+}
+
+hopf_status tt_to_host(const hopf_tt* t, double* cores, size_t cap_doubles) {
+  if (!t || !cores) return HOPF_EINVAL;
+  hopf_ctx* ctx = t->ctx;
+  size_t need = 0;
+  tt_size(t, &need);
+  if (cap_doubles < need) return fail(ctx, HOPF_EINVAL, "tt_to_host: buffer holds %zu doubles, %zu needed", cap_doubles, need);
+  size_t off = 0;
+  for (int k = 0; k < t->d; ++k) {
+    const size_t ne = core_elems(t, k);
+    CK(cudaMemcpyAsync(cores + 2 * off, t->cores[k], ne * sizeof(cplx), cudaMemcpyDeviceToHost, ctx->stream));
+    off += ne;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HOPF_OK;
+}
+
+hopf_status tt_copy(hopf_ctx* ctx, const hopf_tt* src, hopf_tt* dst) {
+  if (!ctx || !src || !dst) return ctx ? fail(ctx, HOPF_EINVAL, "tt_copy: null argument") : HOPF_EINVAL;
+  if (src == dst) return HOPF_OK;
+  return copy_impl(ctx, src, dst);
+}
+
+hopf_status hopf_apply_op(hopf_ctx* ctx, const hopf_tt* in, hopf_tt* out) {
+  if (!ctx || !in || !out || in == out) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_apply_op: bad arguments") : HOPF_EINVAL;
+  if (!(ctx->L > 0.0)) return fail(ctx, HOPF_EINVAL, "L is not set (hopf_set_L or hopf_init_gaussian)");
+  return apply_impl(ctx, in, out);
+}
+
+hopf_status tt_round(hopf_ctx* ctx, hopf_tt* t, double tol, int cap, const int* forced, double* disc) {
+  if (!ctx || !t) return ctx ? fail(ctx, HOPF_EINVAL, "tt_round: null argument") : HOPF_EINVAL;
+  if (!(tol >= 0.0) || cap < 1) return fail(ctx, HOPF_EINVAL, "tt_round: tol must be >= 0 and cap >= 1");
+  if (forced && (forced[0] != 1 || forced[t->d] != 1)) return fail(ctx, HOPF_EINVAL, "forced boundary ranks must be 1");
+  bool capped = false;
+  TRY(round_impl(ctx, t, tol, cap, forced, disc, &capped));
+  return capped ? HOPF_ERANKCAP : HOPF_OK;
+}
+
+hopf_status tt_sum(hopf_ctx* ctx, int nterms, const hopf_tt* const* terms, const double* coef, hopf_tt* out) {
+  if (!ctx || !terms || !coef || !out) return ctx ? fail(ctx, HOPF_EINVAL, "tt_sum: null argument") : HOPF_EINVAL;
+  return sum_impl(ctx, nterms, terms, coef, out);
+}
+
+hopf_status hopf_profile_enable(hopf_ctx* ctx, int on) {
+  if (!ctx) return HOPF_EINVAL;
+  if (on && ctx->prof_ev.empty()) {
+    ctx->prof_ev.resize(2 * kProfSlots);
+    for (auto& e : ctx->prof_ev) CK(cudaEventCreate(&e));
+  }
+  if (!on) TRY(prof_flush(ctx));
+  ctx->prof_on = on != 0;
+  return HOPF_OK;
+}
+
+hopf_status hopf_profile_read(hopf_ctx* ctx, hopf_profile* out, int reset) {
+  if (!ctx || !out) return HOPF_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(prof_flush(ctx));
+  *out = ctx->prof;
+  if (reset) ctx->prof = hopf_profile{};
+  return HOPF_OK;
+}
+
+hopf_status tt_set_from_host(hopf_tt* t, const int* ranks, const double* cores) {
+  if (!t || !ranks || !cores) return HOPF_EINVAL;
+  hopf_ctx* ctx = t->ctx;
+  const int d = t->d, n = t->n;
+  std::vector<int> r(ranks, ranks + d + 1);
+  if (r[0] != 1 || r[d] != 1) return fail(ctx, HOPF_EINVAL, "boundary ranks must be 1");
+  for (int k = 0; k <= d; ++k)
+    if (r[k] < 1) return fail(ctx, HOPF_EINVAL, "rank %d = %d < 1", k, r[k]);
+  TRY(check_fit(ctx, t, r));
+  size_t off = 0;
+  for (int k = 0; k < d; ++k) {
+    const size_t ne = (size_t)r[k] * n * r[k + 1];
+    CK(cudaMemcpyAsync(t->cores[k], cores + 2 * off, ne * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream));
+    off += ne;
+  }
+  t->ranks = r;
+  return sync_meta(ctx, t);
+}
+
+hopf_status tt_norm(hopf_ctx* ctx, const hopf_tt* t, double* norm) {
+  if (!ctx || !t || !norm) return ctx ? fail(ctx, HOPF_EINVAL, "tt_norm: null argument") : HOPF_EINVAL;
+  TRY(round_reserve(ctx, t));
+  std::vector<int> p, nbv;
+  TRY(orth_sweep(ctx, t, p, nbv));
+  TRY(read_small(ctx, 0, 1));
+  TRY(check_barrier(ctx));
+  *norm = std::sqrt(ctx->h_dbl[0]);
+  return HOPF_OK;
+}
+
+hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* f, double dt, int nsteps, double* disc_sum, int* rank_log,
+                      const int* forced_log) {
+  if (!ctx || !f) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_step: null argument") : HOPF_EINVAL;
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(ctx, HOPF_EINVAL, "hopf_step: bad dt or nsteps");
+  if (!(ctx->L > 0.0)) return fail(ctx, HOPF_EINVAL, "L is not set (hopf_set_L or hopf_init_gaussian)");
+  const int cap = ctx->p.rank_cap;
+  const double tol = ctx->p.tol;
+  if (f->cap_rank < cap) return fail(ctx, HOPF_EINVAL, "hopf_step: the state needs capacity >= rank_cap");
+  for (int k = 0; k <= f->d; ++k)
+    if (f->ranks[k] > cap) return fail(ctx, HOPF_EINVAL, "hopf_step: input rank %d exceeds rank_cap", f->ranks[k]);
+  TRY(ensure_step_ws(ctx, cap));
+  hopf_tt* big = ctx->big;
+  hopf_tt** K = ctx->kst;
+  hopf_tt* Y = ctx->ytmp;
+  const int d = f->d;
+  double dsum = 0.0;
+  bool capped = false;
+  int round_idx = 0;
+  auto T = [&](hopf_tt* x, hopf_tt* dst) -> hopf_status {
+    const int* forced = forced_log ? forced_log + (size_t)round_idx * (d + 1) : nullptr;
+    double disc = 0.0;
+    bool c = false;
+    TRY(round_impl(ctx, x, tol, cap, forced, &disc, &c));
+    capped |= c;
+    dsum += disc;
+    if (rank_log) std::copy(x->ranks.begin(), x->ranks.end(), rank_log + (size_t)round_idx * (d + 1));
+    ++round_idx;
+    return copy_impl(ctx, x, dst);
+  };
+  for (int s = 0; s < nsteps; ++s) {
+    const hopf_tt* tm[5];
+    double cf[10] = {0};
+    // K1 = T[G f]
+    TRY(apply_impl(ctx, f, big));
+    TRY(T(big, K[0]));
+    // Y2 = T[f + dt/2 K1]; K2 = T[G Y2]
+    tm[0] = f; tm[1] = K[0]; cf[0] = 1.0; cf[2] = 0.5 * dt;
+    TRY(sum_impl(ctx, 2, tm, cf, big));
+    TRY(T(big, Y));
+    TRY(apply_impl(ctx, Y, big));
+    TRY(T(big, K[1]));
+    // Y3 = T[f + dt/2 K2]; K3 = T[G Y3]
+    tm[1] = K[1];
+    TRY(sum_impl(ctx, 2, tm, cf, big));
+    TRY(T(big, Y));
+    TRY(apply_impl(ctx, Y, big));
+    TRY(T(big, K[2]));
+    // Y4 = T[f + dt K3]; K4 = T[G Y4]
+    tm[1] = K[2]; cf[2] = dt;
+    TRY(sum_impl(ctx, 2, tm, cf, big));
+    TRY(T(big, Y));
+    TRY(apply_impl(ctx, Y, big));
+    TRY(T(big, K[3]));
+    // f <- T[f + dt/6 (K1 + 2 K2 + 2 K3 + K4)]
+    tm[0] = f; tm[1] = K[0]; tm[2] = K[1]; tm[3] = K[2]; tm[4] = K[3];
+    cf[0] = 1.0; cf[2] = dt / 6.0; cf[4] = dt / 3.0; cf[6] = dt / 3.0; cf[8] = dt / 6.0;
+    TRY(sum_impl(ctx, 5, tm, cf, big));
+    TRY(T(big, f));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (disc_sum) *disc_sum = dsum;
+  return capped ? HOPF_ERANKCAP : HOPF_OK;
+}
+
+hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts, const int* idx, double* vals) {
+  if (!ctx || !t || (npts > 0 && (!idx || !vals)) || npts < 0)
+    return ctx ? fail(ctx, HOPF_EINVAL, "hopf_eval_points: bad arguments") : HOPF_EINVAL;
+  if (npts == 0) return HOPF_OK;
+  const int d = t->d, n = t->n;
+  for (size_t e = 0; e < (size_t)npts * d; ++e)
+    if (idx[e] < 0 || idx[e] >= n) return fail(ctx, HOPF_EINVAL, "index %d outside [0, %d)", idx[e], n);
+  int maxr = 1;
+  for (int r : t->ranks) maxr = std::max(maxr, r);
+  int* didx = nullptr;
+  cplx* dv = nullptr;
+  CK(dalloc(&didx, (size_t)npts * d));
+  cudaError_t e = dalloc(&dv, (size_t)npts);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(didx, idx, (size_t)npts * d * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = hk::eval_points(t->d_ptrs, t->d_ranks, d, n, maxr, npts, didx, dv, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(vals, dv, (size_t)npts * sizeof(cplx), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(didx);
+  cudaFree(dv);
+  if (e != cudaSuccess) return fail(ctx, HOPF_ECUDA, "hopf_eval_points: %s", cudaGetErrorString(e));
+  return HOPF_OK;
+}
+
+hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean, double* cov, double* imag_resid) {
+  if (!ctx || !t || !mean || !cov) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_eval_moments: null argument") : HOPF_EINVAL;
+  if (!(ctx->L > 0.0)) return fail(ctx, HOPF_EINVAL, "L is not set");
+  const int d = t->d, n = t->n, c = n / 2;
+  const int npts = 1 + 2 * d + 2 * d * (d - 1);
+  std::vector<int> idx((size_t)npts * d, c);
+  auto at = [&](int pt, int ax, int off) { idx[(size_t)pt * d + ax] = c + off; };
+  int pt = 1;
+  for (int k = 0; k < d; ++k) {
+    at(pt, k, 1); ++pt;
+    at(pt, k, -1); ++pt;
+  }
+  for (int j = 0; j < d; ++j)
+    for (int k = j + 1; k < d; ++k) {
+      at(pt, j, 1); at(pt, k, 1); ++pt;
+      at(pt, j, 1); at(pt, k, -1); ++pt;
+      at(pt, j, -1); at(pt, k, 1); ++pt;
+      at(pt, j, -1); at(pt, k, -1); ++pt;
+    }
+  int maxr = 1;
+  for (int r : t->ranks) maxr = std::max(maxr, r);
+  int* didx = nullptr;
+  cplx* dv = nullptr;
+  double* dout = nullptr;
+  CK(dalloc(&didx, idx.size()));
+  cudaError_t e = dalloc(&dv, (size_t)npts);
+  if (e == cudaSuccess) e = dalloc(&dout, (size_t)d + (size_t)d * d + 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = hk::eval_points(t->d_ptrs, t->d_ranks, d, n, maxr, npts, didx, dv, ctx->stream);
+  const double da = 2.0 * ctx->L / n;
+  if (e == cudaSuccess) e = hk::moments_combine(dv, d, da, dout, dout + d, dout + d + (size_t)d * d, ctx->stream);
+  double ir = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mean, dout, d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cov, dout + d, (size_t)d * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ir, dout + d + (size_t)d * d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(didx);
+  cudaFree(dv);
+  cudaFree(dout);
+  if (e != cudaSuccess) return fail(ctx, HOPF_ECUDA, "hopf_eval_moments: %s", cudaGetErrorString(e));
+  if (imag_resid) *imag_resid = ir;
+  return HOPF_OK;
+}
+
+hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0, const double* C0, hopf_tt** out) {
+  if (!ctx || !m0 || !C0 || !out) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_init_gaussian: null argument") : HOPF_EINVAL;
+  const int d = ctx->p.d, n = ctx->p.n;
+  bool diag = true;
+  double minc = 1e300;
+  for (int j = 0; j < d; ++j) {
+    minc = std::min(minc, C0[j + d * j]);
+    for (int k = 0; k < d; ++k)
+      if (j != k && C0[j + d * k] != 0.0) diag = false;
+  }
+  if (!(minc > 0.0)) return fail(ctx, HOPF_EINVAL, "C0 needs a positive diagonal");
+  if (!(ctx->L > 0.0)) {
+    ctx->L = std::sqrt(36.8 / minc);
+    TRY(build_ops(ctx));
+  }
+  const int cap = ctx->p.rank_cap;
+  if (diag) {
+    hopf_tt* t = nullptr;
+    TRY(tt_create(ctx, cap, &t));
+    for (int k = 0; k < d; ++k) {
+      cudaError_t e = hk::gauss_rank1_core(ctx->d_agrid, n, m0[k], C0[k + d * k], t->cores[k], ctx->stream);
+      if (e != cudaSuccess) {
+        tt_free(t);
+        return fail(ctx, HOPF_ECUDA, "%s", cudaGetErrorString(e));
+      }
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+      tt_free(t);
+      return fail(ctx, HOPF_ECUDA, "init failed");
+    }
+    *out = t;
+    return HOPF_OK;
+  }
+  // exact TT of the full grid: identity cores around one data core, then round
+  const int c = (d - 1) / 2;
+  double total = 1.0;
+  for (int k = 0; k < d; ++k) total *= n;
+  if (total > (double)(1 << 26))
+    return fail(ctx, HOPF_EINVAL, "correlated Gaussian initial state needs n^d <= 2^26 (got %g)", total);
+  size_t A = 1, B = 1;
+  for (int k = 0; k < c; ++k) A *= n;
+  for (int k = c + 1; k < d; ++k) B *= n;
+  const int capr = (int)std::max(A, B);
+  hopf_tt* full = nullptr;
+  TRY(tt_alloc(ctx, capr, &full));
+  std::vector<int> r(d + 1, 1);
+  {
+    size_t a = 1;
+    for (int k = 0; k < c; ++k) {
+      r[k] = (int)a;
+      a *= n;
+    }
+    r[c] = (int)A;
+    r[c + 1] = (int)B;
+    size_t b = B;
+    for (int k = c + 1; k < d; ++k) {
+      r[k] = (int)b;
+      b /= n;
+    }
+    r[d] = 1;
+  }
+  double* dmc = nullptr;
+  hopf_status st = HOPF_OK;
+  cudaError_t e = dalloc(&dmc, (size_t)d + (size_t)d * d);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dmc, m0, d * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dmc + d, C0, (size_t)d * d * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  for (int k = 0; k < d && e == cudaSuccess; ++k) {
+    if (k < c) e = hk::identity_core(n, r[k], r[k + 1], 1, full->cores[k], ctx->stream);
+    else if (k == c) e = hk::gauss_full_core(ctx->d_agrid, n, d, c, dmc, dmc + d, full->cores[k], ctx->stream);
+    else e = hk::identity_core(n, r[k], r[k + 1], 0, full->cores[k], ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dmc);
+  if (e != cudaSuccess) st = fail(ctx, HOPF_ECUDA, "init: %s", cudaGetErrorString(e));
+  if (st == HOPF_OK) {
+    full->ranks = r;
+    st = sync_meta(ctx, full);
+  }
+  bool capped = false;
+  if (st == HOPF_OK) st = round_impl(ctx, full, ctx->p.tol, cap, nullptr, nullptr, &capped);
+  hopf_tt* t = nullptr;
+  if (st == HOPF_OK) st = tt_alloc(ctx, cap, &t);
+  if (st == HOPF_OK) st = copy_impl(ctx, full, t);
+  if (st == HOPF_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, HOPF_ECUDA, "init sync failed");
+  tt_free(full);
+  if (st != HOPF_OK) {
+    tt_free(t);
+    return st;
+  }
+  *out = t;
+  return capped ? HOPF_ERANKCAP : HOPF_OK;
+}
+
+}  // extern "C"

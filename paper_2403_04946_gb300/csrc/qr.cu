@@ -1,0 +1,409 @@
+// Householder QR (geqrf) and application of its Q (ormqr) for tall complex
+// float64 matrices, as cooperative persistent kernels.
+//
+// The rounding sweep (App. A, Alg. 1 mirrored and Alg. 4) factors one
+// flattening per core, (n r) x K with K = 6 r after the operator apply.
+// FP64 throughput on this part is a few FLOP per clock per SM, so every panel
+// is spread over all SMs: CTA g owns a contiguous block of rows, keeps its
+// rows of the current panel in shared memory, and the CTAs meet at bounded
+// grid barriers for the column reductions (two per column) and the blocked
+// trailing update (three per panel of width nb).  Reductions over CTAs are
+// done in a fixed order, so results are bitwise reproducible.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace hk {
+
+constexpr int kQrThreads = 256;
+constexpr int kNbMax = 32;
+
+struct QrSmem {
+  // sizes in cplx
+  static size_t bytes(int R, int nb) {
+    return sizeof(cplx) * ((size_t)nb * R + (size_t)nb * nb + 2 * kNbMax + 32) + 256;
+  }
+};
+
+// v_s(i) for the panel held in P (after fix-up P holds pure V: zeros above
+// the unit diagonal).
+__device__ __forceinline__ cplx ld_cg(const cplx* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+
+// Partial products V^H X over this CTA's rows [lo, hi) (global row index),
+// V in shared memory (P, leading dimension R, rows offset r0), X column l
+// given by a pointer.  One warp per column; results to out[s + nbk * l].
+template <int NB>
+__device__ void partial_vhx(const cplx* P, int R, int r0, int lo, int hi, int nbk,
+                            const cplx* X, int ldx, int ncol, cplx* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = w; l < ncol; l += nw) {
+    cplx acc[NB];
+#pragma unroll
+    for (int s = 0; s < NB; ++s) acc[s] = mk(0, 0);
+    const cplx* x = X + (size_t)ldx * l;
+    for (int i = lo + lane; i < hi; i += 32) {
+      const cplx xi = x[i];
+      const cplx* pv = P + (i - r0);
+#pragma unroll
+      for (int s = 0; s < NB; ++s)
+        if (s < nbk) acc[s] = cfmac(pv[(size_t)s * R], xi, acc[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < NB; ++s) {
+      if (s < nbk) {
+        cplx v = warp_sum(acc[s]);
+        if (lane == 0) out[s + (size_t)nbk * l] = v;
+      }
+    }
+  }
+}
+
+// X[:, l] -= V * W2[:, l] over this CTA's rows [lo, hi); W2 column l at
+// w2 + nbk * l.
+template <int NB>
+__device__ void update_x(const cplx* P, int R, int r0, int lo, int hi, int nbk, cplx* X,
+                         int ldx, int ncol, const cplx* w2) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = w; l < ncol; l += nw) {
+    cplx wc[NB];
+#pragma unroll
+    for (int s = 0; s < NB; ++s) wc[s] = (s < nbk) ? ld_cg(w2 + s + (size_t)nbk * l) : mk(0, 0);
+    cplx* x = X + (size_t)ldx * l;
+    for (int i = lo + lane; i < hi; i += 32) {
+      cplx acc = x[i];
+      const cplx* pv = P + (i - r0);
+#pragma unroll
+      for (int s = 0; s < NB; ++s)
+        if (s < nbk) acc = csub(acc, cmul(pv[(size_t)s * R], wc[s]));
+      x[i] = acc;
+    }
+  }
+}
+
+// Sum over the G per-CTA partials of entry e (stride pstride) by one warp.
+__device__ __forceinline__ cplx reduce_partials(const cplx* pc, size_t pstride, int G, size_t e) {
+  const int lane = threadIdx.x & 31;
+  cplx acc = mk(0, 0);
+  for (int g = lane; g < G; g += 32) acc = cadd(acc, ld_cg(pc + (size_t)g * pstride + e));
+  return warp_sum(acc);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kQrThreads, 1)
+geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
+             CoopWs ws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx* P = reinterpret_cast<cplx*>(smem_raw);
+  cplx* Ts = P + (size_t)nb * R;
+  cplx* wl = Ts + (size_t)nb * nb;  // [2*kNbMax]
+  cplx* red = wl + 2 * kNbMax;      // [32]
+  __shared__ double dred[32];
+  __shared__ cplx bc[4];
+
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int r0 = g * R, r1 = min(m, r0 + R);
+  const int p = min(m, k);
+  const size_t pstride = ws.pc_elems / G;
+
+  for (int j0 = 0, panel = 0; j0 < p; j0 += nb, ++panel) {
+    const int nbk = min(nb, p - j0);
+    const int lo = max(r0, j0);  // rows of this CTA that the panel touches
+    // load panel rows [r0, r1) of columns j0..j0+nbk-1
+    for (int t = 0; t < nbk; ++t)
+      for (int i = r0 + tid; i < r1; i += blockDim.x) P[(size_t)t * R + (i - r0)] = A[i + (size_t)lda * (j0 + t)];
+    __syncthreads();
+
+    for (int t = 0; t < nbk; ++t) {
+      const int jj = j0 + t;
+      cplx* pt = P + (size_t)t * R;
+      // (1) partial squared norm of rows > jj
+      double sq = 0.0;
+      for (int i = max(lo, jj + 1) + tid; i < r1; i += blockDim.x) sq += cabs2(pt[i - r0]);
+      sq = block_sum(sq, dred);
+      if (tid == 0) {
+        ws.pr[g] = sq;
+        if (jj >= r0 && jj < r1) ws.scal[0] = pt[jj - r0];
+      }
+      grid_sync(ws.bar);
+      if (grid_failed(ws.bar)) return;
+      // (2) Householder vector (zlarfg conventions: beta real, v_jj = 1)
+      if (wid == 0) {
+        double s2 = 0.0;
+        for (int gg = lane; gg < G; gg += 32) s2 += ld_cg(ws.pr + gg);
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+          const cplx al = ld_cg(ws.scal);
+          cplx tu, sc;
+          double beta;
+          if (s2 == 0.0 && al.y == 0.0) {
+            tu = mk(0, 0);
+            beta = al.x;
+            sc = mk(0, 0);
+          } else {
+            const double an = sqrt(al.x * al.x + al.y * al.y + s2);
+            beta = (al.x >= 0.0) ? -an : an;
+            tu = mk((beta - al.x) / beta, -al.y / beta);
+            sc = cinv(mk(al.x - beta, al.y));
+          }
+          bc[0] = tu;
+          bc[1] = sc;
+          bc[2] = mk(beta, 0.0);
+        }
+      }
+      __syncthreads();
+      const cplx tu = bc[0], sc = bc[1];
+      for (int i = max(lo, jj + 1) + tid; i < r1; i += blockDim.x) pt[i - r0] = cmul(pt[i - r0], sc);
+      if (tid == 0) {
+        if (jj >= r0 && jj < r1) pt[jj - r0] = bc[2];
+        if (g == 0) tau[jj] = tu;
+      }
+      __syncthreads();
+      // (3) apply H^H = I - conj(tau) v v^H to panel columns t+1..nbk-1
+      const int nrem = nbk - t - 1;
+      if (nrem > 0) {
+        // v_jj = 1 is implicit: the stored diagonal holds beta.
+        for (int l = wid; l < nrem; l += nw) {
+          const cplx* pl = P + (size_t)(t + 1 + l) * R;
+          cplx acc = mk(0, 0);
+          for (int i = max(lo, jj) + lane; i < r1; i += 32) {
+            const cplx vi = (i == jj) ? mk(1, 0) : pt[i - r0];
+            acc = cfmac(vi, pl[i - r0], acc);
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) ws.pc[(size_t)g * pstride + l] = acc;
+        }
+        grid_sync(ws.bar);
+        if (grid_failed(ws.bar)) return;
+        for (int l = wid; l < nrem; l += nw) {
+          cplx sum = reduce_partials(ws.pc, pstride, G, l);
+          if (lane == 0) wl[l] = cmul(cconj(tu), sum);
+        }
+        __syncthreads();
+        for (int l = 0; l < nrem; ++l) {
+          cplx* pl = P + (size_t)(t + 1 + l) * R;
+          const cplx f = wl[l];
+          for (int i = max(lo, jj) + tid; i < r1; i += blockDim.x) {
+            const cplx vi = (i == jj) ? mk(1, 0) : pt[i - r0];
+            pl[i - r0] = csub(pl[i - r0], cmul(vi, f));
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // write the factored panel back (R on/above the diagonal, V below)
+    for (int t = 0; t < nbk; ++t)
+      for (int i = r0 + tid; i < r1; i += blockDim.x) A[i + (size_t)lda * (j0 + t)] = P[(size_t)t * R + (i - r0)];
+    __syncthreads();
+    // fix up P to hold pure reflectors: zero above, one on the diagonal
+    for (int t = 0; t < nbk; ++t)
+      for (int i = r0 + tid; i < r1; i += blockDim.x) {
+        const int gi = i;
+        if (gi < j0 + t) P[(size_t)t * R + (i - r0)] = mk(0, 0);
+        else if (gi == j0 + t) P[(size_t)t * R + (i - r0)] = mk(1, 0);
+      }
+    __syncthreads();
+
+    // S1: partials of V^H [V | A_trail]
+    const int c0 = j0 + nbk;
+    const int nt = k - c0;
+    const int ncol = nbk + nt;
+    {
+      cplx* out = ws.pc + (size_t)g * pstride;
+      // Gram block: columns are the reflectors themselves (from shared memory)
+      for (int l = wid; l < nbk; l += nw) {
+        cplx acc[NB];
+#pragma unroll
+        for (int s = 0; s < NB; ++s) acc[s] = mk(0, 0);
+        for (int i = lo + lane; i < r1; i += 32) {
+          const cplx xi = P[(size_t)l * R + (i - r0)];
+#pragma unroll
+          for (int s = 0; s < NB; ++s)
+            if (s < nbk) acc[s] = cfmac(P[(size_t)s * R + (i - r0)], xi, acc[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+          if (s < nbk) {
+            cplx v = warp_sum(acc[s]);
+            if (lane == 0) out[s + (size_t)nbk * l] = v;
+          }
+      }
+      if (nt > 0)
+        partial_vhx<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, out + (size_t)nbk * nbk);
+    }
+    grid_sync(ws.bar);
+    if (grid_failed(ws.bar)) return;
+    // S2: reduce columns l % G == g into wfin
+    for (int l = g; l < ncol; l += G) {
+      for (int s = wid; s < nbk; s += nw) {
+        cplx v = reduce_partials(ws.pc, pstride, G, s + (size_t)nbk * l);
+        if (lane == 0) ws.wfin[s + (size_t)nbk * l] = v;
+      }
+    }
+    grid_sync(ws.bar);
+    if (grid_failed(ws.bar)) return;
+    // S3: T from the reflector Gram (zlarft, forward, columnwise), then
+    // W2 = T^H W for the trailing columns this CTA reduced.
+    // The build below is a serial recurrence over the panel's columns; each
+    // Gram column is loaded once per lane and broadcast by shuffles, so no L2
+    // latency sits inside the recurrence.
+    for (int e = tid; e < nbk * nbk; e += blockDim.x) Ts[e] = mk(0, 0);
+    __syncthreads();
+    if (wid == 0) {
+      for (int i = 0; i < nbk; ++i) {
+        const cplx ti = ld_cg(tau + j0 + i);
+        // Gram column i held by lanes: g_l = v_l^H v_i for l = lane
+        const cplx gcol = (lane < i) ? ld_cg(ws.wfin + lane + (size_t)nbk * i) : mk(0, 0);
+        // T[0:i, i] = -tau_i * T[0:i, 0:i] * Gram[0:i, i]
+        cplx y = mk(0, 0);
+        for (int l = 0; l < i; ++l) {
+          const cplx gl = make_double2(__shfl_sync(0xffffffffu, gcol.x, l), __shfl_sync(0xffffffffu, gcol.y, l));
+          if (lane <= l) y = cfma(Ts[lane + nbk * l], gl, y);
+        }
+        __syncwarp();
+        if (lane < i) Ts[lane + nbk * i] = cmul(mk(-ti.x, -ti.y), y);
+        if (lane == 0) Ts[i + nbk * i] = ti;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (g == 0)
+      for (int e = tid; e < nbk * nbk; e += blockDim.x) Tg[(size_t)panel * nb * nb + e] = Ts[e];
+    for (int l = nbk + g; l < ncol; l += G) {
+      // W2[s] = sum_{u <= s} conj(T[u, s]) W[u]
+      if (wid == 0) {
+        cplx wv = mk(0, 0);
+        if (lane < nbk) wv = ld_cg(ws.wfin + lane + (size_t)nbk * l);
+        cplx acc = mk(0, 0);
+        for (int u = 0; u < nbk; ++u) {
+          const cplx wu = make_double2(__shfl_sync(0xffffffffu, wv.x, u), __shfl_sync(0xffffffffu, wv.y, u));
+          if (lane < nbk && u <= lane) acc = cfmac(Ts[u + nbk * lane], wu, acc);
+        }
+        if (lane < nbk) ws.wfin[lane + (size_t)nbk * l] = acc;
+      }
+    }
+    grid_sync(ws.bar);
+    if (grid_failed(ws.bar)) return;
+    // S4: trailing update over this CTA's rows
+    if (nt > 0) update_x<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, ws.wfin + (size_t)nbk * nbk);
+    __syncthreads();
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kQrThreads, 1)
+ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx* C, int ldc,
+             int q, int R, CoopWs ws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx* P = reinterpret_cast<cplx*>(smem_raw);
+  cplx* Ts = P + (size_t)nb * R;
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int r0 = g * R, r1 = min(m, r0 + R);
+  const size_t pstride = ws.pc_elems / G;
+  const int npanel = (p + nb - 1) / nb;
+  for (int panel = npanel - 1; panel >= 0; --panel) {
+    const int j0 = panel * nb;
+    const int nbk = min(nb, p - j0);
+    const int lo = max(r0, j0);
+    for (int t = 0; t < nbk; ++t)
+      for (int i = r0 + tid; i < r1; i += blockDim.x) {
+        cplx v;
+        if (i < j0 + t) v = mk(0, 0);
+        else if (i == j0 + t) v = mk(1, 0);
+        else v = A[i + (size_t)lda * (j0 + t)];
+        P[(size_t)t * R + (i - r0)] = v;
+      }
+    // T of a panel is stored packed (leading dimension nbk).
+    for (int e = tid; e < nbk * nbk; e += blockDim.x) Ts[e] = Tg[(size_t)panel * nb * nb + e];
+    __syncthreads();
+    partial_vhx<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
+    grid_sync(ws.bar);
+    if (grid_failed(ws.bar)) return;
+    // reduce and multiply by T: W2 = T W (apply Q, not Q^H)
+    for (int l = g; l < q; l += G) {
+      for (int s = wid; s < nbk; s += nw) {
+        cplx v = reduce_partials(ws.pc, pstride, G, s + (size_t)nbk * l);
+        if (lane == 0) ws.wfin[s + (size_t)nbk * l] = v;
+      }
+      __syncthreads();
+      if (wid == 0) {
+        // W2[s] = sum_{u >= s} T[s, u] W[u]; W held by lanes, broadcast by shuffles
+        const cplx wv = (lane < nbk) ? ws.wfin[lane + (size_t)nbk * l] : mk(0, 0);
+        cplx acc = mk(0, 0);
+        for (int u = 0; u < nbk; ++u) {
+          const cplx wu = make_double2(__shfl_sync(0xffffffffu, wv.x, u), __shfl_sync(0xffffffffu, wv.y, u));
+          if (lane < nbk && u >= lane) acc = cfma(Ts[lane + nbk * u], wu, acc);
+        }
+        if (lane < nbk) ws.wfin[lane + (size_t)nbk * l] = acc;
+      }
+      __syncthreads();
+    }
+    grid_sync(ws.bar);
+    if (grid_failed(ws.bar)) return;
+    update_x<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.wfin);
+    __syncthreads();
+    // No barrier needed here: the next panel writes wfin only after its
+    // first grid_sync, which every CTA reaches after finishing this update.
+  }
+}
+
+static void pick_layout(int m, int* G, int* R, int* nb, size_t* smem) {
+  const DevInfo& di = dev_info();
+  int g = std::max(1, std::min(di.sm_count, (m + 63) / 64));
+  int r = (m + g - 1) / g;
+  int b = kNbMax;
+  const size_t lim = (size_t)di.max_smem_optin - 4096;
+  while (b > 4 && QrSmem::bytes(r, b) > lim) b >>= 1;
+  *G = g;
+  *R = r;
+  *nb = b;
+  *smem = QrSmem::bytes(r, b);
+}
+
+cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_out,
+                  const CoopWs& ws, cudaStream_t s) {
+  if (m <= 0 || k <= 0) return cudaSuccess;
+  int G, R, nb;
+  size_t smem;
+  pick_layout(m, &G, &R, &nb, &smem);
+  if ((size_t)G * nb * (size_t)(nb + k) > ws.pc_elems || (size_t)nb * (nb + k) > ws.wfin_elems)
+    return cudaErrorInvalidValue;
+  *nb_out = nb;
+  void* fn;
+  if (nb == 32) fn = (void*)geqrf_kernel<32>;
+  else if (nb == 16) fn = (void*)geqrf_kernel<16>;
+  else fn = (void*)geqrf_kernel<8>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  CoopWs w = ws;
+  void* args[] = {&A, &lda, &m, &k, &tau, &T, &nb, &R, &w};
+  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, s);
+}
+
+cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* T,
+                  int nb, cplx* C, int ldc, int q, const CoopWs& ws, cudaStream_t s) {
+  (void)tau;
+  if (m <= 0 || p <= 0 || q <= 0) return cudaSuccess;
+  int G, R, nb2;
+  size_t smem;
+  pick_layout(m, &G, &R, &nb2, &smem);
+  if (nb2 != nb) {
+    // the layout depends only on m, so geqrf and ormqr agree
+    return cudaErrorInvalidValue;
+  }
+  if ((size_t)G * nb * (size_t)q > ws.pc_elems || (size_t)nb * q > ws.wfin_elems)
+    return cudaErrorInvalidValue;
+  void* fn;
+  if (nb == 32) fn = (void*)ormqr_kernel<32>;
+  else if (nb == 16) fn = (void*)ormqr_kernel<16>;
+  else fn = (void*)ormqr_kernel<8>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  CoopWs w = ws;
+  void* args[] = {(void*)&A, &lda, &m, &p, (void*)&T, &nb, &C, &ldc, &q, &R, &w};
+  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, s);
+}
+
+}  // namespace hk

@@ -1,0 +1,577 @@
+// TT-level kernels: the operator apply (memory-bound stencil over the cores),
+// block sums, point evaluation, Gaussian set-up, moments, and the dense
+// FP64 helpers (transposes, norms, small GEMMs) the rounding sweep uses.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace hk {
+
+const DevInfo& dev_info() {
+  static DevInfo di = [] {
+    DevInfo d{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return d;
+  }();
+  return di;
+}
+
+static inline int nblk(size_t n, int t) { return (int)((n + t - 1) / t); }
+
+// ---- operator apply ------------------------------------------------------------
+// Y[(alpha, i), m, (beta, j)] = sum_m' W[alpha, beta][m, m'] X[i, m', j] with
+// every W block tridiagonal in (m, m'): one of I, A, P, Q, Z.  One thread per
+// output element, consecutive threads along the fastest (left-rank) index, so
+// loads of X and stores of Y are both coalesced 16-byte accesses.
+__global__ void apply_core_kernel(const cplx* __restrict__ X, int a, int n, int c,
+                                  cplx* __restrict__ Y, int Al, int Ar,
+                                  const unsigned char* __restrict__ blocks,
+                                  const cplx* __restrict__ coef) {
+  const size_t rows = (size_t)Al * a;
+  const size_t total = rows * n * (size_t)(Ar * c);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = e % rows;
+    const size_t rest = e / rows;
+    const int m = (int)(rest % n);
+    const size_t q = rest / n;
+    const int al = (int)(p / a), i = (int)(p % a);
+    const int be = (int)(q / c), j = (int)(q % c);
+    const int op = blocks[al * Ar + be];
+    cplx v = mk(0, 0);
+    if (op != OP_NONE) {
+      const cplx* cf = coef + (size_t)op * 3 * n;
+      const cplx* x = X + i + (size_t)a * n * j;  // X[i, :, j] with stride a
+      v = cmul(cf[n + m], x[(size_t)a * m]);
+      if (m > 0) v = cfma(cf[m], x[(size_t)a * (m - 1)], v);
+      if (m + 1 < n) v = cfma(cf[2 * n + m], x[(size_t)a * (m + 1)], v);
+    }
+    Y[e] = v;
+  }
+}
+
+cudaError_t apply_core(const cplx* in, int a, int n, int c, cplx* out, int Al, int Ar,
+                       const unsigned char* blocks_dev, const OpTable& ops, cudaStream_t s) {
+  const size_t total = (size_t)Al * a * n * Ar * c;
+  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
+  apply_core_kernel<<<grid, 256, 0, s>>>(in, a, n, c, out, Al, Ar, blocks_dev, ops.coef);
+  return cudaGetLastError();
+}
+
+// ---- TT sum ----------------------------------------------------------------------
+__global__ void sum_core_kernel(const SumTerm* __restrict__ terms, int nterms, int kind, int n,
+                                cplx* __restrict__ out, int ora, int orc) {
+  const size_t total = (size_t)ora * n * orc;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e % ora);
+    const size_t rest = e / ora;
+    const int m = (int)(rest % n);
+    const int q = (int)(rest / n);
+    cplx v = mk(0, 0);
+    int offa = 0, offc = 0;
+    for (int t = 0; t < nterms; ++t) {
+      const SumTerm T = terms[t];
+      bool inside;
+      int ii, jj;
+      if (kind == 0) {  // first core: side by side along the right rank
+        inside = (q >= offc && q < offc + T.rc);
+        ii = p;
+        jj = q - offc;
+      } else if (kind == 2) {  // last core: stacked along the left rank
+        inside = (p >= offa && p < offa + T.ra);
+        ii = p - offa;
+        jj = q;
+      } else {  // interior: block diagonal
+        inside = (p >= offa && p < offa + T.ra && q >= offc && q < offc + T.rc);
+        ii = p - offa;
+        jj = q - offc;
+      }
+      if (inside) {
+        v = T.p[ii + (size_t)T.ra * m + (size_t)T.ra * n * jj];
+        if (kind == 0) v = cmul(T.coef, v);
+        break;
+      }
+      offa += T.ra;
+      offc += T.rc;
+    }
+    out[e] = v;
+  }
+}
+
+cudaError_t sum_core(const SumTerm* terms_dev, int nterms, int kind, int n, cplx* out, int ora,
+                     int orc, cudaStream_t s) {
+  const size_t total = (size_t)ora * n * orc;
+  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
+  sum_core_kernel<<<grid, 256, 0, s>>>(terms_dev, nterms, kind, n, out, ora, orc);
+  return cudaGetLastError();
+}
+
+// ---- point evaluation --------------------------------------------------------------
+// Phi[i_1..i_d] = C_1[0,i_1,:] C_2[:,i_2,:] ... C_d[:,i_d,0]; one CTA per point.
+__global__ void eval_points_kernel(const cplx* const* __restrict__ cores,
+                                   const int* __restrict__ ranks, int d, int n,
+                                   const int* __restrict__ idx, cplx* __restrict__ vals) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int maxr = blockDim.y;  // unused, kept for clarity
+  (void)maxr;
+  cplx* v = reinterpret_cast<cplx*>(sm);
+  const int pt = blockIdx.x;
+  int rmax = 1;
+  for (int k = 0; k <= d; ++k) rmax = max(rmax, ranks[k]);
+  cplx* w = v + rmax;
+  if (threadIdx.x == 0) v[0] = mk(1, 0);
+  __syncthreads();
+  for (int k = 0; k < d; ++k) {
+    const int a = ranks[k], c = ranks[k + 1];
+    const int ik = idx[(size_t)pt * d + k];
+    const cplx* C = cores[k] + (size_t)a * ik;  // C[:, ik, :] with column stride a*n
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+      const cplx* col = C + (size_t)a * n * j;
+      cplx acc = mk(0, 0);
+      for (int i = 0; i < a; ++i) acc = cfma(v[i], col[i], acc);
+      w[j] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < c; j += blockDim.x) v[j] = w[j];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) vals[pt] = v[0];
+}
+
+cudaError_t eval_points(const cplx* const* cores_dev, const int* ranks_dev, int d, int n, int maxr,
+                        int npts, const int* idx_dev, cplx* vals, cudaStream_t s) {
+  if (npts <= 0) return cudaSuccess;
+  const size_t smem = sizeof(cplx) * 2 * (size_t)std::max(maxr, 1);
+  eval_points_kernel<<<npts, 128, smem, s>>>(cores_dev, ranks_dev, d, n, idx_dev, vals);
+  return cudaGetLastError();
+}
+
+// ---- Gaussian initial state ------------------------------------------------------------
+__global__ void gauss_rank1_kernel(const double* agrid, int n, double m, double c, cplx* core) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double a = agrid[i];
+    const double mag = (i == 0) ? 0.0 : exp(-0.5 * c * a * a);
+    double sn, cs;
+    sincos(a * m, &sn, &cs);
+    core[i] = mk(mag * cs, mag * sn);
+  }
+}
+
+cudaError_t gauss_rank1_core(const double* agrid, int n, double m, double c, cplx* core,
+                             cudaStream_t s) {
+  gauss_rank1_kernel<<<nblk(n, 128), 128, 0, s>>>(agrid, n, m, c, core);
+  return cudaGetLastError();
+}
+
+// Middle core of the exact full-grid TT: C[x, i, y] = Phi0(modes) with
+// x = i_0 + n i_1 + ... (modes 0..c-1) and y = i_{c+1} + n i_{c+2} + ...
+__global__ void gauss_full_kernel(const double* agrid, int n, int d, int c, const double* m0,
+                                  const double* C0, cplx* core, size_t A, size_t B) {
+  const size_t total = A * n * B;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int ind[64];
+    size_t x = e % A;
+    const size_t rest = e / A;
+    ind[c] = (int)(rest % n);
+    size_t y = rest / n;
+    for (int k = 0; k < c; ++k) {
+      ind[k] = (int)(x % n);
+      x /= n;
+    }
+    for (int k = c + 1; k < d; ++k) {
+      ind[k] = (int)(y % n);
+      y /= n;
+    }
+    bool zero = false;
+    double ph = 0.0, q = 0.0;
+    for (int j = 0; j < d; ++j) {
+      zero |= (ind[j] == 0);
+      const double aj = agrid[ind[j]];
+      ph += aj * m0[j];
+      double row = 0.0;
+      for (int k = 0; k < d; ++k) row += C0[j + (size_t)d * k] * agrid[ind[k]];
+      q += aj * row;
+    }
+    cplx v = mk(0, 0);
+    if (!zero) {
+      const double mag = exp(-0.5 * q);
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      v = mk(mag * cs, mag * sn);
+    }
+    core[e] = v;
+  }
+}
+
+cudaError_t gauss_full_core(const double* agrid, int n, int d, int c, const double* m0,
+                            const double* C0, cplx* core, cudaStream_t s) {
+  size_t A = 1, B = 1;
+  for (int k = 0; k < c; ++k) A *= n;
+  for (int k = c + 1; k < d; ++k) B *= n;
+  const size_t total = A * n * B;
+  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
+  gauss_full_kernel<<<grid, 256, 0, s>>>(agrid, n, d, c, m0, C0, core, A, B);
+  return cudaGetLastError();
+}
+
+// Left identity core a x n x (a n): C[x, i, y] = [y == x + a i];
+// right identity core (n b) x n x b: C[x, i, y] = [x == i + n y].
+__global__ void identity_core_kernel(int n, int a, int b, int left, cplx* core) {
+  const size_t total = (size_t)a * n * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t x = e % a;
+    const size_t rest = e / a;
+    const size_t i = rest % n;
+    const size_t y = rest / n;
+    const bool one = left ? (y == x + (size_t)a * i) : (x == i + (size_t)n * y);
+    core[e] = mk(one ? 1.0 : 0.0, 0.0);
+  }
+}
+
+cudaError_t identity_core(int n, int a, int b, int left, cplx* core, cudaStream_t s) {
+  const size_t total = (size_t)a * n * b;
+  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
+  identity_core_kernel<<<grid, 256, 0, s>>>(n, a, b, left, core);
+  return cudaGetLastError();
+}
+
+// Cell moments by tensor Gauss-Legendre (nodes/weights on [0,1] in gl[0..q),
+// gl[q..2q)).  One thread per (j, k) pair; thread k of row d computes m0_k.
+__global__ void cell_moments_kernel(int d, int nmodes, const double* alpha, const double* beta,
+                                    double sigma, double ell, const double* gl, int q,
+                                    double* m0, double* C0) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const double h = 2.0 * 3.14159265358979323846 / d;
+  if (e < d * d) {
+    const int j = e % d, k = e / d;
+    double acc = 0.0;
+    for (int u = 0; u < q; ++u) {
+      const double x = (j + gl[u]) * h;
+      double inner = 0.0;
+      for (int v = 0; v < q; ++v) {
+        const double y = (k + gl[v]) * h;
+        const double sh = sin(0.5 * (x - y));
+        inner += gl[q + v] * exp(-2.0 * sh * sh / (ell * ell));
+      }
+      acc += gl[q + u] * inner;
+    }
+    C0[e] = sigma * sigma * acc;
+  } else if (e < d * d + d) {
+    const int k = e - d * d;
+    double acc = 0.0;
+    for (int u = 0; u < q; ++u) {
+      const double x = (k + gl[u]) * h;
+      double mu = 0.0;
+      for (int mm = 1; mm <= nmodes; ++mm) {
+        double sn, cs;
+        sincos(mm * x, &sn, &cs);
+        mu += alpha[mm - 1] * cs + beta[mm - 1] * sn;
+      }
+      acc += gl[q + u] * mu;
+    }
+    m0[k] = acc;
+  }
+}
+
+cudaError_t cell_moments(int d, int nmodes, const double* alpha, const double* beta,
+                         double sigma, double ell, const double* gl, int q, double* m0,
+                         double* C0, cudaStream_t s) {
+  cell_moments_kernel<<<nblk((size_t)d * d + d, 128), 128, 0, s>>>(d, nmodes, alpha, beta, sigma,
+                                                                  ell, gl, q, m0, C0);
+  return cudaGetLastError();
+}
+
+__global__ void init_sh_pad_kernel(const cplx* S, int lds, int q, int p, cplx* X, int ldx,
+                                   int mrows) {
+  const size_t total = (size_t)mrows * q;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % mrows), l = (int)(e / mrows);
+    X[r + (size_t)ldx * l] = (r < p) ? cconj(S[l + (size_t)lds * r]) : mk(0, 0);
+  }
+}
+
+cudaError_t init_sh_pad(const cplx* S, int lds, int q, int p, cplx* X, int ldx, int mrows,
+                        cudaStream_t s) {
+  const size_t total = (size_t)mrows * q;
+  if (total == 0) return cudaSuccess;
+  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 8);
+  init_sh_pad_kernel<<<grid, 256, 0, s>>>(S, lds, q, p, X, ldx, mrows);
+  return cudaGetLastError();
+}
+
+__global__ void gather_u_kernel(const cplx* src, int lds, int pp, const int* perm,
+                                const double* sigma, int use_sigma, int rho, cplx* X, int ldx,
+                                int mrows, cplx* Ub, int ldub) {
+  const size_t total = (size_t)mrows * rho;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % mrows), l = (int)(e / mrows);
+    cplx v = mk(0, 0);
+    if (r < pp) {
+      const int col = perm[l];
+      v = src[r + (size_t)lds * col];
+      if (use_sigma) {
+        const double sg = sigma[col];
+        v = (sg > 0.0) ? cscale(v, 1.0 / sg) : mk(0, 0);
+      }
+      Ub[r + (size_t)ldub * l] = v;
+    }
+    X[r + (size_t)ldx * l] = v;
+  }
+}
+
+cudaError_t gather_u(const cplx* src, int lds, int pp, const int* perm, const double* sigma,
+                     int use_sigma, int rho, cplx* X, int ldx, int mrows, cplx* Ub, int ldub,
+                     cudaStream_t s) {
+  const size_t total = (size_t)mrows * rho;
+  if (total == 0) return cudaSuccess;
+  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 8);
+  gather_u_kernel<<<grid, 256, 0, s>>>(src, lds, pp, perm, sigma, use_sigma, rho, X, ldx, mrows,
+                                       Ub, ldub);
+  return cudaGetLastError();
+}
+
+// ---- moments ----------------------------------------------------------------------------
+// vals layout: [0] Phi(0); [1+2k] Phi(+e_k), [2+2k] Phi(-e_k); then for each
+// pair j < k (row-major order) four values Phi(+j+k), Phi(+j-k), Phi(-j+k),
+// Phi(-j-k).
+__global__ void moments_combine_kernel(const cplx* vals, int d, double da, double* mean,
+                                       double* cov, double* imag_resid) {
+  __shared__ double mshared[256];
+  __shared__ double ires[256];
+  const int t = threadIdx.x;
+  double ir = 0.0;
+  for (int k = t; k < d; k += blockDim.x) {
+    const cplx p = vals[1 + 2 * k], m = vals[2 + 2 * k];
+    // -i (p - m) / (2 da)
+    const cplx dlt = csub(p, m);
+    const double re = dlt.y / (2 * da), im = -dlt.x / (2 * da);
+    mean[k] = re;
+    mshared[k] = re;
+    ir = fmax(ir, fabs(im));
+  }
+  __syncthreads();
+  for (int e = t; e < d * d; e += blockDim.x) {
+    const int j = e % d, k = e / d;
+    cplx v;
+    if (j == k) {
+      const cplx p = vals[1 + 2 * k], m = vals[2 + 2 * k], z = vals[0];
+      const cplx s2 = cadd(csub(p, cscale(z, 2.0)), m);
+      v = cscale(s2, -1.0 / (da * da));
+    } else {
+      const int a = min(j, k), b = max(j, k);
+      // pair index of (a, b), a < b, in row-major order over a
+      const int pidx = a * d - a * (a + 1) / 2 + (b - a - 1);
+      const cplx* f = vals + 1 + 2 * d + 4 * pidx;
+      // f: (+a+b), (+a-b), (-a+b), (-a-b); symmetric in (j, k)
+      const cplx s4 = csub(csub(f[0], f[1]), csub(f[2], f[3]));
+      v = cscale(s4, -1.0 / (4 * da * da));
+    }
+    cov[e] = v.x - mshared[j] * mshared[k];
+    ir = fmax(ir, fabs(v.y));
+  }
+  ires[t] = ir;
+  __syncthreads();
+  if (t == 0) {
+    double mx = 0.0;
+    for (int u = 0; u < blockDim.x; ++u) mx = fmax(mx, ires[u]);
+    if (imag_resid) *imag_resid = mx;
+  }
+}
+
+cudaError_t moments_combine(const cplx* vals, int d, double da, double* mean, double* cov,
+                            double* imag_resid, cudaStream_t s) {
+  if (d > 256) return cudaErrorInvalidValue;
+  moments_combine_kernel<<<1, 256, 0, s>>>(vals, d, da, mean, cov, imag_resid);
+  return cudaGetLastError();
+}
+
+// ---- dense helpers -------------------------------------------------------------------------
+__global__ void conj_transpose_kernel(const cplx* __restrict__ A, int lda, int k, int m,
+                                      cplx* __restrict__ B, int ldb) {
+  // A is k x m; B (m x k) = A^H.  32 x 32 tiles through shared memory.
+  __shared__ cplx tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;  // bx over m, by over k
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int col = bx + yy;        // column of A (index in m)
+    const int row = by + threadIdx.x;  // row of A (index in k)
+    if (row < k && col < m) tile[yy][threadIdx.x] = A[row + (size_t)lda * col];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int row = bx + threadIdx.x;  // row of B (index in m)
+    const int col = by + yy;           // column of B (index in k)
+    if (row < m && col < k) B[row + (size_t)ldb * col] = cconj(tile[threadIdx.x][yy]);
+  }
+}
+
+cudaError_t conj_transpose(const cplx* A, int lda, int k, int m, cplx* B, int ldb,
+                           cudaStream_t s) {
+  if (k <= 0 || m <= 0) return cudaSuccess;
+  dim3 grid((m + 31) / 32, (k + 31) / 32);
+  conj_transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(A, lda, k, m, B, ldb);
+  return cudaGetLastError();
+}
+
+__global__ void frob2_kernel(const cplx* A, int lda, int m, int k, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  const size_t total = (size_t)m * k;
+  for (size_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const size_t i = e % m, j = e / m;
+    acc += cabs2(A[i + (size_t)lda * j]);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+cudaError_t frob2(const cplx* A, int lda, int m, int k, double* out, cudaStream_t s) {
+  frob2_kernel<<<1, 1024, 0, s>>>(A, lda, m, k, out);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_zero(cplx* A, size_t count, cudaStream_t s) {
+  return cudaMemsetAsync(A, 0, count * sizeof(cplx), s);
+}
+
+__global__ void extract_r_kernel(const cplx* A, int lda, int p, int k, cplx* R, int ldr) {
+  const size_t total = (size_t)p * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % p), j = (int)(e / p);
+    R[i + (size_t)ldr * j] = (i <= j) ? A[i + (size_t)lda * j] : mk(0, 0);
+  }
+}
+
+cudaError_t extract_r(const cplx* A, int lda, int p, int k, cplx* R, int ldr, cudaStream_t s) {
+  const size_t total = (size_t)p * k;
+  extract_r_kernel<<<std::max(1, std::min(nblk(total, 256), 1024)), 256, 0, s>>>(A, lda, p, k, R, ldr);
+  return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const cplx* x, size_t count, int* flag) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const cplx v = x[e];
+    if (!isfinite(v.x) || !isfinite(v.y)) *flag = 1;
+  }
+}
+
+cudaError_t check_finite(const cplx* x, size_t count, int* flag, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int grid = std::min<size_t>(nblk(count, 256), (size_t)dev_info().sm_count * 8);
+  check_finite_kernel<<<grid, 256, 0, s>>>(x, count, flag);
+  return cudaGetLastError();
+}
+
+// ---- FP64 complex GEMM (64 x 64 tiles, 4 x 4 outputs per thread) -------------------------
+constexpr int GT = 64, GK = 16;
+
+struct LoadA_N {  // A(i, t) = A[i + lda t]
+  const cplx* A;
+  int lda, M, K;
+  __device__ cplx operator()(int i, int t) const {
+    return (i < M && t < K) ? A[i + (size_t)lda * t] : mk(0, 0);
+  }
+};
+struct LoadB_RH {  // B(t, j) = conj(R[j + ldr t]) for j <= t (R upper trapezoidal)
+  const cplx* R;
+  int ldr, K, N;
+  __device__ cplx operator()(int t, int j) const {
+    return (t < K && j < N && j <= t) ? cconj(R[j + (size_t)ldr * t]) : mk(0, 0);
+  }
+};
+struct LoadA_UH {  // A(i, t) = conj(U[t + ldu i])
+  const cplx* U;
+  int ldu, M, K;
+  __device__ cplx operator()(int i, int t) const {
+    return (i < M && t < K) ? cconj(U[t + (size_t)ldu * i]) : mk(0, 0);
+  }
+};
+struct LoadB_N {  // B(t, j) = B[t + ldb j]
+  const cplx* B;
+  int ldb, K, N;
+  __device__ cplx operator()(int t, int j) const {
+    return (t < K && j < N) ? B[t + (size_t)ldb * j] : mk(0, 0);
+  }
+};
+struct StoreC {  // mode 0: C[i + ldc j]; mode 1: conj into the H^H layout
+  cplx* C;
+  int ldc, M, N, mode, rl, n;
+  __device__ void operator()(int i, int j, cplx v) const {
+    if (i >= M || j >= N) return;
+    if (mode == 0) {
+      C[i + (size_t)ldc * j] = v;
+    } else {
+      const int ii = i % rl, mm = i / rl;
+      C[(size_t)(mm + (size_t)n * j) + (size_t)ldc * ii] = cconj(v);
+    }
+  }
+};
+
+template <class LA, class LB, class ST>
+__global__ void __launch_bounds__(256) gemm_kernel(LA la, LB lb, ST st, int M, int N, int K) {
+  __shared__ cplx As[GK][GT + 1];
+  __shared__ cplx Bs[GK][GT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  cplx acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = mk(0, 0);
+  for (int t0 = 0; t0 < K; t0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+      const int r = e % GT, kk = e / GT;
+      As[kk][r] = la(i0 + r, t0 + kk);
+      const int kk2 = e % GK, cc = e / GK;
+      Bs[kk2][cc] = lb(t0 + kk2, j0 + cc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      cplx av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = cfma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) st(i0 + tx + 16 * a, j0 + ty + 16 * b, acc[a][b]);
+}
+
+cudaError_t gemm_a_rh(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int N,
+                      cplx* C, int ldc, int mode, int rl, int n, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
+  gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N},
+                                   StoreC{C, ldc, M, N, mode, rl, n}, M, N, K);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_uh_r(const cplx* U, int ldu, int M, int K, const cplx* R, int ldr, int N,
+                      cplx* C, int ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
+  gemm_kernel<<<grid, 256, 0, s>>>(LoadA_UH{U, ldu, M, K}, LoadB_N{R, ldr, K, N},
+                                   StoreC{C, ldc, M, N, 0, 1, 1}, M, N, K);
+  return cudaGetLastError();
+}
+
+}  // namespace hk
