@@ -109,7 +109,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- oracle arm ----
-def oracle_sample_seconds(d_sample: int = 8):
+def oracle_sample_seconds(d_sample: int = 6):
     """One operator apply + rounding at rank 6r (the first RK4 stage) by the
     CPU oracle on a d_sample-core slice of the saturated workload.  Returns
     (seconds, extrapolated seconds per full RK4 step at d=32)."""
@@ -147,9 +147,9 @@ def run_reference(args, rank):
         per.append(oracle_sample_seconds()[1])
     step_s = sum(per) / len(per)
     value = 1.0 / step_s
-    sample = ("one operator apply + rank-6r rounding (first RK4 stage) on an 8-core slice "
-              "(d=8, n=128, r=64) of the saturated state; step time extrapolated by "
-              f"(d-1)/7 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")
+    sample = ("one operator apply + rank-6r rounding (first RK4 stage) on a 6-core slice "
+              "(d=6, n=128, r=64) of the saturated state; step time extrapolated by "
+              f"(d-1)/5 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")
     return {"metric": METRIC, "value": value, "unit": "steps/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -277,9 +277,9 @@ def run_ours(args, rank, world, local_rank):
         if world == 1 and not args.no_cpu_baseline:
             sec, per_step = oracle_sample_seconds()
             cpu = {"value": 1.0 / per_step, "unit": "steps/s", "cores": cpu_cores(), "kind": "oracle",
-                   "sample": ("one operator apply + rank-6r rounding (first RK4 stage) on an 8-core slice "
-                              f"(d=8, n=128, r=64) of the saturated state, {sec:.1f} s; step time extrapolated by "
-                              f"(d-1)/7 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")}
+                   "sample": ("one operator apply + rank-6r rounding (first RK4 stage) on a 6-core slice "
+                              f"(d=6, n=128, r=64) of the saturated state, {sec:.1f} s; step time extrapolated by "
+                              f"(d-1)/5 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")}
         result = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
@@ -302,7 +302,7 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

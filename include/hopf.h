@@ -211,6 +211,8 @@ typedef struct {
   double bytes[HOPF_K_NCLASS];     /* algorithmic DRAM bytes (apply, sums) */
   long long launches[HOPF_K_NCLASS]; /* kernels launched                   */
   long long timed_launches[HOPF_K_NCLASS]; /* launches covered by ms      */
+  long long svd_count;             /* Jacobi SVDs run                      */
+  long long svd_sweeps;            /* their sweeps, summed                 */
 } hopf_profile;
 
 /* Turns per-launch event timing on or off (launch counting is always on).

@@ -59,7 +59,8 @@ KERNEL_CLASSES = ["qr", "apply_q", "svd", "apply", "gemm", "sum", "small", "unus
 
 class HopfProfile(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("flops", C.c_double * 8), ("bytes", C.c_double * 8),
-                ("launches", C.c_longlong * 8), ("timed_launches", C.c_longlong * 8)]
+                ("launches", C.c_longlong * 8), ("timed_launches", C.c_longlong * 8),
+                ("svd_count", C.c_longlong), ("svd_sweeps", C.c_longlong)]
 
 
 class HopfParams(C.Structure):
@@ -281,9 +282,12 @@ class Context:
     def hopf_profile_read(self, reset=True):
         p = HopfProfile()
         self._check(self.lib.hopf_profile_read(self.h, C.byref(p), 1 if reset else 0))
-        return {name: {"ms": p.ms[i], "flops": p.flops[i], "bytes": p.bytes[i],
-                       "launches": int(p.launches[i]), "timed_launches": int(p.timed_launches[i])}
-                for i, name in enumerate(KERNEL_CLASSES)}
+        out = {name: {"ms": p.ms[i], "flops": p.flops[i], "bytes": p.bytes[i],
+                      "launches": int(p.launches[i]), "timed_launches": int(p.timed_launches[i])}
+               for i, name in enumerate(KERNEL_CLASSES)}
+        out["svd"]["count"] = int(p.svd_count)
+        out["svd"]["sweeps"] = int(p.svd_sweeps)
+        return out
 
     def tt_norm(self, t):
         v = C.c_double()

@@ -396,13 +396,13 @@ hopf_status orth_sweep(hopf_ctx* ctx, const hopf_tt* t, std::vector<int>& p, std
   return HOPF_OK;
 }
 
-hopf_status round_impl(hopf_ctx* ctx, hopf_tt* t, double tol, int cap, const int* forced,
-                       double* disc_out, bool* capped) {
+// Phase 2 of the rounding (left-to-right truncated SVDs, App. A Alg. 2
+// mirrored, factor-then-SVD as in Alg. 4), after a phase-1 sweep left the
+// factored flattenings in the workspace.  Writes the new cores into t.
+hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const std::vector<int>& nbv,
+                   double tol, int cap, const int* forced, double* disc_out, bool* capped) {
   const int d = t->d, n = t->n;
-  TRY(round_reserve(ctx, t));
   RoundWs& w = ctx->rw;
-  std::vector<int> p, nbv;
-  TRY(orth_sweep(ctx, t, p, nbv));
   TRY(read_small(ctx, 0, 1));
   TRY(check_barrier(ctx));
   const double nrm2 = ctx->h_dbl[0];
@@ -456,6 +456,8 @@ hopf_status round_impl(hopf_ctx* ctx, hopf_tt* t, double tol, int cap, const int
       TRY(read_small(ctx, 3, 5));
       TRY(check_barrier(ctx));
       if (ctx->h_int[2] < 0) return fail(ctx, HOPF_ENUMERIC, "Jacobi SVD did not converge at bond %d", c + 1);
+      ctx->prof.svd_count += 1;
+      ctx->prof.svd_sweeps += ctx->h_int[2];
       const double theta = std::max(1e-3 * eps_hat, 64.0 * 2.220446049250313e-16 * std::sqrt(ctx->h_dbl[4]));
       if (pass == 0 && !(ctx->h_dbl[3] > theta)) continue;  // smallest kept sigma below theta
       break;
@@ -494,6 +496,75 @@ hopf_status round_impl(hopf_ctx* ctx, hopf_tt* t, double tol, int cap, const int
   if (disc_out) *disc_out = std::sqrt(disc2);
   if (capped) *capped = cap_hit;
   return HOPF_OK;
+}
+
+hopf_status round_impl(hopf_ctx* ctx, hopf_tt* t, double tol, int cap, const int* forced,
+                       double* disc_out, bool* capped) {
+  TRY(round_reserve(ctx, t));
+  std::vector<int> p, nbv;
+  TRY(orth_sweep(ctx, t, p, nbv));
+  return phase2(ctx, t, p, nbv, tol, cap, forced, disc_out, capped);
+}
+
+// FLOPs of C = A (columns coff..coff+K of R)^H with R upper trapezoidal.
+double rblk_flops(double M, int K, int N, int coff) {
+  double s = 0.0;
+  for (int t = 0; t < K; ++t) s += std::min(N, coff + t + 1);
+  return 8.0 * M * s;
+}
+
+// Phase 1 for the rounding of Y = G X without forming Y: the LQ factor L_c
+// of core c is merged into core c-1 as
+//   Y'_{c-1}(alpha, i, m, q) = sum_beta W[alpha, beta] along m of
+//                              (X_{c-1} x_3 L_c[beta-block])(i, m, q),
+// i.e. six r x r x p products (one per MPO bond state beta) and one stencil
+// pass, instead of one (6r) x (6r) x p product on the materialised apply.
+// The stencil pass writes the next QR's input layout directly.
+hopf_status orth_sweep_apply(hopf_ctx* ctx, const hopf_tt* X, std::vector<int>& p, std::vector<int>& nbv) {
+  RoundWs& w = ctx->rw;
+  const int d = X->d, n = X->n;
+  const std::vector<int>& r = X->ranks;
+  const hk::OpTable ops{ctx->d_coef, n};
+  p.assign(d + 1, 1);
+  nbv.assign(d, 32);
+  {
+    const double rd = (double)r[d - 1] * n;
+    LAUNCH(HOPF_K_APPLY, 0, 16.0 * rd * 7.0, 1,
+           hk::stencil_combine(X->cores[d - 1], r[d - 1], n, 1, 1, 6, 1, ctx->d_blocks + 72, ops, w.B[d - 1], 1, n,
+                               ctx->stream));
+  }
+  for (int c = d - 1; c >= 1; --c) {
+    const int m = n * p[c + 1], k = 6 * r[c];
+    LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1,
+           hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream));
+    p[c] = std::min(m, k);
+    const int rl = r[c - 1];
+    const size_t blk = (size_t)rl * n * p[c];
+    for (int be = 0; be < 6; ++be) {
+      LAUNCH(HOPF_K_GEMM, rblk_flops((double)rl * n, r[c], p[c], be * r[c]), 0, 1,
+             hk::gemm_a_rblk_h(X->cores[c - 1], rl * n, rl * n, r[c], w.B[c], m, be * r[c], p[c], w.W1 + be * blk, rl * n,
+                               ctx->stream));
+    }
+    const int Al = (c - 1 == 0) ? 1 : 6;
+    const int kind = (c - 1 == 0) ? 0 : 1;
+    LAUNCH(HOPF_K_APPLY, 0, 16.0 * (double)blk * (6.0 + Al), 1,
+           hk::stencil_combine(w.W1, rl, n, p[c], 6, Al, 6, ctx->d_blocks + 36 * kind, ops, w.B[c - 1],
+                               (c - 1 == 0) ? 0 : 1, n * p[c], ctx->stream));
+  }
+  LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::frob2(w.B[0], n, n, p[1], ctx->d_dbl, ctx->stream));
+  return HOPF_OK;
+}
+
+// out <- T[G X] (hopf_apply_op followed by tt_round, without the apply).
+hopf_status round_apply_impl(hopf_ctx* ctx, const hopf_tt* X, hopf_tt* out, double tol, int cap,
+                             const int* forced, double* disc_out, bool* capped) {
+  std::vector<int> r(X->d + 1, 1);
+  for (int k = 1; k < X->d; ++k) r[k] = 6 * X->ranks[k];
+  TRY(check_fit(ctx, out, r));
+  TRY(round_reserve(ctx, out));
+  std::vector<int> p, nbv;
+  TRY(orth_sweep_apply(ctx, X, p, nbv));
+  return phase2(ctx, out, p, nbv, tol, cap, forced, disc_out, capped);
 }
 
 hopf_status apply_impl(hopf_ctx* ctx, const hopf_tt* in, hopf_tt* out) {
@@ -897,30 +968,38 @@ hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* f, double dt, int nsteps, double* 
     ++round_idx;
     return copy_impl(ctx, x, dst);
   };
+  // K = T[G y] with the apply fused into the orthogonalisation sweep
+  auto TG = [&](const hopf_tt* y, hopf_tt* dst) -> hopf_status {
+    const int* forced = forced_log ? forced_log + (size_t)round_idx * (d + 1) : nullptr;
+    double disc = 0.0;
+    bool c = false;
+    TRY(round_apply_impl(ctx, y, big, tol, cap, forced, &disc, &c));
+    capped |= c;
+    dsum += disc;
+    if (rank_log) std::copy(big->ranks.begin(), big->ranks.end(), rank_log + (size_t)round_idx * (d + 1));
+    ++round_idx;
+    return copy_impl(ctx, big, dst);
+  };
   for (int s = 0; s < nsteps; ++s) {
     const hopf_tt* tm[5];
     double cf[10] = {0};
     // K1 = T[G f]
-    TRY(apply_impl(ctx, f, big));
-    TRY(T(big, K[0]));
+    TRY(TG(f, K[0]));
     // Y2 = T[f + dt/2 K1]; K2 = T[G Y2]
     tm[0] = f; tm[1] = K[0]; cf[0] = 1.0; cf[2] = 0.5 * dt;
     TRY(sum_impl(ctx, 2, tm, cf, big));
     TRY(T(big, Y));
-    TRY(apply_impl(ctx, Y, big));
-    TRY(T(big, K[1]));
+    TRY(TG(Y, K[1]));
     // Y3 = T[f + dt/2 K2]; K3 = T[G Y3]
     tm[1] = K[1];
     TRY(sum_impl(ctx, 2, tm, cf, big));
     TRY(T(big, Y));
-    TRY(apply_impl(ctx, Y, big));
-    TRY(T(big, K[2]));
+    TRY(TG(Y, K[2]));
     // Y4 = T[f + dt K3]; K4 = T[G Y4]
     tm[1] = K[2]; cf[2] = dt;
     TRY(sum_impl(ctx, 2, tm, cf, big));
     TRY(T(big, Y));
-    TRY(apply_impl(ctx, Y, big));
-    TRY(T(big, K[3]));
+    TRY(TG(Y, K[3]));
     // f <- T[f + dt/6 (K1 + 2 K2 + 2 K3 + K4)]
     tm[0] = f; tm[1] = K[0]; tm[2] = K[1]; tm[3] = K[2]; tm[4] = K[3];
     cf[0] = 1.0; cf[2] = dt / 6.0; cf[4] = dt / 3.0; cf[6] = dt / 3.0; cf[8] = dt / 6.0;

@@ -76,6 +76,10 @@ cudaError_t extract_r(const cplx* A, int lda, int p, int k, cplx* R, int ldr, cu
 // B[(mm + n * j) + ldb * i] = conj(C[i_all, j]).
 cudaError_t gemm_a_rh(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int N,
                       cplx* C, int ldc, int mode, int rl, int n, cudaStream_t s);
+// C[M x N] = A[M x K] * (columns coff..coff+K of R)^H, R upper trapezoidal
+// (ldr): C[i, q] = sum_t A[i, t] conj(R[q, coff + t]) over q <= coff + t.
+cudaError_t gemm_a_rblk_h(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int coff,
+                          int N, cplx* C, int ldc, cudaStream_t s);
 // C[M x N] = U[:, perm[0..M)]^H-gathered * R: C[i, j] = sum_t conj(U[t, i]) R[t, j].
 cudaError_t gemm_uh_r(const cplx* U, int ldu, int M, int K, const cplx* R, int ldr, int N,
                       cplx* C, int ldc, cudaStream_t s);
@@ -88,6 +92,12 @@ struct OpTable {
   int n;
 };
 enum { OP_I = 0, OP_A = 1, OP_P = 2, OP_Q = 3, OP_Z = 4, OP_NONE = 7 };
+// Operator blocks applied along the middle index and summed over beta:
+// out(alpha, i, m, q) = sum_{beta < Bn} W[alpha*Ar + beta](T_beta[i, :, q])[m].
+// mode 0: V layout, mode 1: conj-transposed H^H layout with leading dim ldo.
+cudaError_t stencil_combine(const cplx* T, int r, int n, int p, int Bn, int Al, int Ar,
+                            const unsigned char* blocks_dev, const OpTable& ops, cplx* out,
+                            int mode, int ldo, cudaStream_t s);
 // out core (Al*a) x n x (Ar*c) from in core a x n x c; blocks[alpha*Ar+beta]
 // holds the op index (OP_NONE = zero block).
 cudaError_t apply_core(const cplx* in, int a, int n, int c, cplx* out, int Al, int Ar,

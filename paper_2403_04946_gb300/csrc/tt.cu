@@ -482,11 +482,11 @@ struct LoadA_N {  // A(i, t) = A[i + lda t]
     return (i < M && t < K) ? A[i + (size_t)lda * t] : mk(0, 0);
   }
 };
-struct LoadB_RH {  // B(t, j) = conj(R[j + ldr t]) for j <= t (R upper trapezoidal)
-  const cplx* R;
-  int ldr, K, N;
+struct LoadB_RH {  // B(t, j) = conj(R[j + ldr (coff + t)]) for j <= coff + t
+  const cplx* R;    // (R upper trapezoidal; coff selects a block of columns)
+  int ldr, K, N, coff;
   __device__ cplx operator()(int t, int j) const {
-    return (t < K && j < N && j <= t) ? cconj(R[j + (size_t)ldr * t]) : mk(0, 0);
+    return (t < K && j < N && j <= coff + t) ? cconj(R[j + (size_t)ldr * (coff + t)]) : mk(0, 0);
   }
 };
 struct LoadA_UH {  // A(i, t) = conj(U[t + ldu i])
@@ -560,8 +560,62 @@ cudaError_t gemm_a_rh(const cplx* A, int lda, int M, int K, const cplx* R, int l
                       cplx* C, int ldc, int mode, int rl, int n, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
-  gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N},
+  gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, 0},
                                    StoreC{C, ldc, M, N, mode, rl, n}, M, N, K);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_a_rblk_h(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int coff,
+                          int N, cplx* C, int ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
+  gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, coff},
+                                   StoreC{C, ldc, M, N, 0, 1, 1}, M, N, K);
+  return cudaGetLastError();
+}
+
+// out(alpha, i, m, q) = sum_beta W[alpha, beta] applied along m to
+// T_beta[i, :, q] (T_beta: r x n x p, consecutive blocks of r n p).  Written
+// in the V layout (mode 0: out[(alpha r + i) + Al r m + Al r n q]) or
+// conj-transposed into the H^H layout of the next QR (mode 1:
+// out[(m + n q) + ldo (alpha r + i)] = conj(value)).
+__global__ void stencil_combine_kernel(const cplx* __restrict__ T, int r, int n, int p, int Bn,
+                                       int Al, int Ar, const unsigned char* __restrict__ blocks,
+                                       const cplx* __restrict__ coef, cplx* __restrict__ out,
+                                       int mode, int ldo) {
+  const size_t rows = (size_t)Al * r;
+  const size_t total = rows * n * (size_t)p;
+  const size_t blk = (size_t)r * n * p;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t pr = e % rows;
+    const size_t rest = e / rows;
+    const int m = (int)(rest % n);
+    const int q = (int)(rest / n);
+    const int al = (int)(pr / r), i = (int)(pr % r);
+    cplx v = mk(0, 0);
+    for (int be = 0; be < Bn; ++be) {
+      const int op = blocks[al * Ar + be];
+      if (op == OP_NONE) continue;
+      const cplx* cf = coef + (size_t)op * 3 * n;
+      const cplx* x = T + blk * be + i + (size_t)r * n * q;  // T_beta[i, :, q], stride r
+      v = cfma(cf[n + m], x[(size_t)r * m], v);
+      if (m > 0) v = cfma(cf[m], x[(size_t)r * (m - 1)], v);
+      if (m + 1 < n) v = cfma(cf[2 * n + m], x[(size_t)r * (m + 1)], v);
+    }
+    if (mode == 0) out[e] = v;
+    else out[(size_t)(m + (size_t)n * q) + (size_t)ldo * pr] = cconj(v);
+  }
+}
+
+cudaError_t stencil_combine(const cplx* T, int r, int n, int p, int Bn, int Al, int Ar,
+                            const unsigned char* blocks_dev, const OpTable& ops, cplx* out,
+                            int mode, int ldo, cudaStream_t s) {
+  const size_t total = (size_t)Al * r * n * p;
+  if (total == 0) return cudaSuccess;
+  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
+  stencil_combine_kernel<<<grid, 256, 0, s>>>(T, r, n, p, Bn, Al, Ar, blocks_dev, ops.coef, out,
+                                              mode, ldo);
   return cudaGetLastError();
 }
 
