@@ -184,6 +184,31 @@ hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean,
 hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts,
                              const int* idx, double* vals);
 
+/* Allocation-free variant of hopf_eval_points (the paper has no counterpart;
+ * it exists for callers that cannot allocate device memory).
+ *
+ * hopf_eval_points allocates its device staging buffers with cudaMalloc and
+ * releases them with cudaFree on every call.  cudaFree waits for all work on
+ * the device, so a caller that probes Phi between solver steps while other
+ * streams keep the GPU busy would stall them; and a process whose device
+ * memory is fully reserved by another allocator may not be able to allocate
+ * at all.  This call stages the same data in two fixed arrays inside the
+ * library's device image instead (HOPF_NOALLOC_MAX_POINTS points of at most
+ * HOPF_NOALLOC_MAX_D modes: 512 KiB of indices and 32 KiB of results,
+ * reserved on every GPU that loads the library until the process exits).
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Arguments and results are those of hopf_eval_points (the tensor's context
+ * and stream are used).  npts > HOPF_NOALLOC_MAX_POINTS or d >
+ * HOPF_NOALLOC_MAX_D returns HOPF_EINVAL.  The first call on a device looks
+ * up the arrays' device addresses (with that device current); make that
+ * first call before any stream capture.  All calls share the two arrays:
+ * calls whose GPU work overlaps (on different streams or contexts) race on
+ * them and must be serialised by the caller. */
+#define HOPF_NOALLOC_MAX_POINTS 2048
+#define HOPF_NOALLOC_MAX_D 64
+hopf_status hopf_eval_points_noalloc(const hopf_tt* t, int npts, const int* idx, double* vals);
+
 /* ||t||_F (by orthogonalisation, computed on the device). */
 hopf_status tt_norm(hopf_ctx* ctx, const hopf_tt* t, double* norm);
 

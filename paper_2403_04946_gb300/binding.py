@@ -52,6 +52,7 @@ SIGNATURES = {
     "tt_set_from_host": (_i, [_vp, _pi, _pd]),
     "hopf_profile_enable": (_i, [_vp, _i]),
     "hopf_profile_read": (_i, [_vp, _vp, _i]),
+    "hopf_eval_points_noalloc": (_i, [_vp, _i, _pi, _pd]),
 }
 
 KERNEL_CLASSES = ["qr", "apply_q", "svd", "apply", "gemm", "sum", "small", "unused"]
@@ -288,6 +289,14 @@ class Context:
         out["svd"]["count"] = int(p.svd_count)
         out["svd"]["sweeps"] = int(p.svd_sweeps)
         return out
+
+    def hopf_eval_points_noalloc(self, t, idx):
+        """As hopf_eval_points, staged in the library's fixed device arrays
+        (no device allocation; at most 2048 points per call)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        vals = np.zeros(2 * idx.shape[0])
+        self._check(self.lib.hopf_eval_points_noalloc(t, idx.shape[0], _iptr(idx), _dptr(vals)))
+        return vals.view(np.complex128)
 
     def tt_norm(self, t):
         v = C.c_double()

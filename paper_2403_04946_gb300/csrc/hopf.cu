@@ -679,6 +679,24 @@ std::vector<double> gauss_legendre01(int q) {
 
 }  // namespace
 
+// Accessors for the allocation-free entry point (noalloc.cu).
+hopf_ctx* hopf_internal_tt_ctx(const hopf_tt* t) { return t->ctx; }
+cudaStream_t hopf_internal_stream(const hopf_ctx* ctx) { return ctx->stream; }
+hopf_status hopf_internal_tt_view(const hopf_tt* t, const double2* const** d_ptrs, const int** d_ranks,
+                                  int* d, int* n, int* maxr) {
+  *d_ptrs = t->d_ptrs;
+  *d_ranks = t->d_ranks;
+  *d = t->d;
+  *n = t->n;
+  int m = 1;
+  for (int r : t->ranks) m = std::max(m, r);
+  *maxr = m;
+  return HOPF_OK;
+}
+void hopf_internal_set_error(hopf_ctx* ctx, const char* msg) {
+  if (ctx) ctx->err = msg;
+}
+
 // ===========================================================================
 extern "C" {
 
