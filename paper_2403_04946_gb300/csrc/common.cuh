@@ -76,47 +76,49 @@ DV uint64_t global_ns() {
   return t;
 }
 
-// Grid barrier state (device memory, zeroed before the first launch).
+// Grid barrier state (device memory).  `count` is zeroed by the host before
+// every cooperative launch; `err` records an expired wait.
 struct GridBar {
   unsigned int count;
-  unsigned int gen;
+  unsigned int unused;
   int err;  // nonzero after a wait expired
   int pad;
 };
 
 // Barrier across all CTAs of a cooperative launch (co-residency guaranteed
-// by cudaLaunchCooperativeKernel).  Every wait is bounded: after
-// `timeout_ns` of wall time the CTA records the expiry in bar->err and
+// by cudaLaunchCooperativeKernel).  The arrival counter only grows: on its
+// k-th barrier every CTA adds one and waits until the counter reaches
+// k * gridDim, so no CTA has to reset anything between barriers (one atomic
+// and one polled load per CTA per barrier).  Every wait is bounded: after
+// kBarrierTimeoutNs of wall time the CTA records the expiry in err and
 // leaves; callers check grid_failed() and return early.
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 
-DV void grid_sync(GridBar* bar) {
+struct GridSync {
+  GridBar* bar;
+  unsigned int target;  // used by thread 0 of each CTA
+};
+
+DV void grid_sync(GridSync& gs) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
-    volatile int* verr = &bar->err;
+    volatile int* verr = &gs.bar->err;
+    gs.target += gridDim.x * gridDim.y * gridDim.z;
     if (*verr == 0) {
-      const unsigned int g = *vgen;
       __threadfence();
-      const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-      const unsigned int arrived = atomicAdd(&bar->count, 1u);
-      if (arrived == nb - 1) {
-        atomicExch(&bar->count, 0u);
-        __threadfence();
-        atomicAdd(&bar->gen, 1u);
-      } else {
-        const uint64_t t0 = global_ns();
-        unsigned int spins = 0;
-        while (*vgen == g) {
-          if (((++spins) & 255u) == 0u) {
-            if (*verr != 0) break;
-            if (global_ns() - t0 > kBarrierTimeoutNs) {
-              atomicExch(&bar->err, 1);
-              break;
-            }
+      atomicAdd(&gs.bar->count, 1u);
+      volatile unsigned int* vc = &gs.bar->count;
+      const uint64_t t0 = global_ns();
+      unsigned int spins = 0;
+      while ((int)(*vc - gs.target) < 0) {
+        if (((++spins) & 255u) == 0u) {
+          if (*verr != 0) break;
+          if (global_ns() - t0 > kBarrierTimeoutNs) {
+            atomicExch(&gs.bar->err, 1);
+            break;
           }
-          __nanosleep(64);
         }
+        __nanosleep(32);
       }
     }
     __threadfence();

@@ -42,8 +42,12 @@ __device__ void partial_vhx(const cplx* P, int R, int r0, int lo, int hi, int nb
 #pragma unroll
     for (int s = 0; s < NB; ++s) acc[s] = mk(0, 0);
     const cplx* x = X + (size_t)ldx * l;
+    // one row of look-ahead: the next row's load is in flight while this
+    // row's NB complex multiply-adds run
+    cplx xn = (lo + lane < hi) ? x[lo + lane] : mk(0, 0);
     for (int i = lo + lane; i < hi; i += 32) {
-      const cplx xi = x[i];
+      const cplx xi = xn;
+      if (i + 32 < hi) xn = x[i + 32];
       const cplx* pv = P + (i - r0);
 #pragma unroll
       for (int s = 0; s < NB; ++s)
@@ -68,14 +72,19 @@ __device__ void update_x(const cplx* P, int R, int r0, int lo, int hi, int nbk, 
   for (int l = w; l < ncol; l += nw) {
     cplx wc[NB];
 #pragma unroll
-    for (int s = 0; s < NB; ++s) wc[s] = (s < nbk) ? ld_cg(w2 + s + (size_t)nbk * l) : mk(0, 0);
+    for (int s = 0; s < NB; ++s) {
+      const cplx w = (s < nbk) ? ld_cg(w2 + s + (size_t)nbk * l) : mk(0, 0);
+      wc[s] = mk(-w.x, -w.y);
+    }
     cplx* x = X + (size_t)ldx * l;
+    cplx xn = (lo + lane < hi) ? x[lo + lane] : mk(0, 0);
     for (int i = lo + lane; i < hi; i += 32) {
-      cplx acc = x[i];
+      cplx acc = xn;
+      if (i + 32 < hi) xn = x[i + 32];
       const cplx* pv = P + (i - r0);
 #pragma unroll
       for (int s = 0; s < NB; ++s)
-        if (s < nbk) acc = csub(acc, cmul(pv[(size_t)s * R], wc[s]));
+        if (s < nbk) acc = cfma(pv[(size_t)s * R], wc[s], acc);  // wc holds -W2: 4 FMAs
       x[i] = acc;
     }
   }
@@ -106,6 +115,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
   const int r0 = g * R, r1 = min(m, r0 + R);
   const int p = min(m, k);
   const size_t pstride = ws.pc_elems / G;
+  GridSync gs{ws.bar, 0u};
 
   for (int j0 = 0, panel = 0; j0 < p; j0 += nb, ++panel) {
     const int nbk = min(nb, p - j0);
@@ -126,7 +136,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         ws.pr[g] = sq;
         if (jj >= r0 && jj < r1) ws.scal[0] = pt[jj - r0];
       }
-      grid_sync(ws.bar);
+      grid_sync(gs);
       if (grid_failed(ws.bar)) return;
       // (2) Householder vector (zlarfg conventions: beta real, v_jj = 1)
       if (wid == 0) {
@@ -174,7 +184,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
           acc = warp_sum(acc);
           if (lane == 0) ws.pc[(size_t)g * pstride + l] = acc;
         }
-        grid_sync(ws.bar);
+        grid_sync(gs);
         if (grid_failed(ws.bar)) return;
         for (int l = wid; l < nrem; l += nw) {
           cplx sum = reduce_partials(ws.pc, pstride, G, l);
@@ -232,7 +242,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
       if (nt > 0)
         partial_vhx<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, out + (size_t)nbk * nbk);
     }
-    grid_sync(ws.bar);
+    grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     // S2: reduce columns l % G == g into wfin
     for (int l = g; l < ncol; l += G) {
@@ -241,7 +251,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         if (lane == 0) ws.wfin[s + (size_t)nbk * l] = v;
       }
     }
-    grid_sync(ws.bar);
+    grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     // S3: T from the reflector Gram (zlarft, forward, columnwise), then
     // W2 = T^H W for the trailing columns this CTA reduced.
@@ -283,7 +293,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         if (lane < nbk) ws.wfin[lane + (size_t)nbk * l] = acc;
       }
     }
-    grid_sync(ws.bar);
+    grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     // S4: trailing update over this CTA's rows
     if (nt > 0) update_x<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, ws.wfin + (size_t)nbk * nbk);
@@ -303,6 +313,7 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
   const int r0 = g * R, r1 = min(m, r0 + R);
   const size_t pstride = ws.pc_elems / G;
   const int npanel = (p + nb - 1) / nb;
+  GridSync gs{ws.bar, 0u};
   for (int panel = npanel - 1; panel >= 0; --panel) {
     const int j0 = panel * nb;
     const int nbk = min(nb, p - j0);
@@ -319,7 +330,7 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
     for (int e = tid; e < nbk * nbk; e += blockDim.x) Ts[e] = Tg[(size_t)panel * nb * nb + e];
     __syncthreads();
     partial_vhx<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
-    grid_sync(ws.bar);
+    grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     // reduce and multiply by T: W2 = T W (apply Q, not Q^H)
     for (int l = g; l < q; l += G) {
@@ -340,7 +351,7 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
       }
       __syncthreads();
     }
-    grid_sync(ws.bar);
+    grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     update_x<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.wfin);
     __syncthreads();
@@ -378,6 +389,8 @@ cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_ou
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CoopWs w = ws;
+  e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
   void* args[] = {&A, &lda, &m, &k, &tau, &T, &nb, &R, &w};
   return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, s);
 }
@@ -402,6 +415,8 @@ cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const c
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CoopWs w = ws;
+  e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&A, &lda, &m, &p, (void*)&T, &nb, &C, &ldc, &q, &R, &w};
   return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, s);
 }

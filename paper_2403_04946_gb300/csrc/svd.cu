@@ -48,6 +48,7 @@ jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, do
   const int lane = gt & 31, gw = gt >> 5;
   const int N = nc + (nc & 1);
   const int npairs = N / 2;
+  GridSync gs{ws.bar, 0u};
 
   // ||M||_F^2 (invariant under the rotations), reduced over all CTAs
   {
@@ -59,7 +60,7 @@ jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, do
     s = block_sum(s, fro_red);
     if (threadIdx.x == 0) ws.pr[g] = s;
   }
-  grid_sync(ws.bar);
+  grid_sync(gs);
   if (grid_failed(ws.bar)) return;
   double fro2 = 0.0;
   for (int gg = 0; gg < G; ++gg) fro2 += __ldcg(ws.pr + gg);
@@ -165,7 +166,7 @@ jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, do
           if (gt == 0) atomicAdd(ws.counters + (sweep & 31), 1);
         }
       }
-      grid_sync(ws.bar);
+      grid_sync(gs);
       if (grid_failed(ws.bar)) return;
     }
     // every CTA sees the same count after the last round's barrier
@@ -196,6 +197,8 @@ cudaError_t jacobi_svd(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int a
     init_identity_kernel<<<(nc * nc + 255) / 256, 256, 0, s>>>(J, ldj, nc);
   }
   cudaError_t e = cudaMemsetAsync(ws.counters, 0, 32 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   const DevInfo& di = dev_info();
   const int npairs = (nc + 1) / 2;

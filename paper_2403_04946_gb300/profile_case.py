@@ -1,0 +1,52 @@
+"""Small, self-contained invocation of the hot path for profilers.
+
+Runs the first RK4 stage of the saturated workload on a d-mode slice:
+operator apply (hopf_apply_op) and one rounding (tt_round) at rank 6r, plus
+one fused hopf_step when --step is given.  Sized by --d/--n/--r so a capture
+stays small (d=4, n=128, r=64 holds about 2.5 GB on the device).
+
+  python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--d", type=int, default=4)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--r", type=int, default=64)
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--step", action="store_true")
+    args = ap.parse_args()
+    from paper_2403_04946_gb300 import binding
+    import synthetic
+
+    cores, _ = synthetic.saturated_tt_cores(args.d, args.n, args.r, seed=0)
+    ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r, L=12.4)
+    t = ctx.tt_from_host(cores, max_rank=args.r)
+    big = ctx.tt_create(6 * args.r)
+    t0 = time.time()
+    ctx.hopf_apply_op(t, big)
+    disc, _ = ctx.tt_round(big, args.tol, args.r)
+    print(f"apply+round d={args.d} n={args.n} r={args.r}: {time.time() - t0:.3f} s, "
+          f"ranks {ctx.tt_get_ranks(big)}, discarded {disc:.3e}")
+    if args.step:
+        t0 = time.time()
+        ctx.hopf_step(t, 1.2e-5, 1)
+        print(f"hopf_step: {time.time() - t0:.3f} s")
+    ctx.tt_free(big)
+    ctx.tt_free(t)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
