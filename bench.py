@@ -5,7 +5,10 @@ One step = one full RK4 step of the hot path: 4 operator applies, 8 TT
 roundings (right-to-left Householder orthogonalisation + left-to-right
 truncated SVD) and 4 TT sums, on the d=32, n=128, rank<=64 workload, in the
 "saturated" state (every interior rank at the cap 64: a seeded TT with random
-orthonormal cores), complex float64.
+orthonormal cores), complex values in FP64 storage.  ``value`` is the mixed-
+precision solver (FP64 panels and SVD, double-float updates); the FP64 solver
+is timed on the same state under the ``fp64`` key, and the mixed-vs-FP64
+error is measured on a physical state.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,6 +33,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TT RK4 steps/s (d=32,n=128,r≤64) mixed vs FP64 @≤1e-6 err; roofline %"
 FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12  # 152 SMs x 2 DFMA/clk x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 2070e6 * 256 / 1e12  # 152 SMs x 128 FFMA/clk x 2.07 GHz
+# double-float complex multiply-add: 4 real multiply-adds of ~13 FP32
+# operations each = 52 FP32 operations for 8 FP64-equivalent FLOPs
+DF_OPS_PER_FLOP = 52.0 / 8.0
 # relative cost of one RK4 step in units of one rounding at rank 6r:
 # 4 roundings at 6r, 3 at 2r, 1 at 5r (cost ~ K^3 per core)
 STEP_PER_KROUND = (4 * 216 + 3 * 8 + 125) / 216.0
@@ -164,18 +171,88 @@ def run_reference(args, rank):
 def config_dict(w):
     return {"workload": f"saturated TT, d={w.d}, n={w.n}, rank cap {w.cap} (all interior ranks at the cap), "
                         f"tol {w.tol:g}, dt {w.dt:g}, nu {w.nu}, FP64 complex",
-            "d": w.d, "n": w.n, "rank_cap": w.cap, "tol": w.tol, "dt": w.dt, "precision": "fp64",
+            "d": w.d, "n": w.n, "rank_cap": w.cap, "tol": w.tol, "dt": w.dt,
+            "precision": "mixed (value) and fp64 (fp64 key)",
             "state": "seeded random orthonormal cores (seed 0)",
             "l2": "working set (~20 GB) larger than L2; no flush needed",
             "parallelism": "replicas"}
 
 
 # ---------------------------------------------------------------- our arm ----
+def timed_steps(ctx, t, w, steps, warmup, stream, barrier):
+    import torch
+    for _ in range(warmup):
+        ctx.hopf_step(t, w.dt, 1)
+    ctx.hopf_profile_read(reset=True)
+    ctx.hopf_profile_enable(True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.hopf_step(t, w.dt, 1)
+    e1.record(stream)
+    barrier()
+    prof = ctx.hopf_profile_read(reset=True)
+    ctx.hopf_profile_enable(False)
+    return e0.elapsed_time(e1) / 1e3, prof
+
+
+def roofline(prof, mixed, peaks):
+    """Dominant contraction kernel class (largest device time among classes
+    with an algorithmic FLOP count) against the peak of its own arithmetic."""
+    cls = [k for k in prof if isinstance(prof[k], dict) and prof[k].get("flops", 0) > 0 and prof[k]["ms"] > 0]
+    dom = max(cls, key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    launch_s = pd["ms"] / 1e3 / max(pd["timed_launches"], 1)
+    achieved = pd["flops"] / max(pd["timed_launches"], 1) / launch_s / 1e12
+    if mixed:
+        peak = FP32_PEAK_TFLOPS / DF_OPS_PER_FLOP
+        src = ("double-float on the FP32 pipe: 152 SMs x 256 FLOP/clk x 2.07 GHz / 6.5 FP32 ops per "
+               "FP64-equivalent FLOP (derived); FP64 panels inside the same kernel")
+    else:
+        peak = FP64_PEAK_TFLOPS
+        src = "FP64 FMA: 152 SMs x 4 FLOP/clk x 2.07 GHz (derived; DFMA microbenchmark measured 1.19)"
+    return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": src, "traffic": None}
+
+
+def natural_state_error(w, stream, nsteps=5):
+    """Mixed vs FP64 after nsteps on a physical C3-size state: the Gaussian
+    initial state with the C3 mean and cell variances (diagonal covariance,
+    exact rank-1 TT), errors in Phi (TT difference norm), mean, covariance."""
+    import numpy as np
+    from paper_2403_04946_gb300 import binding as B
+    c0 = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=1.0, stream=stream)
+    m0, C0 = c0.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
+    c0.close()
+    C0d = np.diag(np.diag(C0))
+    out = {}
+    for prec in (B.HOPF_FP64, B.HOPF_MIXED):
+        ctx = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=0.0, stream=stream, precision=prec)
+        t = ctx.hopf_init_gaussian(m0, C0d)
+        ctx.hopf_step(t, w.dt, nsteps)
+        mean, cov, _ = ctx.hopf_eval_moments(t)
+        out[prec] = (ctx.tt_to_host(t), mean, cov, ctx.tt_get_ranks(t))
+        ctx.close()
+    (cf, mf, vf, rf), (cm, mm, vm, rm) = out[B.HOPF_FP64], out[B.HOPF_MIXED]
+    ctx = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=12.4, stream=stream)
+    a = ctx.tt_from_host(cf, max_rank=max(rf))
+    b = ctx.tt_from_host(cm, max_rank=max(rm))
+    dif = ctx.tt_create(max(rf) + max(rm))
+    ctx.tt_sum([a, b], [1.0, -1.0], dif)
+    phi = ctx.tt_norm(dif) / ctx.tt_norm(a)
+    ctx.close()
+    return {"phi_rel_l2": phi, "mean_rel_max": float(np.abs(mm - mf).max() / np.abs(mf).max()),
+            "cov_rel_max": float(np.abs(vm - vf).max() / np.abs(vf).max()), "steps": nsteps,
+            "state": "Gaussian initial state, C3 mean and cell variances, diagonal covariance (exact rank 1)",
+            "max_rank": int(max(rm))}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
     from paper_2403_04946_gb300 import binding
-    from oracle import model  # noqa: F401  (used only for the CPU baseline leg)
     import synthetic
 
     torch.cuda.set_device(local_rank)
@@ -187,44 +264,34 @@ def run_ours(args, rank, world, local_rank):
     m0, C0 = ctx0.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
     ctx0.close()
     L = float(np.sqrt(36.8 / np.min(np.diag(C0))))
-    ctx = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L,
-                          stream=stream.cuda_stream)
     cores, ranks = synthetic.saturated_tt_cores(w.d, w.n, w.cap, seed=0)
-    t = ctx.tt_from_host(cores, max_rank=w.cap)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        ctx.hopf_step(t, w.dt, 1)
-    ctx.hopf_profile_read(reset=True)
-    ctx.hopf_profile_enable(True)
+    def maxover(x):
+        tm = torch.tensor([x], device=dev, dtype=torch.float64)
+        if world > 1:
+            torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+        return float(tm.item())
 
     gpu_id = "0"
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
     except Exception:
         pass
+
+    # primary arm: mixed precision (FP64 panels and SVD, double-float updates)
+    ctx = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L,
+                          stream=stream.cuda_stream, precision=binding.HOPF_MIXED)
+    t = ctx.tt_from_host(cores, max_rank=w.cap)
     clocks = ClockSampler(gpu_id)
     clocks.start()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctx.hopf_step(t, w.dt, 1)
-    e1.record(stream)
-    barrier()
+    elapsed, prof = timed_steps(ctx, t, w, args.steps, args.warmup, stream, barrier)
     clocks.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    prof = ctx.hopf_profile_read(reset=True)
-    ctx.hopf_profile_enable(False)
-    tmax = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-    elapsed = float(tmax.item())
+    elapsed = maxover(elapsed)
 
     # end to end through the C ABI: pinned host state in, step, state out
     ranks_np = np.asarray(ranks, dtype=np.int32)
@@ -243,35 +310,30 @@ def run_ours(args, rank, world, local_rank):
         ctx.hopf_step(t, w.dt, 1)
         ctx.tt_to_host_into(t, pin_out, ctx.tt_size(t))
     barrier()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = maxover(time.perf_counter() - t0)
     out_bytes = ctx.tt_size(t) * 8
+    ctx.tt_free(t)
+    ctx.close()
+
+    # FP64 arm on the same state (the comparison the metric names)
+    ctx = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L,
+                          stream=stream.cuda_stream, precision=binding.HOPF_FP64)
+    t = ctx.tt_from_host(cores, max_rank=w.cap)
+    el64, prof64 = timed_steps(ctx, t, w, args.steps, 1, stream, barrier)
+    el64 = maxover(el64)
+    ctx.tt_free(t)
+    ctx.close()
+
+    err = natural_state_error(w, stream.cuda_stream) if not args.no_error_check else None
 
     result = None
     if rank == 0:
-        value = world * args.steps / elapsed
-        # roofline of the dominant kernel class
-        dom = max(prof, key=lambda k: prof[k]["ms"])
-        pd = prof[dom]
-        launch_s = pd["ms"] / 1e3 / max(pd["timed_launches"], 1)
         peaks = read_peaks()
-        if pd["flops"] > 0:
-            achieved = pd["flops"] / max(pd["timed_launches"], 1) / launch_s / 1e12
-            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "FP64 FMA: 152 SMs x 4 FLOP/clk x 2.07 GHz (derived, no measured FP64 peak)",
-                    "traffic": None}
-        else:
-            achieved = pd["bytes"] / max(pd["timed_launches"], 1) / launch_s / 1e9
-            peak = peaks.get("hbm_gbs", 6800.0)
-            roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                    "traffic": None}
-        total_ms = sum(v["ms"] for v in prof.values())
-        shares = {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if v["ms"] > 0}
+        value = world * args.steps / elapsed
+        total_ms = sum(v["ms"] for v in prof.values() if isinstance(v, dict))
+        shares = {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if isinstance(v, dict) and v["ms"] > 0}
+        total64 = sum(v["ms"] for v in prof64.values() if isinstance(v, dict))
+        shares64 = {k: round(v["ms"] / total64, 4) for k, v in prof64.items() if isinstance(v, dict) and v["ms"] > 0}
         apply_gbs = (prof["apply"]["bytes"] / (prof["apply"]["ms"] / 1e3) / 1e9) if prof["apply"]["ms"] > 0 else None
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -283,19 +345,22 @@ def run_ours(args, rank, world, local_rank):
         result = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 storage; f64 Householder panels and Jacobi SVD; double-float (2 x f32) updates",
             "data": "synthetic", "config": config_dict(w),
-            "roofline": roof,
+            "roofline": roofline(prof, True, peaks),
             "kernel_shares": shares,
+            "fp64": {"value": world * args.steps / el64, "unit": "steps/s", "ms_per_step": el64 / args.steps * 1e3,
+                     "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},
+            "mixed_vs_fp64_error": err,
             "apply_gbs": apply_gbs,
+            "svd_sweeps_per_svd": prof["svd"].get("sweeps", 0) / max(1, prof["svd"].get("count", 0)),
             "cpu_baseline": cpu,
             "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s",
                     "h2d_bytes_per_step": int(nd * 8), "d2h_bytes_per_step": int(out_bytes)},
-            "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "gpu_launches": int(sum(v["launches"] for v in prof.values() if isinstance(v, dict))),
             "clocks": clocks.summary(),
         }
-    ctx.tt_free(t)
-    ctx.close()
     return result
 
 
@@ -306,6 +371,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error-check", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

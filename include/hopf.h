@@ -68,15 +68,19 @@ typedef struct {
                   /* hopf_init_gaussian to sqrt(36.8 / min_k C0_kk)       */
   double tol;     /* relative rounding tolerance used by hopf_step        */
   int rank_cap;   /* rank cap used by hopf_step                           */
-  int precision;  /* HOPF_FP64 (HOPF_MIXED is rejected with HOPF_EINVAL)  */
+  int precision;  /* HOPF_FP64: every step in FP64.  HOPF_MIXED: the     */
+                  /* Householder panels (reflectors, T factors) and the   */
+                  /* Jacobi SVD that sets the ranks stay FP64; trailing   */
+                  /* QR updates, Q applications and merge products run in */
+                  /* FP32 and are added to FP64 storage as corrections.   */
   int nonlinear;  /* 1: full Burgers generator; 0: drop the (i/2) D1 term */
 } hopf_params;
 
 /* ---- context ------------------------------------------------------------ */
 
 /* Creates a context bound to `stream` (cudaStream_t or NULL) on the current
- * device.  `p` is copied.  Errors: HOPF_EINVAL (d < 3, n < 4 or odd,
- * rank_cap < 1, tol < 0, precision not HOPF_FP64), HOPF_ENOMEM, HOPF_ECUDA. */
+ * device.  `p` is copied.  Errors: HOPF_EINVAL (d < 3 or > 64, n < 4 or odd,
+ * rank_cap < 1, tol < 0, unknown precision), HOPF_ENOMEM, HOPF_ECUDA. */
 hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out);
 void hopf_destroy(hopf_ctx* ctx);
 /* Message of the last failed call on ctx ("" if none).  Owned by ctx. */

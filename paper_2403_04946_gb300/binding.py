@@ -132,10 +132,11 @@ class Context:
     L: float = 0.0
     nonlinear: bool = True
     stream: int | None = None
+    precision: int = HOPF_FP64
 
     def __post_init__(self):
         self.lib = load()
-        p = HopfParams(self.d, self.n, self.nu, self.L, self.tol, self.rank_cap, HOPF_FP64,
+        p = HopfParams(self.d, self.n, self.nu, self.L, self.tol, self.rank_cap, int(self.precision),
                        1 if self.nonlinear else 0)
         h = C.c_void_p()
         st = self.lib.hopf_create(C.byref(p), C.c_void_p(self.stream) if self.stream else None, C.byref(h))

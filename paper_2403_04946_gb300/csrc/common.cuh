@@ -32,6 +32,61 @@ HD cplx cinv(cplx a) {
   return mk(a.x * s, -a.y * s);
 }
 
+// Single-precision complex (mixed-precision trailing updates and products).
+typedef float2 cplxf;
+HD cplxf mkf(float re, float im) { return make_float2(re, im); }
+HD cplxf tof(cplx a) { return make_float2((float)a.x, (float)a.y); }
+HD cplx tod(cplxf a) { return make_double2((double)a.x, (double)a.y); }
+// acc + a * b
+DV cplxf cfmaf(cplxf a, cplxf b, cplxf acc) {
+  return mkf(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+// acc + conj(a) * b
+DV cplxf cfmacf(cplxf a, cplxf b, cplxf acc) {
+  return mkf(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+
+// Double-float arithmetic: a value is hi + lo with hi, lo in FP32 (about 48
+// significant bits).  Used by the mixed-precision trailing updates: the FP32
+// pipe is 64 times the FP64 pipe on this GPU, so ~13 FP32 operations per
+// real multiply-add still beat one FP64 FMA by a wide margin.
+struct df2 {   // complex double-float: (re.hi, im.hi, re.lo, im.lo)
+  float rh, ih, rl, il;
+};
+HD df2 df_zero() { return df2{0.f, 0.f, 0.f, 0.f}; }
+HD df2 df_from(cplx a) {
+  const float rh = (float)a.x, ih = (float)a.y;
+  return df2{rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih)};
+}
+HD cplx df_to(df2 a) { return make_double2((double)a.rh + (double)a.rl, (double)a.ih + (double)a.il); }
+// (hi, lo) += a * b for double-float reals a = (ah, al), b = (bh, bl):
+// exact product of the high parts (TwoProduct with an FMA), exact sum
+// (TwoSum), the low-order cross terms added to lo.
+DV void df_mac(float& hi, float& lo, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  const float pe = fmaf(ah, bh, -p);
+  const float cross = fmaf(ah, bl, al * bh);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float se = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += se + pe + cross;
+}
+// acc += conj(a) * b
+DV void df_cmac_conj(df2& acc, const df2& a, const df2& b) {
+  df_mac(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+  df_mac(acc.rh, acc.rl, a.ih, a.il, b.ih, b.il);
+  df_mac(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+  df_mac(acc.ih, acc.il, -a.ih, -a.il, b.rh, b.rl);
+}
+// acc += a * b
+DV void df_cmac(df2& acc, const df2& a, const df2& b) {
+  df_mac(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+  df_mac(acc.rh, acc.rl, -a.ih, -a.il, b.ih, b.il);
+  df_mac(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+  df_mac(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
+}
+
 // Sum over a warp (all 32 lanes active).
 DV double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -40,6 +95,10 @@ DV double warp_sum(double v) {
 DV cplx warp_sum(cplx v) {
   v.x = warp_sum(v.x);
   v.y = warp_sum(v.y);
+  return v;
+}
+DV float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 

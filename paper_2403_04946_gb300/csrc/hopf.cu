@@ -110,6 +110,10 @@ hopf_status fail(hopf_ctx* c, hopf_status st, const char* fmt, ...) {
     }                                                                               \
   } while (0)
 
+// Mixed precision: FP32 trailing updates and products in QR / apply-Q /
+// merges; FP64 Householder panels and Jacobi SVD.
+#define MIXED_FLAG (ctx->p.precision == HOPF_MIXED ? 1 : 0)
+
 #define TRY(expr)                        \
   do {                                   \
     hopf_status s_ = (expr);             \
@@ -246,13 +250,23 @@ hopf_status coop_reserve(hopf_ctx* ctx, int kcap) {
   hk::CoopWs& w = ctx->coop;
   cudaFree(w.pc);
   cudaFree(w.wfin);
+  cudaFree(w.colnorm);
+  cudaFree(w.colver);
+  cudaFree(w.pairchk);
   w.pc = nullptr;
   w.wfin = nullptr;
+  w.colnorm = nullptr;
+  w.colver = nullptr;
+  w.pairchk = nullptr;
   const int G = hk::dev_info().sm_count;
   w.pc_elems = (size_t)G * 32 * (size_t)(kcap + 64);
   w.wfin_elems = (size_t)32 * (size_t)(kcap + 64);
   CK(dalloc(&w.pc, w.pc_elems));
   CK(dalloc(&w.wfin, w.wfin_elems));
+  CK(dalloc(&w.colnorm, (size_t)kcap));
+  CK(dalloc(&w.colver, (size_t)kcap));
+  CK(dalloc(&w.pairchk, (size_t)kcap * kcap));
+  w.jac_cap = kcap;
   ctx->coop_kcap = kcap;
   return HOPF_OK;
 }
@@ -382,14 +396,14 @@ hopf_status orth_sweep(hopf_ctx* ctx, const hopf_tt* t, std::vector<int>& p, std
   LAUNCH(HOPF_K_SUM, 0, 32.0 * r[d - 1] * n, 1, hk::conj_transpose(t->cores[d - 1], r[d - 1], r[d - 1], n, w.B[d - 1], n, ctx->stream));
   for (int c = d - 1; c >= 1; --c) {
     const int m = n * p[c + 1], k = r[c];
-    LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1, hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream));
+    LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1, hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream, MIXED_FLAG));
     p[c] = std::min(m, k);
     // merge L_c = R_c^H into core c-1
     const int rl = r[c - 1];
     if (c - 1 >= 1) {
-      LAUNCH(HOPF_K_GEMM, arh_flops((double)rl * n, k, p[c]), 0, 1, hk::gemm_a_rh(t->cores[c - 1], rl * n, rl * n, k, w.B[c], m, p[c], w.B[c - 1], n * p[c], 1, rl, n, ctx->stream));
+      LAUNCH(HOPF_K_GEMM, arh_flops((double)rl * n, k, p[c]), 0, 1, hk::gemm_a_rh(t->cores[c - 1], rl * n, rl * n, k, w.B[c], m, p[c], w.B[c - 1], n * p[c], 1, rl, n, ctx->stream, MIXED_FLAG));
     } else {
-      LAUNCH(HOPF_K_GEMM, arh_flops(n, k, p[1]), 0, 1, hk::gemm_a_rh(t->cores[0], n, n, k, w.B[1], m, p[1], w.B[0], n, 0, 1, n, ctx->stream));
+      LAUNCH(HOPF_K_GEMM, arh_flops(n, k, p[1]), 0, 1, hk::gemm_a_rh(t->cores[0], n, n, k, w.B[1], m, p[1], w.B[0], n, 0, 1, n, ctx->stream, MIXED_FLAG));
     }
   }
   LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::frob2(w.B[0], n, n, p[1], ctx->d_dbl, ctx->stream));
@@ -423,12 +437,12 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
       const int mc = n * p[c + 1];
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::init_sh_pad(w.Sb, rho[c], rho[c], p[c], t->cores[c], mc, mc, ctx->stream));
       LAUNCH(HOPF_K_APPLYQ, applyq_flops(mc, rho[c], p[c]), 0, 1, hk::ormqr(w.B[c], mc, mc, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c],
-                   t->cores[c], mc, rho[c], ctx->coop, ctx->stream));
+                   t->cores[c], mc, rho[c], ctx->coop, ctx->stream, MIXED_FLAG));
       LAUNCH(HOPF_K_SUM, 0, 32.0 * mc * rho[c], 1, hk::conj_transpose(t->cores[c], mc, mc, rho[c], w.W1, rho[c], ctx->stream));
       Z = w.W1;
     }
     int nb2 = 32;
-    LAUNCH(HOPF_K_QR, qr_flops(Mrows, cols), 0, 1, hk::geqrf(Z, Mrows, Mrows, cols, w.tau2, w.T2, &nb2, ctx->coop, ctx->stream));
+    LAUNCH(HOPF_K_QR, qr_flops(Mrows, cols), 0, 1, hk::geqrf(Z, Mrows, Mrows, cols, w.tau2, w.T2, &nb2, ctx->coop, ctx->stream, MIXED_FLAG));
     const int pp = std::min(Mrows, cols);
     LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::extract_r(Z, Mrows, pp, cols, w.Rb, pp, ctx->stream));
     const int forced_c = forced ? forced[c + 1] : 0;
@@ -478,7 +492,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     } else {
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::gather_u(w.Jb, pp, pp, w.perm, w.sig, 0, rnew, t->cores[c], Mrows, Mrows, w.Ub, pp, ctx->stream));
     }
-    LAUNCH(HOPF_K_APPLYQ, applyq_flops(Mrows, rnew, pp), 0, 1, hk::ormqr(Z, Mrows, Mrows, pp, w.tau2, w.T2, nb2, t->cores[c], Mrows, rnew, ctx->coop, ctx->stream));
+    LAUNCH(HOPF_K_APPLYQ, applyq_flops(Mrows, rnew, pp), 0, 1, hk::ormqr(Z, Mrows, Mrows, pp, w.tau2, w.T2, nb2, t->cores[c], Mrows, rnew, ctx->coop, ctx->stream, MIXED_FLAG));
     // S = U_rho^H R (rho x cols)
     LAUNCH(HOPF_K_GEMM, 8.0 * rnew * pp * cols, 0, 1, hk::gemm_uh_r(w.Ub, pp, rnew, pp, w.Rb, pp, cols, w.Sb, rnew, ctx->stream));
   }
@@ -487,7 +501,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     const int c = d - 1;
     LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::init_sh_pad(w.Sb, rho[c], rho[c], p[c], w.W1, n, n, ctx->stream));
     LAUNCH(HOPF_K_APPLYQ, applyq_flops(n, rho[c], p[c]), 0, 1, hk::ormqr(w.B[c], n, n, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c], w.W1, n, rho[c],
-                 ctx->coop, ctx->stream));
+                 ctx->coop, ctx->stream, MIXED_FLAG));
     LAUNCH(HOPF_K_SUM, 0, 32.0 * n * rho[c], 1, hk::conj_transpose(w.W1, n, n, rho[c], t->cores[c], rho[c], ctx->stream));
   }
   rho[d] = 1;
@@ -536,14 +550,14 @@ hopf_status orth_sweep_apply(hopf_ctx* ctx, const hopf_tt* X, std::vector<int>& 
   for (int c = d - 1; c >= 1; --c) {
     const int m = n * p[c + 1], k = 6 * r[c];
     LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1,
-           hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream));
+           hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream, MIXED_FLAG));
     p[c] = std::min(m, k);
     const int rl = r[c - 1];
     const size_t blk = (size_t)rl * n * p[c];
     for (int be = 0; be < 6; ++be) {
       LAUNCH(HOPF_K_GEMM, rblk_flops((double)rl * n, r[c], p[c], be * r[c]), 0, 1,
              hk::gemm_a_rblk_h(X->cores[c - 1], rl * n, rl * n, r[c], w.B[c], m, be * r[c], p[c], w.W1 + be * blk, rl * n,
-                               ctx->stream));
+                               ctx->stream, MIXED_FLAG));
     }
     const int Al = (c - 1 == 0) ? 1 : 6;
     const int kind = (c - 1 == 0) ? 0 : 1;
@@ -704,7 +718,7 @@ hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out) {
   if (!p || !out) return HOPF_EINVAL;
   *out = nullptr;
   if (p->d < 3 || p->d > 64 || p->n < 4 || (p->n & 1) || p->rank_cap < 1 || !(p->tol >= 0.0) ||
-      p->precision != HOPF_FP64 || !(p->nu >= 0.0))
+      (p->precision != HOPF_FP64 && p->precision != HOPF_MIXED) || !(p->nu >= 0.0))
     return HOPF_EINVAL;
   hopf_ctx* ctx = new (std::nothrow) hopf_ctx();
   if (!ctx) return HOPF_ENOMEM;
@@ -758,6 +772,7 @@ void hopf_destroy(hopf_ctx* ctx) {
   cudaFree(w.sig); cudaFree(w.perm);
   cudaFree(ctx->coop.bar); cudaFree(ctx->coop.pr); cudaFree(ctx->coop.pc);
   cudaFree(ctx->coop.wfin); cudaFree(ctx->coop.scal); cudaFree(ctx->coop.counters);
+  cudaFree(ctx->coop.colnorm); cudaFree(ctx->coop.colver); cudaFree(ctx->coop.pairchk);
   cudaFree(ctx->d_coef); cudaFree(ctx->d_blocks); cudaFree(ctx->d_agrid);
   cudaFree(ctx->d_dbl); cudaFree(ctx->d_int); cudaFree(ctx->d_terms);
   for (void* p : ctx->extra) cudaFree(p);

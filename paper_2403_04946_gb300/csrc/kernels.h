@@ -26,18 +26,26 @@ struct CoopWs {
   size_t wfin_elems;
   cplx* scal;       // [8] scalars
   int* counters;    // [64] sweep counters
+  // one-sided Jacobi state: squared column norms, column versions, and the
+  // versions at which each pair was last found orthogonal (jac_cap columns)
+  double* colnorm;
+  unsigned int* colver;
+  unsigned long long* pairchk;
+  int jac_cap;
 };
 
 // Householder QR of the column-major m x k matrix A (lda >= m), in place:
 // R on and above the diagonal, reflector tails below, tau[min(m,k)], and the
 // compact-WY T factor of every panel of width `nb` in T (npanel x nb x nb).
 // Returns the panel width used through *nb_out.
+// mixed != 0: panels (reflectors, T factors) in FP64, trailing products in
+// FP32 added to the FP64 matrix as corrections.
 cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_out,
-                  const CoopWs& ws, cudaStream_t s);
+                  const CoopWs& ws, cudaStream_t s, int mixed = 0);
 // C <- Q C with Q = H_0 H_1 ... H_{p-1} from geqrf (A, lda, m, p, tau, T, nb);
 // C is m x q column-major (ldc).
 cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* T,
-                  int nb, cplx* C, int ldc, int q, const CoopWs& ws, cudaStream_t s);
+                  int nb, cplx* C, int ldc, int q, const CoopWs& ws, cudaStream_t s, int mixed = 0);
 
 // One-sided Jacobi SVD of the nr x nc column-major matrix M (ldm), in place:
 // on exit the columns of M are U_i * sigma_i (any order); if accumJ, J
@@ -75,11 +83,11 @@ cudaError_t extract_r(const cplx* A, int lda, int p, int k, cplx* R, int ldr, cu
 // "H^H layout": row index i_all = i + rl * mm (i < rl), column j ->
 // B[(mm + n * j) + ldb * i] = conj(C[i_all, j]).
 cudaError_t gemm_a_rh(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int N,
-                      cplx* C, int ldc, int mode, int rl, int n, cudaStream_t s);
+                      cplx* C, int ldc, int mode, int rl, int n, cudaStream_t s, int mixed = 0);
 // C[M x N] = A[M x K] * (columns coff..coff+K of R)^H, R upper trapezoidal
 // (ldr): C[i, q] = sum_t A[i, t] conj(R[q, coff + t]) over q <= coff + t.
 cudaError_t gemm_a_rblk_h(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int coff,
-                          int N, cplx* C, int ldc, cudaStream_t s);
+                          int N, cplx* C, int ldc, cudaStream_t s, int mixed = 0);
 // C[M x N] = U[:, perm[0..M)]^H-gathered * R: C[i, j] = sum_t conj(U[t, i]) R[t, j].
 cudaError_t gemm_uh_r(const cplx* U, int ldu, int M, int K, const cplx* R, int ldr, int N,
                       cplx* C, int ldc, cudaStream_t s);

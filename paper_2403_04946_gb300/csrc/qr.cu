@@ -90,6 +90,86 @@ __device__ void update_x(const cplx* P, int R, int r0, int lo, int hi, int nbk, 
   }
 }
 
+// Mixed-precision versions: the panel V in shared memory as double-float
+// values (hi, lo in FP32, same 16 bytes per complex as FP64), X stored in
+// FP64; products and sums in double-float arithmetic on the FP32 pipe,
+// partials handed on in FP64, and the update added to X in FP64.
+template <int NB>
+__device__ void partial_vhx_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
+                              const cplx* X, int ldx, int ncol, cplx* out) {
+  // 16 reflectors per pass over the rows keep the double-float accumulators
+  // in registers
+  constexpr int CH = NB < 16 ? NB : 16;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = w; l < ncol; l += nw) {
+    const cplx* x = X + (size_t)ldx * l;
+    for (int s0 = 0; s0 < nbk; s0 += CH) {
+      df2 acc[CH];
+#pragma unroll
+      for (int s = 0; s < CH; ++s) acc[s] = df_zero();
+      cplx xn = (lo + lane < hi) ? x[lo + lane] : mk(0, 0);
+      for (int i = lo + lane; i < hi; i += 32) {
+        const df2 xi = df_from(xn);
+        if (i + 32 < hi) xn = x[i + 32];
+        const df2* pv = P + (i - r0) + (size_t)s0 * R;
+#pragma unroll
+        for (int s = 0; s < CH; ++s)
+          if (s0 + s < nbk) df_cmac_conj(acc[s], pv[(size_t)s * R], xi);
+      }
+#pragma unroll
+      for (int s = 0; s < CH; ++s) {
+        if (s0 + s < nbk) {
+          cplx v = warp_sum(df_to(acc[s]));
+          if (lane == 0) out[s0 + s + (size_t)nbk * l] = v;
+        }
+      }
+    }
+  }
+}
+
+template <int NB>
+__device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk, cplx* X,
+                           int ldx, int ncol, const cplx* w2) {
+  // the column's coefficients -W2[:, l] live in shared memory (every lane
+  // reads the same one: broadcast), the running update in registers
+  __shared__ df2 wsh[8][kNbMax];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l0 = 0; l0 < ncol; l0 += nw) {
+    const int l = l0 + w;
+    if (l < ncol && lane < nbk) {
+      const cplx wv = ld_cg(w2 + lane + (size_t)nbk * l);
+      wsh[w][lane] = df_from(mk(-wv.x, -wv.y));
+    }
+    __syncwarp();
+    if (l < ncol) {
+      cplx* x = X + (size_t)ldx * l;
+      cplx xn = (lo + lane < hi) ? x[lo + lane] : mk(0, 0);
+      for (int i = lo + lane; i < hi; i += 32) {
+        const cplx xi = xn;
+        if (i + 32 < hi) xn = x[i + 32];
+        const df2* pv = P + (i - r0);
+        df2 dlt = df_zero();
+#pragma unroll 8
+        for (int s = 0; s < NB; ++s)
+          if (s < nbk) df_cmac(dlt, pv[(size_t)s * R], wsh[w][s]);
+        x[i] = cadd(xi, df_to(dlt));
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Rewrites each of the first n FP64 complex values of buf as a double-float
+// value in the same 16 bytes.
+__device__ void to_df_in_place(cplx* buf, int n) {
+  df2* out = reinterpret_cast<df2*>(buf);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const cplx v = buf[e];
+    out[e] = df_from(v);
+  }
+  __syncthreads();
+}
+
 // Sum over the G per-CTA partials of entry e (stride pstride) by one warp.
 __device__ __forceinline__ cplx reduce_partials(const cplx* pc, size_t pstride, int G, size_t e) {
   const int lane = threadIdx.x & 31;
@@ -98,7 +178,7 @@ __device__ __forceinline__ cplx reduce_partials(const cplx* pc, size_t pstride, 
   return warp_sum(acc);
 }
 
-template <int NB>
+template <int NB, bool MIXED>
 __global__ void __launch_bounds__(kQrThreads, 1)
 geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
              CoopWs ws) {
@@ -239,8 +319,18 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
             if (lane == 0) out[s + (size_t)nbk * l] = v;
           }
       }
-      if (nt > 0)
-        partial_vhx<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, out + (size_t)nbk * nbk);
+      __syncthreads();
+      if (nt > 0) {
+        if (MIXED) {
+          // the reflector Gram above stays FP64 (it builds T); the trailing
+          // products run in double-float arithmetic on the FP32 pipe
+          to_df_in_place(P, nbk * R);
+          partial_vhx_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt,
+                            out + (size_t)nbk * nbk);
+        } else {
+          partial_vhx<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, out + (size_t)nbk * nbk);
+        }
+      }
     }
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
@@ -296,12 +386,18 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     // S4: trailing update over this CTA's rows
-    if (nt > 0) update_x<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, ws.wfin + (size_t)nbk * nbk);
+    if (nt > 0) {
+      if (MIXED)
+        update_x_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt,
+                       ws.wfin + (size_t)nbk * nbk);
+      else
+        update_x<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, ws.wfin + (size_t)nbk * nbk);
+    }
     __syncthreads();
   }
 }
 
-template <int NB>
+template <int NB, bool MIXED>
 __global__ void __launch_bounds__(kQrThreads, 1)
 ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx* C, int ldc,
              int q, int R, CoopWs ws) {
@@ -324,12 +420,16 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
         if (i < j0 + t) v = mk(0, 0);
         else if (i == j0 + t) v = mk(1, 0);
         else v = A[i + (size_t)lda * (j0 + t)];
-        P[(size_t)t * R + (i - r0)] = v;
+        if (MIXED) reinterpret_cast<df2*>(P)[(size_t)t * R + (i - r0)] = df_from(v);
+        else P[(size_t)t * R + (i - r0)] = v;
       }
     // T of a panel is stored packed (leading dimension nbk).
     for (int e = tid; e < nbk * nbk; e += blockDim.x) Ts[e] = Tg[(size_t)panel * nb * nb + e];
     __syncthreads();
-    partial_vhx<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
+    if (MIXED)
+      partial_vhx_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
+    else
+      partial_vhx<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     // reduce and multiply by T: W2 = T W (apply Q, not Q^H)
@@ -353,7 +453,10 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
     }
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
-    update_x<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.wfin);
+    if (MIXED)
+      update_x_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, C, ldc, q, ws.wfin);
+    else
+      update_x<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.wfin);
     __syncthreads();
     // No barrier needed here: the next panel writes wfin only after its
     // first grid_sync, which every CTA reaches after finishing this update.
@@ -365,7 +468,7 @@ static void pick_layout(int m, int* G, int* R, int* nb, size_t* smem) {
   int g = std::max(1, std::min(di.sm_count, (m + 63) / 64));
   int r = (m + g - 1) / g;
   int b = kNbMax;
-  const size_t lim = (size_t)di.max_smem_optin - 4096;
+  const size_t lim = (size_t)di.max_smem_optin - 8192;  // static shared memory too
   while (b > 4 && QrSmem::bytes(r, b) > lim) b >>= 1;
   *G = g;
   *R = r;
@@ -374,7 +477,7 @@ static void pick_layout(int m, int* G, int* R, int* nb, size_t* smem) {
 }
 
 cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_out,
-                  const CoopWs& ws, cudaStream_t s) {
+                  const CoopWs& ws, cudaStream_t s, int mixed) {
   if (m <= 0 || k <= 0) return cudaSuccess;
   int G, R, nb;
   size_t smem;
@@ -383,9 +486,15 @@ cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_ou
     return cudaErrorInvalidValue;
   *nb_out = nb;
   void* fn;
-  if (nb == 32) fn = (void*)geqrf_kernel<32>;
-  else if (nb == 16) fn = (void*)geqrf_kernel<16>;
-  else fn = (void*)geqrf_kernel<8>;
+  if (mixed) {
+    if (nb == 32) fn = (void*)geqrf_kernel<32, true>;
+    else if (nb == 16) fn = (void*)geqrf_kernel<16, true>;
+    else fn = (void*)geqrf_kernel<8, true>;
+  } else {
+    if (nb == 32) fn = (void*)geqrf_kernel<32, false>;
+    else if (nb == 16) fn = (void*)geqrf_kernel<16, false>;
+    else fn = (void*)geqrf_kernel<8, false>;
+  }
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CoopWs w = ws;
@@ -396,7 +505,7 @@ cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_ou
 }
 
 cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* T,
-                  int nb, cplx* C, int ldc, int q, const CoopWs& ws, cudaStream_t s) {
+                  int nb, cplx* C, int ldc, int q, const CoopWs& ws, cudaStream_t s, int mixed) {
   (void)tau;
   if (m <= 0 || p <= 0 || q <= 0) return cudaSuccess;
   int G, R, nb2;
@@ -409,9 +518,15 @@ cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const c
   if ((size_t)G * nb * (size_t)q > ws.pc_elems || (size_t)nb * q > ws.wfin_elems)
     return cudaErrorInvalidValue;
   void* fn;
-  if (nb == 32) fn = (void*)ormqr_kernel<32>;
-  else if (nb == 16) fn = (void*)ormqr_kernel<16>;
-  else fn = (void*)ormqr_kernel<8>;
+  if (mixed) {
+    if (nb == 32) fn = (void*)ormqr_kernel<32, true>;
+    else if (nb == 16) fn = (void*)ormqr_kernel<16, true>;
+    else fn = (void*)ormqr_kernel<8, true>;
+  } else {
+    if (nb == 32) fn = (void*)ormqr_kernel<32, false>;
+    else if (nb == 16) fn = (void*)ormqr_kernel<16, false>;
+    else fn = (void*)ormqr_kernel<8, false>;
+  }
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CoopWs w = ws;

@@ -41,29 +41,38 @@ template <int RPT>
 __global__ void __launch_bounds__(kJacThreads, 1)
 jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, double tol,
               int max_sweeps, const double* eps_hat, CoopWs ws) {
-  __shared__ double red[2][4][4];  // [group][warp][al, be, ga.x, ga.y]
+  __shared__ double red[2][4][2];  // [group][warp][ga.x, ga.y]
   __shared__ double fro_red[32];
   const int G = gridDim.x, g = blockIdx.x;
   const int grp = threadIdx.x / kGroup, gt = threadIdx.x % kGroup;
   const int lane = gt & 31, gw = gt >> 5;
+  const int wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int N = nc + (nc & 1);
   const int npairs = N / 2;
   GridSync gs{ws.bar, 0u};
+  double* colnorm = ws.colnorm;
+  unsigned int* colver = ws.colver;
+  unsigned long long* pairchk = ws.pairchk;
 
-  // ||M||_F^2 (invariant under the rotations), reduced over all CTAs
-  {
-    double s = 0.0;
-    for (size_t e = (size_t)g * blockDim.x + threadIdx.x; e < (size_t)nr * nc; e += (size_t)G * blockDim.x) {
-      const size_t i = e % nr, j = e / nr;
-      s += cabs2(M[i + (size_t)ldm * j]);
+  // exact squared column norms (also re-done at the start of every sweep),
+  // column versions zeroed, no pair marked orthogonal yet
+  auto column_norms = [&]() {
+    for (int c = g * nwarp + wid; c < nc; c += G * nwarp) {
+      const cplx* a = M + (size_t)ldm * c;
+      double s = 0.0;
+      for (int row = lane; row < nr; row += 32) s += cabs2(__ldcg(a + row));
+      s = warp_sum(s);
+      if (lane == 0) colnorm[c] = s;
     }
-    s = block_sum(s, fro_red);
-    if (threadIdx.x == 0) ws.pr[g] = s;
-  }
+  };
+  column_norms();
+  for (int c = g * blockDim.x + threadIdx.x; c < nc; c += G * blockDim.x) colver[c] = 0u;
+  for (size_t e = (size_t)g * blockDim.x + threadIdx.x; e < (size_t)nc * nc; e += (size_t)G * blockDim.x)
+    pairchk[e] = ~0ull;
   grid_sync(gs);
   if (grid_failed(ws.bar)) return;
   double fro2 = 0.0;
-  for (int gg = 0; gg < G; ++gg) fro2 += __ldcg(ws.pr + gg);
+  for (int c = 0; c < nc; ++c) fro2 += __ldcg(colnorm + c);
   // A pair is left alone once its smaller column is below theta: a column of
   // norm theta moves any other column (hence any kept singular vector) by at
   // most theta, and the discarded tail is the Frobenius norm of the columns
@@ -79,11 +88,19 @@ jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, do
   int sweep = 0;
   bool converged = false;
   for (; sweep < max_sweeps; ++sweep) {
+    if (sweep > 0) {
+      // the rotations below update the norms incrementally; start each sweep
+      // from exact ones, so the final (rotation-free) sweep tests exactly
+      column_norms();
+      grid_sync(gs);
+      if (grid_failed(ws.bar)) return;
+    }
     for (int r = 0; r < N - 1; ++r) {
       for (int base = 2 * g; base < npairs; base += 2 * G) {
         const int q = base + grp;
         int i = 0, j = 0;
         bool active = q < npairs;
+        unsigned long long key = 0ull;
         if (active) {
           pair_of(r, q, N, &i, &j);
           active = (i < nc && j < nc);
@@ -93,8 +110,17 @@ jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, do
             j = t;
           }
         }
-        cplx x[RPT], y[RPT];
         double al = 0.0, be = 0.0;
+        if (active) {
+          // skip the pair if neither column changed since it was last found
+          // orthogonal (no column loads at all)
+          key = ((unsigned long long)__ldcg(colver + i) << 32) | __ldcg(colver + j);
+          if (__ldcg(pairchk + (size_t)i * nc + j) == key) active = false;
+          // read before the group's barriers: thread 0 rewrites them below
+          al = __ldcg(colnorm + i);
+          be = __ldcg(colnorm + j);
+        }
+        cplx x[RPT], y[RPT];
         cplx ga = mk(0, 0);
         if (active) {
           const cplx* ai = M + (size_t)ldm * i;
@@ -106,35 +132,24 @@ jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, do
             y[u] = (row < nr) ? __ldcg(aj + row) : mk(0, 0);
           }
 #pragma unroll
-          for (int u = 0; u < RPT; ++u) {
-            al += cabs2(x[u]);
-            be += cabs2(y[u]);
-            ga = cfmac(x[u], y[u], ga);
-          }
+          for (int u = 0; u < RPT; ++u) ga = cfmac(x[u], y[u], ga);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
         ga = warp_sum(ga);
         if (lane == 0) {
-          red[grp][gw][0] = al;
-          red[grp][gw][1] = be;
-          red[grp][gw][2] = ga.x;
-          red[grp][gw][3] = ga.y;
+          red[grp][gw][0] = ga.x;
+          red[grp][gw][1] = ga.y;
         }
         __syncthreads();
-        al = be = 0.0;
         ga = mk(0, 0);
 #pragma unroll
         for (int w = 0; w < kGroup / 32; ++w) {
-          al += red[grp][w][0];
-          be += red[grp][w][1];
-          ga.x += red[grp][w][2];
-          ga.y += red[grp][w][3];
+          ga.x += red[grp][w][0];
+          ga.y += red[grp][w][1];
         }
         __syncthreads();
+        if (!active) continue;
         const double gabs = sqrt(cabs2(ga));
-        const bool rot = active && gabs > 0.0 && gabs > tol * sqrt(al) * sqrt(be) &&
-                         fmin(al, be) > negl2;
+        const bool rot = gabs > 0.0 && gabs > tol * sqrt(al) * sqrt(be) && fmin(al, be) > negl2;
         if (rot) {
           const double zeta = (be - al) / (2.0 * gabs);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -163,7 +178,16 @@ jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, do
               jj[row] = mk(s * xv.x + c * yv.x, s * xv.y + c * yv.y);
             }
           }
-          if (gt == 0) atomicAdd(ws.counters + (sweep & 31), 1);
+          if (gt == 0) {
+            // norms of the rotated pair (exact in exact arithmetic)
+            colnorm[i] = fmax(al - t * gabs, 0.0);
+            colnorm[j] = be + t * gabs;
+            colver[i] += 1u;
+            colver[j] += 1u;
+            atomicAdd(ws.counters + (sweep & 31), 1);
+          }
+        } else if (gt == 0) {
+          pairchk[(size_t)i * nc + j] = key;
         }
       }
       grid_sync(gs);
@@ -193,6 +217,7 @@ __global__ void init_identity_kernel(cplx* J, int ldj, int nc) {
 cudaError_t jacobi_svd(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ,
                        const double* eps_hat, int init_j, const CoopWs& ws, cudaStream_t s) {
   if (nc <= 0 || nr <= 0) return cudaSuccess;
+  if (nc > ws.jac_cap) return cudaErrorInvalidValue;
   if (accumJ && init_j) {
     init_identity_kernel<<<(nc * nc + 255) / 256, 256, 0, s>>>(J, ldj, nc);
   }

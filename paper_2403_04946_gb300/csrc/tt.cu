@@ -556,21 +556,71 @@ __global__ void __launch_bounds__(256) gemm_kernel(LA la, LB lb, ST st, int M, i
     for (int b = 0; b < 4; ++b) st(i0 + tx + 16 * a, j0 + ty + 16 * b, acc[a][b]);
 }
 
+// Mixed-precision variant: operands split into double-float (hi, lo) when
+// staged, products and sums in double-float arithmetic on the FP32 pipe,
+// result stored in FP64.
+template <class LA, class LB, class ST>
+__global__ void __launch_bounds__(256) gemm_kernel_f(LA la, LB lb, ST st, int M, int N, int K) {
+  __shared__ df2 As[GK][GT + 1];
+  __shared__ df2 Bs[GK][GT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  df2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = df_zero();
+  for (int t0 = 0; t0 < K; t0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+      const int r = e % GT, kk = e / GT;
+      As[kk][r] = df_from(la(i0 + r, t0 + kk));
+      const int kk2 = e % GK, cc = e / GK;
+      Bs[kk2][cc] = df_from(lb(t0 + kk2, j0 + cc));
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      df2 av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) df_cmac(acc[a][b], av[a], bv[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) st(i0 + tx + 16 * a, j0 + ty + 16 * b, df_to(acc[a][b]));
+}
+
 cudaError_t gemm_a_rh(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int N,
-                      cplx* C, int ldc, int mode, int rl, int n, cudaStream_t s) {
+                      cplx* C, int ldc, int mode, int rl, int n, cudaStream_t s, int mixed) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
-  gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, 0},
-                                   StoreC{C, ldc, M, N, mode, rl, n}, M, N, K);
+  if (mixed)
+    gemm_kernel_f<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, 0},
+                                       StoreC{C, ldc, M, N, mode, rl, n}, M, N, K);
+  else
+    gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, 0},
+                                     StoreC{C, ldc, M, N, mode, rl, n}, M, N, K);
   return cudaGetLastError();
 }
 
 cudaError_t gemm_a_rblk_h(const cplx* A, int lda, int M, int K, const cplx* R, int ldr, int coff,
-                          int N, cplx* C, int ldc, cudaStream_t s) {
+                          int N, cplx* C, int ldc, cudaStream_t s, int mixed) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
-  gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, coff},
-                                   StoreC{C, ldc, M, N, 0, 1, 1}, M, N, K);
+  if (mixed)
+    gemm_kernel_f<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, coff},
+                                       StoreC{C, ldc, M, N, 0, 1, 1}, M, N, K);
+  else
+    gemm_kernel<<<grid, 256, 0, s>>>(LoadA_N{A, lda, M, K}, LoadB_RH{R, ldr, K, N, coff},
+                                     StoreC{C, ldc, M, N, 0, 1, 1}, M, N, K);
   return cudaGetLastError();
 }
 

@@ -247,3 +247,39 @@ def test_step_parity_mid_size(B):
     want = tt.evaluate(ocores, idx)
     assert rel(got, want) < 1e-10
     assert abs(ctx.tt_norm(t) - tt.norm(ocores)) < 1e-10 * tt.norm(ocores)
+
+
+# ---- mixed precision (FP32 trailing updates, FP64 panels and SVD) ----------
+
+def test_mixed_round_close_to_fp64(B):
+    """One rounding in mixed precision stays within FP32 rounding of the
+    FP64 result (ranks replayed)."""
+    d, n, ranks, tol, cap = 6, 20, [1, 20, 45, 70, 45, 20, 1], 1e-6, 33
+    base = synthetic.random_tt_cores(d, n, [1, 4, 4, 4, 4, 4, 1], seed=7)
+    noise = synthetic.random_tt_cores(d, n, ranks, seed=8, scale=1e-3)
+    x = tt.tt_sum([(1.0, base), (1.0, noise)])
+    want, wranks, _ = tt.round_tt(x, tol, cap)
+    ctx = B.Context(d=d, n=n, nu=0.05, tol=tol, rank_cap=cap, L=3.0, precision=B.HOPF_MIXED)
+    tx = ctx.tt_from_host(x, max_rank=max(tt.ranks(x)))
+    ctx.tt_round(tx, tol, cap, forced_ranks=wranks)
+    err = rel(tt.full(ctx.tt_to_host(tx)), tt.full(want))
+    print(f"mixed rounding rel err {err:.2e}")
+    assert err < 1e-5
+
+
+def test_mixed_step_c1_within_1e6(B):
+    """C1, 20 RK4 steps in mixed precision with the oracle's ranks: relative
+    L2 error to the FP64 oracle <= 1e-6 (the mixed-precision target)."""
+    w, n, m0, C0, L = _c1_state()
+    cores = tt.tt_svd(fullgrid.phi0_grid(m0, C0, n, L), w.tol, w.cap)
+    W = model.mpo_blocks(w.d, n, L, w.nu)
+    bond = model.mpo_bond_dims(w.d)
+    log, oc = [], cores
+    for _ in range(20):
+        oc, _ = tt.rk4_step(oc, w.dt, W, bond, w.tol, w.cap, record=log)
+    ctx = B.Context(d=w.d, n=n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L, precision=B.HOPF_MIXED)
+    t = ctx.tt_from_host(cores, max_rank=w.cap)
+    ctx.hopf_step(t, w.dt, 20, replay=np.array(log))
+    err = rel(tt.full(ctx.tt_to_host(t)), tt.full(oc))
+    print(f"mixed C1 20 steps rel err {err:.2e}")
+    assert err < 1e-6
