@@ -88,6 +88,14 @@ const char* hopf_last_error(const hopf_ctx* ctx);
 /* Sets / reads the a-box half-width L (must be > 0). */
 hopf_status hopf_set_L(hopf_ctx* ctx, double L);
 hopf_status hopf_get_L(const hopf_ctx* ctx, double* L);
+/* Method of the small SVDs of the truncation (App. A, Alg. 4: the SVD of
+ * the triangular factor R of each bond).  HOPF_SVD_AUTO (the default):
+ * square factors through Householder bidiagonalisation, Sturm bisection
+ * and inverse iteration; wide factors by one-sided Jacobi.
+ * HOPF_SVD_JACOBI: one-sided Jacobi for every factor.  Both give the same
+ * truncation up to rounding.  Errors: HOPF_EINVAL (unknown method). */
+enum { HOPF_SVD_AUTO = 0, HOPF_SVD_JACOBI = 1 };
+hopf_status hopf_set_svd_method(hopf_ctx* ctx, int method);
 
 /* ---- model set-up -------------------------------------------------------- */
 

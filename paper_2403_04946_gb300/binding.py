@@ -23,6 +23,7 @@ HOPF_OK, HOPF_EINVAL, HOPF_ENOMEM, HOPF_ECUDA, HOPF_ENUMERIC, HOPF_ETIMEOUT, HOP
 STATUS_NAMES = ["HOPF_OK", "HOPF_EINVAL", "HOPF_ENOMEM", "HOPF_ECUDA", "HOPF_ENUMERIC",
                 "HOPF_ETIMEOUT", "HOPF_ERANKCAP"]
 HOPF_FP64, HOPF_MIXED = 0, 1
+HOPF_SVD_AUTO, HOPF_SVD_JACOBI = 0, 1
 
 # Every symbol include/hopf.h declares, with (restype, argtypes).
 _vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
@@ -33,6 +34,7 @@ SIGNATURES = {
     "hopf_last_error": (C.c_char_p, [_vp]),
     "hopf_set_L": (_i, [_vp, _d]),
     "hopf_get_L": (_i, [_vp, _pd]),
+    "hopf_set_svd_method": (_i, [_vp, _i]),
     "hopf_cell_moments": (_i, [_vp, _i, _pd, _pd, _d, _d, _pd, _pd]),
     "tt_from_host": (_i, [_vp, _pi, _pd, _i, C.POINTER(_vp)]),
     "tt_create": (_i, [_vp, _i, C.POINTER(_vp)]),
@@ -164,6 +166,9 @@ class Context:
     # -- calls ----------------------------------------------------------------
     def hopf_set_L(self, L):
         self._check(self.lib.hopf_set_L(self.h, float(L)))
+
+    def hopf_set_svd_method(self, method):
+        self._check(self.lib.hopf_set_svd_method(self.h, int(method)))
 
     def hopf_get_L(self):
         v = C.c_double()

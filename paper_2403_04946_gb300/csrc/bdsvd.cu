@@ -1,0 +1,633 @@
+// SVD of the small square factor R through bidiagonalisation.
+//
+// The truncation at a bond needs every singular value of the triangular
+// factor R (the discarded tail) and the left singular vectors of the kept
+// ones (App. A, the QR-then-SVD structure of Alg. 4).  Instead of Jacobi
+// rotations (O(n^3) flops per sweep, a dozen sweeps), R is reduced once:
+//
+//  1. Householder bidiagonalisation R = Q B P^H (Golub & Kahan 1965), B real
+//     upper bidiagonal, with the reflector conventions of LAPACK's zgebrd.
+//     One cooperative launch; CTA g keeps the rows r = g (mod G) of R in
+//     shared memory and the CTAs meet once per column (see gebrd_kernel).
+//  2. Singular values of B: eigenvalues of the Golub-Kahan tridiagonal T_GK
+//     (order 2n, zero diagonal, off-diagonals d_1, e_1, d_2, ..., d_n, whose
+//     eigenvalues are +-sigma) by Sturm-count multisection, one warp per
+//     value.  Counts are taken in double-float arithmetic (hi + lo FP32
+//     pair, ~2^-47 relative): a Sturm count is exact for a matrix whose
+//     entries are perturbed by a few units of the working precision, and
+//     the singular values of a bidiagonal move by a relative amount of the
+//     same order under such perturbations (Demmel & Kahan 1990), so every
+//     value, large or small, is found to a relative accuracy of ~1e-13.
+//  3. Left singular vectors of B for the kept values: inverse iteration on
+//     T_GK - sigma I (the eigenvector for +sigma is (v_1, u_1, ..., v_n,
+//     u_n)/sqrt 2), FP64, tridiagonal LU with partial pivoting, modified
+//     Gram-Schmidt inside clusters of close values (as in LAPACK's dstein).
+//     Kept values at the rounding-noise level of R get an orthonormal
+//     completion instead (their vectors are not determined by R).
+//  4. U = Q [u_1 .. u_rho] by applying the left reflectors.
+#include <algorithm>
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace hk {
+
+constexpr int kBdThreads = 256;
+
+DV void house_scalars(cplx alpha, double xnorm2, cplx* tau, cplx* scale, double* beta) {
+  // H^H [alpha; x] = [beta; 0] with H = I - tau v v^H, v = [1; x * scale]
+  if (xnorm2 == 0.0 && alpha.y == 0.0) {
+    *tau = mk(0, 0);
+    *scale = mk(0, 0);
+    *beta = alpha.x;
+    return;
+  }
+  const double an = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+  const double b = (alpha.x >= 0.0) ? -an : an;
+  *tau = mk((b - alpha.x) / b, -alpha.y / b);
+  *scale = cinv(mk(alpha.x - b, alpha.y));
+  *beta = b;
+}
+
+// ---- 1. bidiagonalisation -------------------------------------------------------
+// Column i, with H = I - tau v v^H the left reflector (v_i = 1,
+// v_r = A[r,i] * scale for r > i) and w_c = sum_r conj(v_r) A[r,c]:
+//   w_c = A[i,c] + conj(scale) * sum_{r>i} conj(A[r,i]) A[r,c],
+// so the CTAs exchange only their partial sums over their own rows plus
+// row i (published by its owner) and meet at ONE grid barrier.  After it,
+// every CTA forms the updated row i, A[i,c] - conj(tau) w_c, itself, hence
+// also the right reflector G = I - taup u u^H of that row, and applies
+// both reflectors to its own rows without further synchronisation.  The
+// partial-sum buffers alternate between two halves (a CTA writing column
+// i+1's partials has passed barrier i, so every reader of column i-1's
+// half is done).
+__global__ void __launch_bounds__(kBdThreads, 1)
+gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* tauq, cplx* taup,
+             CoopWs ws) {
+  extern __shared__ __align__(16) unsigned char bd_smem[];
+  cplx* rows = reinterpret_cast<cplx*>(bd_smem);  // nloc x n, row-major
+  cplx* wv = rows + (size_t)nloc * n;            // w_c
+  cplx* nrow = wv + n;                           // updated row i
+  cplx* uv = nrow + n;                           // right reflector u
+  __shared__ double dred[32];
+  __shared__ cplx bc[4];
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const size_t pstride = (size_t)n + 1;
+  GridSync gs{ws.bar, 0u};
+  auto grow = [&](int lr) { return g + lr * G; };
+  auto R = [&](int lr, int c) -> cplx& { return rows[(size_t)lr * n + c]; };
+  const int nact = min(nloc, (n - g + G - 1) / G);  // local rows that exist
+
+  for (int lr = 0; lr < nloc; ++lr) {
+    const int r = grow(lr);
+    for (int c = tid; c < n; c += blockDim.x) R(lr, c) = (r < n) ? A[r + (size_t)lda * c] : mk(0, 0);
+  }
+  __syncthreads();
+
+  for (int i = 0; i < n; ++i) {
+    const int buf = i & 1;
+    cplx* pc = ws.pc + (size_t)buf * G * pstride;
+    double* pr = ws.pr + buf * G;
+    cplx* rowb = ws.wfin + (size_t)buf * n;
+    // first own local row strictly below i (rows of this CTA: g + lr G)
+    const int lr0 = (i + 1 > g) ? (i + 1 - g + G - 1) / G : 0;
+    // (a) partial sums over own rows r > i
+    double sq = 0.0;
+    for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) sq += cabs2(R(lr, i));
+    sq = block_sum(sq, dred);
+    for (int c = i + 1 + tid; c < n; c += blockDim.x) {
+      cplx acc = mk(0, 0);
+      for (int lr = lr0; lr < nact; ++lr) acc = cfmac(R(lr, i), R(lr, c), acc);
+      pc[(size_t)g * pstride + c] = acc;
+    }
+    if (tid == 0) pr[g] = sq;
+    const bool owner = (i % G == g);
+    if (owner) {
+      const int lri = i / G;
+      for (int c = i + tid; c < n; c += blockDim.x) rowb[c] = R(lri, c);
+    }
+    grid_sync(gs);
+    if (grid_failed(ws.bar)) return;
+    // (b) left reflector of column i
+    if (wid == 0) {
+      double s2 = 0.0;
+      for (int gg = lane; gg < G; gg += 32) s2 += __ldcg(pr + gg);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        cplx tq, sc;
+        double beta;
+        house_scalars(__ldcg(rowb + i), s2, &tq, &sc, &beta);
+        bc[0] = tq;
+        bc[1] = sc;
+        bc[2] = mk(beta, 0.0);
+      }
+    }
+    __syncthreads();
+    const cplx tq = bc[0], scq = bc[1];
+    const cplx ctq = cconj(tq), cscq = cconj(scq);
+    double sqp = 0.0;
+    for (int c = i + 1 + tid; c < n; c += blockDim.x) {
+      cplx s0 = mk(0, 0), s1 = mk(0, 0), s2 = mk(0, 0), s3 = mk(0, 0);
+      int gg = 0;
+      for (; gg + 4 <= G; gg += 4) {
+        s0 = cadd(s0, __ldcg(pc + (size_t)(gg + 0) * pstride + c));
+        s1 = cadd(s1, __ldcg(pc + (size_t)(gg + 1) * pstride + c));
+        s2 = cadd(s2, __ldcg(pc + (size_t)(gg + 2) * pstride + c));
+        s3 = cadd(s3, __ldcg(pc + (size_t)(gg + 3) * pstride + c));
+      }
+      for (; gg < G; ++gg) s0 = cadd(s0, __ldcg(pc + (size_t)gg * pstride + c));
+      const cplx psum = cadd(cadd(s0, s1), cadd(s2, s3));
+      const cplx a_ic = __ldcg(rowb + c);
+      const cplx w = cadd(a_ic, cmul(cscq, psum));
+      const cplx nr = csub(a_ic, cmul(ctq, w));
+      wv[c] = w;
+      nrow[c] = nr;
+      if (c >= i + 2) sqp += cabs2(nr);
+    }
+    sqp = block_sum(sqp, dred);  // its barriers also publish wv / nrow
+    // left update of own rows r > i (A[r,c] -= v_r conj(tau) w_c); column i
+    // then keeps v_r = A[r,i] * scale
+    for (int c = i + 1 + tid; c < n; c += blockDim.x) {
+      const cplx f = cmul(ctq, wv[c]);
+      for (int lr = lr0; lr < nact; ++lr) R(lr, c) = csub(R(lr, c), cmul(cmul(R(lr, i), scq), f));
+    }
+    __syncthreads();
+    for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) R(lr, i) = cmul(R(lr, i), scq);
+    if (owner && tid == 0) {
+      R(i / G, i) = bc[2];
+      dg[i] = bc[2].x;
+      tauq[i] = tq;
+    }
+    if (i + 1 >= n) break;
+    __syncthreads();
+    // right reflector of the updated row i (computed by every CTA): it
+    // zeroes the row beyond i+1
+    if (tid == 0) {
+      cplx tp, sp;
+      double beta;
+      house_scalars(cconj(nrow[i + 1]), sqp, &tp, &sp, &beta);
+      bc[0] = tp;
+      bc[1] = sp;
+      bc[2] = mk(beta, 0.0);
+    }
+    __syncthreads();
+    const cplx tp = bc[0], scp = bc[1];
+    for (int c = i + 1 + tid; c < n; c += blockDim.x) {
+      const cplx u = (c == i + 1) ? mk(1, 0) : cmul(cconj(nrow[c]), scp);
+      uv[c] = u;
+      if (owner) R(i / G, c) = (c == i + 1) ? bc[2] : cconj(u);
+    }
+    if (owner && tid == 0) {
+      eg[i] = bc[2].x;
+      taup[i] = tp;
+    }
+    __syncthreads();
+    // right update of own rows r > i: A[r,:] -= taup (A[r,:] . u) u^H
+    for (int lr = lr0 + wid; lr < nact; lr += nw) {
+      cplx dot = mk(0, 0);
+      for (int c = i + 1 + lane; c < n; c += 32) dot = cfma(R(lr, c), uv[c], dot);
+      dot = warp_sum(dot);
+      const cplx f = cmul(tp, dot);
+      for (int c = i + 1 + lane; c < n; c += 32) R(lr, c) = csub(R(lr, c), cmul(f, cconj(uv[c])));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int lr = 0; lr < nact; ++lr) {
+    const int r = grow(lr);
+    for (int c = tid; c < n; c += blockDim.x) A[r + (size_t)lda * c] = R(lr, c);
+  }
+}
+
+int gebrd_grid(int n, int* nloc_out, size_t* smem_out) {
+  const DevInfo& di = dev_info();
+  int G = std::max(1, std::min(di.sm_count, (n + 3) / 4));
+  for (;;) {
+    const int nloc = (n + G - 1) / G;
+    const size_t smem = ((size_t)nloc * n + 3 * (size_t)n) * sizeof(cplx);
+    if (smem + 8192 <= (size_t)di.max_smem_optin) {
+      *nloc_out = nloc;
+      *smem_out = smem;
+      return G;
+    }
+    if (G >= di.sm_count) return 0;
+    G = std::min(di.sm_count, G + 8);
+  }
+}
+
+bool gebrd_fits(int n) {
+  int nloc;
+  size_t smem;
+  return n >= 1 && gebrd_grid(n, &nloc, &smem) > 0;
+}
+
+cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cplx* taup,
+                  const CoopWs& ws, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int nloc;
+  size_t smem;
+  const int G = gebrd_grid(n, &nloc, &smem);
+  if (G <= 0) return cudaErrorInvalidValue;
+  if ((size_t)2 * G * (n + 1) > ws.pc_elems || (size_t)2 * n > ws.wfin_elems || 2 * G > 1024)
+    return cudaErrorInvalidValue;
+  cudaError_t err = cudaFuncSetAttribute(gebrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  err = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
+  if (err != cudaSuccess) return err;
+  CoopWs w = ws;
+  void* args[] = {&A, &lda, &n, &nloc, &d, &e, &tauq, &taup, &w};
+  return cudaLaunchCooperativeKernel((void*)gebrd_kernel, dim3(G), dim3(kBdThreads), args, smem, s);
+}
+
+// ---- 2. singular values ------------------------------------------------------------
+// Double-float reals: value = h + l, |l| <= ulp(h)/2.
+struct dfr {
+  float h, l;
+};
+DV dfr df_quick(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return dfr{s, b - (s - a)};
+}
+DV dfr df_add(dfr a, dfr b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
+  return df_quick(s, e);
+}
+DV dfr df_div(dfr a, dfr b) {
+  // long division: q1 = a/b to FP32, exact remainder a - q1 b, q2 = rem/b
+  const float r = __frcp_rn(b.h);
+  const float q1 = a.h * r;
+  const float p = q1 * b.h;
+  const float pe = fmaf(q1, b.h, -p);
+  const float rem = (((a.h - p) - pe) + a.l) - q1 * b.l;
+  return df_quick(q1, rem * r);
+}
+DV dfr df_of(double x) {
+  const float h = (float)x;
+  return dfr{h, (float)(x - (double)h)};
+}
+
+// Prepare the scaled squared off-diagonals of T_GK: a_k = d[k/2] (k even),
+// e[k/2] (k odd), k < 2n-1; a2[k] = (a_k / amax)^2 as double-float;
+// info[0] = amax, info[1] = Gershgorin bound of T_GK / amax.
+__global__ void bd_prep_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
+                               float2* __restrict__ a2, double* __restrict__ info) {
+  __shared__ double red[32];
+  const int N = 2 * n;
+  auto off = [&](int k) { return (k & 1) ? e[k >> 1] : d[k >> 1]; };
+  const int nw = blockDim.x >> 5;
+  double m = 0.0;
+  for (int k = threadIdx.x; k < N - 1; k += blockDim.x) m = fmax(m, fabs(off(k)));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double amax = 0.0;
+  for (int w = 0; w < nw; ++w) amax = fmax(amax, red[w]);
+  __syncthreads();
+  const double inv = amax > 0.0 ? 1.0 / amax : 0.0;
+  double bnd = 0.0;
+  for (int k = threadIdx.x; k < N - 1; k += blockDim.x) {
+    const double a = fabs(off(k)) * inv;
+    const double a_sq = a * a;
+    float2 v = make_float2(0.f, 0.f);
+    if (a_sq >= 1e-36) {
+      v.x = (float)a_sq;
+      v.y = (float)(a_sq - (double)v.x);
+    }
+    a2[k] = v;
+    // row k+1 of T_GK holds a_k and a_{k+1}
+    const double nb = (k + 1 < N - 1) ? fabs(off(k + 1)) * inv : 0.0;
+    bnd = fmax(bnd, a + nb);
+  }
+  for (int o = 16; o > 0; o >>= 1) bnd = fmax(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bnd;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < nw; ++w) b = fmax(b, red[w]);
+    info[0] = amax;
+    info[1] = b * (1.0 + 1e-6) + 1e-30;
+  }
+}
+
+// Number of eigenvalues of the scaled T_GK below x: negative pivots of the
+// LDL^T factorisation of T_GK - x I (pivots clamped away from zero).
+__device__ __forceinline__ int sturm_count_df(const float2* __restrict__ a2, int N, double x) {
+  const float pivmin = 1e-30f;
+  const dfr xd = df_of(x);
+  dfr q{-xd.h, -xd.l};
+  if (fabsf(q.h) < pivmin) q = dfr{-pivmin, 0.f};
+  int cnt = (q.h < 0.f);
+  for (int k = 1; k < N; ++k) {
+    const float2 a = __ldg(a2 + k - 1);
+    const dfr t = df_div(dfr{a.x, a.y}, q);
+    const dfr s = df_add(xd, t);
+    q = dfr{-s.h, -s.l};
+    if (fabsf(q.h) < pivmin) q = dfr{-pivmin, 0.f};
+    cnt += (q.h < 0.f);
+  }
+  return cnt;
+}
+
+// One warp per value: sig[k] = k-th largest singular value of B.  The
+// bracket [lo, hi) keeps #{sigma < lo} < target <= #{sigma < hi} with
+// target = n - k; each round the lanes count at 32 interior points.
+__global__ void bd_sigma_kernel(const float2* __restrict__ a2, const double* __restrict__ info, int n,
+                                double* __restrict__ sig) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= n) return;
+  const double amax = info[0];
+  if (amax == 0.0) {
+    if (lane == 0) sig[k] = 0.0;
+    return;
+  }
+  const int N = 2 * n, target = n - k;
+  double lo = 0.0, hi = info[1];
+  for (int it = 0; it < 24; ++it) {
+    if (hi - lo <= 0x1p-42 * hi || hi - lo <= 1e-32) break;
+    const double x = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
+    const int below = sturm_count_df(a2, N, x) - n;
+    const unsigned ok = __ballot_sync(0xffffffffu, below >= target);
+    const int first = ok ? (__ffs(ok) - 1) : 32;
+    const double xl = __shfl_sync(0xffffffffu, x, first == 0 ? 0 : first - 1);
+    const double xh = __shfl_sync(0xffffffffu, x, first == 32 ? 31 : first);
+    if (first > 0) lo = xl;
+    if (first < 32) hi = xh;
+  }
+  if (lane == 0) sig[k] = 0.5 * (lo + hi) * amax;
+}
+
+cudaError_t bd_sigma(const double* d, const double* e, int n, float2* a2, double* info, double* sig,
+                     cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  bd_prep_kernel<<<1, 256, 0, s>>>(d, e, n, a2, info);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int warps = 4;
+  bd_sigma_kernel<<<(n + warps - 1) / warps, 32 * warps, 0, s>>>(a2, info, n, sig);
+  return cudaGetLastError();
+}
+
+// Rank rule on the sorted values (the same rule as rank_select).
+__global__ void bd_rank_kernel(const double* sig, int n, const double* eps_hat, int cap, int forced,
+                               int* out_int, double* out_dbl, double* tail2) {
+  if (threadIdx.x != 0) return;
+  tail2[n] = 0.0;
+  for (int r = n - 1; r >= 0; --r) tail2[r] = tail2[r + 1] + sig[r] * sig[r];
+  const double eh = *eps_hat;
+  int rho_tol = n;
+  for (int r = 1; r <= n; ++r)
+    if (sqrt(tail2[r]) <= eh) {
+      rho_tol = r;
+      break;
+    }
+  int rho = forced > 0 ? forced : (rho_tol < cap ? rho_tol : cap);
+  rho = rho < 1 ? 1 : (rho > n ? n : rho);
+  // kept values at the noise level of a factorisation of B (their vectors
+  // are not determined by B and are completed instead)
+  const double thr = 2.0 * n * DBL_EPSILON * sqrt(tail2[0]);
+  int kt = 0;
+  while (kt < rho && sig[kt] > thr) ++kt;
+  out_int[0] = rho;
+  out_int[1] = rho_tol;
+  out_int[2] = kt;
+  out_dbl[0] = sqrt(tail2[rho]);
+  out_dbl[1] = sig[rho - 1];
+  out_dbl[2] = tail2[0];
+}
+
+cudaError_t bd_rank(const double* sig, int n, const double* eps_hat, int cap, int forced, int* out_int,
+                    double* out_dbl, double* tail2, cudaStream_t s) {
+  bd_rank_kernel<<<1, 32, 0, s>>>(sig, n, eps_hat, cap, forced, out_int, out_dbl, tail2);
+  return cudaGetLastError();
+}
+
+// ---- 3. singular vectors of B -------------------------------------------------------------
+DV double hash_unit(unsigned a, unsigned b) {
+  unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (double)(h & 0xFFFFFFu) * (1.0 / 16777216.0) - 0.5;
+}
+
+// Per-thread scratch of the tridiagonal solver: six arrays of length N,
+// interleaved by lane so that a warp's accesses coalesce.
+struct LaneArrays {
+  double* base;
+  int N;
+  DV double& at(int arr, int i) const { return base[((size_t)arr * N + i) * 32]; }
+};
+enum { L_DINV = 0, L_DU = 1, L_DU2 = 2, L_DL = 3, L_PV = 4, L_B = 5 };
+constexpr int kLaneArrays = 6;
+
+// LU with partial pivoting of T_GK - lam I (scaled: off-diagonals a_k / amax).
+DV void gk_factor(const double* d, const double* e, int n, double inv, double lam, LaneArrays w) {
+  const int N = 2 * n;
+  const double tiny = 4.0 * DBL_EPSILON;
+  auto off = [&](int k) { return ((k & 1) ? e[k >> 1] : d[k >> 1]) * inv; };
+  auto guard = [&](double p) { return fabs(p) < tiny ? (p < 0.0 ? -tiny : tiny) : p; };
+  double di = -lam, dui = (N > 1) ? off(0) : 0.0;
+  for (int i = 0; i < N - 1; ++i) {
+    const double sub = off(i), dn = -lam, un = (i + 1 < N - 1) ? off(i + 1) : 0.0;
+    if (fabs(di) >= fabs(sub)) {
+      const double piv = guard(di);
+      const double f = sub / piv;
+      w.at(L_DINV, i) = 1.0 / piv;
+      w.at(L_DU, i) = dui;
+      w.at(L_DU2, i) = 0.0;
+      w.at(L_DL, i) = f;
+      w.at(L_PV, i) = 0.0;
+      di = dn - f * dui;
+      dui = un;
+    } else {
+      // rows i and i+1 swapped: new row i = (sub, dn, un)
+      const double f = di / sub;
+      w.at(L_DINV, i) = 1.0 / sub;
+      w.at(L_DU, i) = dn;
+      w.at(L_DU2, i) = un;
+      w.at(L_DL, i) = f;
+      w.at(L_PV, i) = 1.0;
+      di = dui - f * dn;
+      dui = -f * un;
+    }
+  }
+  w.at(L_DINV, N - 1) = 1.0 / guard(di);
+}
+
+DV void gk_solve(int N, LaneArrays w) {
+  for (int i = 0; i < N - 1; ++i) {
+    const double bi = w.at(L_B, i), bn = w.at(L_B, i + 1), f = w.at(L_DL, i);
+    if (w.at(L_PV, i) != 0.0) {
+      w.at(L_B, i) = bn;
+      w.at(L_B, i + 1) = bi - f * bn;
+    } else {
+      w.at(L_B, i + 1) = bn - f * bi;
+    }
+  }
+  double x2 = 0.0, x1 = w.at(L_B, N - 1) * w.at(L_DINV, N - 1);
+  w.at(L_B, N - 1) = x1;
+  for (int i = N - 2; i >= 0; --i) {
+    const double x = (w.at(L_B, i) - w.at(L_DU, i) * x1 - w.at(L_DU2, i) * x2) * w.at(L_DINV, i);
+    w.at(L_B, i) = x;
+    x2 = x1;
+    x1 = x;
+  }
+}
+
+// One thread per cluster of kept values (consecutive values closer than
+// 1e-3 sigma_max): inverse iteration for each member, re-orthogonalised
+// against the members before it.  X (n x nvec, ldx) receives the
+// normalised left vectors u_k.  Every k < nvec is above the noise level
+// (the caller passes the count of such values).
+__global__ void bd_vectors_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                  const double* __restrict__ info, const double* __restrict__ sig,
+                                  int nvec, double* __restrict__ X, int ldx,
+                                  double* __restrict__ scratch, double* __restrict__ Zs) {
+  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = 2 * n;
+  if (k0 >= nvec) return;
+  const double amax = info[0];
+  if (amax == 0.0) return;
+  const double gap_tol = 1e-3 * sig[0];
+  if (k0 > 0 && sig[k0 - 1] - sig[k0] < gap_tol) return;  // not the first of its cluster
+  int k1 = k0 + 1;
+  while (k1 < nvec && sig[k1 - 1] - sig[k1] < gap_tol) ++k1;
+  const double inv = 1.0 / amax;
+  const int lane = k0 & 31, warp = k0 >> 5;
+  LaneArrays w{scratch + (size_t)warp * kLaneArrays * N * 32 + lane, N};
+  for (int k = k0; k < k1; ++k) {
+    const double lam = sig[k] * inv;
+    gk_factor(d, e, n, inv, lam, w);
+    for (int i = 0; i < N; ++i) w.at(L_B, i) = 1.0 + 0.25 * hash_unit((unsigned)i, (unsigned)k);
+    for (int it = 0; it < 3; ++it) {
+      gk_solve(N, w);
+      for (int j = k0; j < k; ++j) {
+        const double* zj = Zs + (size_t)j * N;
+        double dot = 0.0;
+        for (int i = 0; i < N; ++i) dot += zj[i] * w.at(L_B, i);
+        for (int i = 0; i < N; ++i) w.at(L_B, i) -= dot * zj[i];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < N; ++i) nrm += w.at(L_B, i) * w.at(L_B, i);
+      const double s = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+      for (int i = 0; i < N; ++i) w.at(L_B, i) *= s;
+    }
+    double* zk = Zs + (size_t)k * N;
+    double un = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double z = w.at(L_B, i);
+      zk[i] = z;
+      if (i & 1) un += z * z;
+    }
+    const double s = un > 0.0 ? 1.0 / sqrt(un) : 0.0;
+    for (int i = 0; i < n; ++i) X[i + (size_t)ldx * k] = zk[2 * i + 1] * s;
+  }
+}
+
+// Orthonormal completion for kept values at the noise level (indices
+// kt..nvec-1): pseudo-random vectors, classical Gram-Schmidt twice against
+// every earlier column of X.  One CTA.
+__global__ void bd_complete_kernel(int n, int kt, int nvec, double* __restrict__ X, int ldx) {
+  extern __shared__ __align__(16) unsigned char cs_smem[];
+  double* x = reinterpret_cast<double*>(cs_smem);  // n
+  double* dots = x + n;                             // nvec
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = kt; k < nvec; ++k) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = hash_unit((unsigned)i + 7919u, (unsigned)k * 31u + 3u);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = wid; j < k; j += nw) {
+        double s = 0.0;
+        for (int i = lane; i < n; i += 32) s += X[i + (size_t)ldx * j] * x[i];
+        s = warp_sum(s);
+        if (lane == 0) dots[j] = s;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = x[i];
+        for (int j = 0; j < k; ++j) v -= dots[j] * X[i + (size_t)ldx * j];
+        x[i] = v;
+      }
+      __syncthreads();
+    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i] * x[i];
+    s = block_sum(s, red);
+    const double sc = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) X[i + (size_t)ldx * k] = x[i] * sc;
+    __syncthreads();
+  }
+}
+
+size_t bd_scratch_doubles(int n, int nvec) {
+  return (size_t)kLaneArrays * 2 * n * 32 * (size_t)((nvec + 31) / 32);
+}
+
+cudaError_t bd_vectors(const double* d, const double* e, int n, const double* info, const double* sig,
+                       int kt, int nvec, double* X, int ldx, double* scratch, double* Zs, cudaStream_t s) {
+  if (nvec <= 0) return cudaSuccess;
+  if (kt > 0) {
+    bd_vectors_kernel<<<(kt + 31) / 32, 32, 0, s>>>(d, e, n, info, sig, kt, X, ldx, scratch, Zs);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  if (kt < nvec) {
+    const size_t smem = sizeof(double) * ((size_t)n + nvec);
+    bd_complete_kernel<<<1, 256, smem, s>>>(n, kt, nvec, X, ldx);
+  }
+  return cudaGetLastError();
+}
+
+// ---- 4. back-transformation -------------------------------------------------------------------
+// u_k <- Q u_k with Q = H_0 H_1 ... H_{n-1} (reflector j: unit entry at j,
+// tail A[j+1:n, j], tau[j]).  One warp per vector (the FP64 work of a
+// vector is small; spreading the vectors over SMs is what counts).  The
+// result goes to U (n x nvec, ldu) and to Xp (mrows x nvec, ldp, zero below
+// row n).
+__global__ void bd_back_kernel(const cplx* __restrict__ A, int lda, const cplx* __restrict__ tauq, int n,
+                               const double* __restrict__ Xr, int ldx, int nvec, cplx* __restrict__ U,
+                               int ldu, cplx* __restrict__ Xp, int ldp, int mrows) {
+  extern __shared__ __align__(16) unsigned char bk_smem[];
+  cplx* x = reinterpret_cast<cplx*>(bk_smem);
+  const int k = blockIdx.x, lane = threadIdx.x;
+  if (k >= nvec) return;
+  for (int i = lane; i < n; i += 32) x[i] = mk(Xr[i + (size_t)ldx * k], 0.0);
+  __syncwarp();
+  for (int j = n - 1; j >= 0; --j) {
+    const cplx t = tauq[j];
+    if (t.x == 0.0 && t.y == 0.0) continue;
+    cplx acc = mk(0, 0);
+    for (int i = j + lane; i < n; i += 32) {
+      const cplx v = (i == j) ? mk(1, 0) : A[i + (size_t)lda * j];
+      acc = cfmac(v, x[i], acc);
+    }
+    acc = warp_sum(acc);
+    const cplx f = cmul(t, acc);
+    for (int i = j + lane; i < n; i += 32) {
+      const cplx v = (i == j) ? mk(1, 0) : A[i + (size_t)lda * j];
+      x[i] = csub(x[i], cmul(v, f));
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < mrows; i += 32) {
+    const cplx v = (i < n) ? x[i] : mk(0, 0);
+    if (i < n) U[i + (size_t)ldu * k] = v;
+    Xp[i + (size_t)ldp * k] = v;
+  }
+}
+
+cudaError_t bd_back(const cplx* A, int lda, const cplx* tauq, int n, const double* X, int ldx, int nvec,
+                    cplx* U, int ldu, cplx* Xp, int ldp, int mrows, cudaStream_t s) {
+  if (nvec <= 0) return cudaSuccess;
+  bd_back_kernel<<<nvec, 32, sizeof(cplx) * (size_t)n, s>>>(A, lda, tauq, n, X, ldx, nvec, U, ldu, Xp, ldp, mrows);
+  return cudaGetLastError();
+}
+
+}  // namespace hk

@@ -45,6 +45,16 @@ struct RoundWs {
   cplx* Sb = nullptr;     // kcap * kcap
   double* sig = nullptr;  // 2 * kcap + 2
   int* perm = nullptr;    // kcap
+  // bidiagonal SVD of square factors
+  double* bd_d = nullptr;     // kcap
+  double* bd_e = nullptr;     // kcap
+  cplx* bd_tauq = nullptr;    // kcap
+  cplx* bd_taup = nullptr;    // kcap
+  float2* bd_a2 = nullptr;    // 2 * kcap
+  double* bd_info = nullptr;  // 4
+  double* bd_X = nullptr;     // kcap * kcap
+  double* bd_Zs = nullptr;    // kcap * 2 kcap
+  double* bd_scr = nullptr;   // bd_scratch_doubles(kcap, kcap)
 };
 
 struct hopf_ctx {
@@ -60,6 +70,7 @@ struct hopf_ctx {
   // cooperative-kernel workspace
   hk::CoopWs coop{};
   int coop_kcap = 0;
+  int svd_method = HOPF_SVD_AUTO;
   // small device scalars and pinned mirrors
   double* d_dbl = nullptr;  // [16]
   int* d_int = nullptr;     // [16]
@@ -167,6 +178,8 @@ void prof_end(hopf_ctx* ctx, int slot, int cls, double flops, double bytes, int 
 double qr_flops(double m, double k) {
   return (m >= k) ? 8.0 * m * k * k - 8.0 * k * k * k / 3.0 : 8.0 * k * m * m - 8.0 * m * m * m / 3.0;
 }
+// Bidiagonalisation of a square n x n complex matrix (LAPACK count).
+double gebrd_flops(double n) { return 32.0 * n * n * n / 3.0; }
 // Q (m x m, p reflectors) applied to an m x q block.
 double applyq_flops(double m, double q, double p) { return 16.0 * m * q * p - 8.0 * q * p * p; }
 // C = A R^H with R upper trapezoidal N x K: sum_j (K - j) MACs per row.
@@ -281,6 +294,8 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   cudaFree(w.W1); cudaFree(w.tau); cudaFree(w.T); cudaFree(w.tau2); cudaFree(w.T2);
   cudaFree(w.Rb); cudaFree(w.Mb); cudaFree(w.Jb); cudaFree(w.Ub); cudaFree(w.Sb);
   cudaFree(w.sig); cudaFree(w.perm);
+  cudaFree(w.bd_d); cudaFree(w.bd_e); cudaFree(w.bd_tauq); cudaFree(w.bd_taup); cudaFree(w.bd_a2);
+  cudaFree(w.bd_info); cudaFree(w.bd_X); cudaFree(w.bd_Zs); cudaFree(w.bd_scr);
   w = RoundWs{};
   const size_t elems = std::max(need, w.elems);
   const int d = t->d;
@@ -300,6 +315,15 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   CK(dalloc(&w.Sb, (size_t)K * K));
   CK(dalloc(&w.sig, (size_t)2 * K + 2));
   CK(dalloc(&w.perm, (size_t)K));
+  CK(dalloc(&w.bd_d, (size_t)K));
+  CK(dalloc(&w.bd_e, (size_t)K));
+  CK(dalloc(&w.bd_tauq, (size_t)K));
+  CK(dalloc(&w.bd_taup, (size_t)K));
+  CK(dalloc(&w.bd_a2, (size_t)2 * K));
+  CK(dalloc(&w.bd_info, 4));
+  CK(dalloc(&w.bd_X, (size_t)K * K));
+  CK(dalloc(&w.bd_Zs, (size_t)2 * K * K));
+  CK(dalloc(&w.bd_scr, hk::bd_scratch_doubles(K, K)));
   w.elems = elems;
   w.d = d;
   w.kcap = K;
@@ -450,10 +474,21 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     const int nsv = case1 ? cols : pp;
     if (forced && (forced_c < 1 || forced_c > nsv))
       return fail(ctx, HOPF_EINVAL, "forced rank %d at bond %d outside [1, %d]", forced_c, c + 1, nsv);
+    // Square factors: bidiagonalisation, bisection and inverse iteration.
+    const bool use_bd = case1 && ctx->svd_method != HOPF_SVD_JACOBI && hk::gebrd_fits(pp);
+    if (use_bd) {
+      CK(cudaMemcpyAsync(w.Mb, w.Rb, (size_t)pp * cols * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
+      LAUNCH(HOPF_K_SVD, gebrd_flops(pp), 0, 1, hk::gebrd(w.Mb, pp, pp, w.bd_d, w.bd_e, w.bd_tauq, w.bd_taup, ctx->coop, ctx->stream));
+      LAUNCH(HOPF_K_SVD, 0, 0, 2, hk::bd_sigma(w.bd_d, w.bd_e, pp, w.bd_a2, w.bd_info, w.sig, ctx->stream));
+      LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::bd_rank(w.sig, pp, ctx->d_dbl + 1, cap, forced_c, ctx->d_int, ctx->d_dbl + 2, w.sig + pp, ctx->stream));
+      TRY(read_small(ctx, 3, 5));
+      TRY(check_barrier(ctx));
+      ctx->prof.svd_count += 1;
+    }
     // Jacobi leaves out pairs far below the truncation tolerance (theta);
     // if the rank kept reaches below theta, finish the SVD exactly so that
     // every kept singular vector is orthogonal to all others.
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 2 && !use_bd; ++pass) {
       const double* eh = (pass == 0) ? ctx->d_dbl + 1 : nullptr;
       if (case1) {
         if (pass == 0)
@@ -487,7 +522,11 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     rho[c + 1] = rnew;
     disc2 += delta * delta;
     // new core c = Q [U_rho; 0]
-    if (case1) {
+    if (use_bd) {
+      const int kt = std::min(ctx->h_int[2], rnew);
+      LAUNCH(HOPF_K_SVD, 0, 0, (kt > 0) + (kt < rnew), hk::bd_vectors(w.bd_d, w.bd_e, pp, w.bd_info, w.sig, kt, rnew, w.bd_X, pp, w.bd_scr, w.bd_Zs, ctx->stream));
+      LAUNCH(HOPF_K_SVD, 0, 0, 1, hk::bd_back(w.Mb, pp, w.bd_tauq, pp, w.bd_X, pp, rnew, w.Ub, pp, t->cores[c], Mrows, Mrows, ctx->stream));
+    } else if (case1) {
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::gather_u(w.Mb, pp, pp, w.perm, w.sig, 1, rnew, t->cores[c], Mrows, Mrows, w.Ub, pp, ctx->stream));
     } else {
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::gather_u(w.Jb, pp, pp, w.perm, w.sig, 0, rnew, t->cores[c], Mrows, Mrows, w.Ub, pp, ctx->stream));
@@ -789,6 +828,13 @@ hopf_status hopf_set_L(hopf_ctx* ctx, double L) {
   if (!(L > 0.0) || !std::isfinite(L)) return fail(ctx, HOPF_EINVAL, "L must be positive");
   ctx->L = L;
   return build_ops(ctx);
+}
+
+hopf_status hopf_set_svd_method(hopf_ctx* ctx, int method) {
+  if (!ctx) return HOPF_EINVAL;
+  if (method != HOPF_SVD_AUTO && method != HOPF_SVD_JACOBI) return fail(ctx, HOPF_EINVAL, "unknown SVD method %d", method);
+  ctx->svd_method = method;
+  return HOPF_OK;
 }
 
 hopf_status hopf_get_L(const hopf_ctx* ctx, double* L) {

@@ -67,6 +67,32 @@ cudaError_t rank_select(const cplx* M, int ldm, int nr, int nc, const double* ep
                         int cap, int forced, double* sigma, int* perm, int* out_int,
                         double* out_dbl, cudaStream_t s);
 
+// ---- SVD of a square factor through bidiagonalisation (bdsvd.cu) --------
+// R (n x n, lda) = Q B P^H in place (LAPACK zgebrd layout: left reflector
+// tails below the diagonal, right reflector tails right of the
+// superdiagonal); B: diagonal d[n], superdiagonal e[n-1], both real.
+// Cooperative launch, one grid barrier per column.
+cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cplx* taup,
+                  const CoopWs& ws, cudaStream_t s);
+bool gebrd_fits(int n);  // shared-memory resident rows fit on this device
+// All singular values of B, sorted descending, into sig[n]; a2 (float2
+// [2n]) and info (double [4]) are scratch kept for bd_vectors.
+cudaError_t bd_sigma(const double* d, const double* e, int n, float2* a2, double* info, double* sig,
+                     cudaStream_t s);
+// Rank rule on sorted values: out_int[0] = rho, [1] = rho by tolerance,
+// [2] = number of kept values above the noise level 2 n eps ||B||_F;
+// out_dbl as rank_select; tail2[n+1] scratch.
+cudaError_t bd_rank(const double* sig, int n, const double* eps_hat, int cap, int forced, int* out_int,
+                    double* out_dbl, double* tail2, cudaStream_t s);
+// Left singular vectors of B: columns k < kt by inverse iteration, columns
+// kt..nvec-1 by orthonormal completion; X (n x nvec, ldx), real.
+size_t bd_scratch_doubles(int n, int nvec);
+cudaError_t bd_vectors(const double* d, const double* e, int n, const double* info, const double* sig,
+                       int kt, int nvec, double* X, int ldx, double* scratch, double* Zs, cudaStream_t s);
+// U = Q X -> U (n x nvec, ldu) and Xp (mrows x nvec, ldp, zero below row n).
+cudaError_t bd_back(const cplx* A, int lda, const cplx* tauq, int n, const double* X, int ldx, int nvec,
+                    cplx* U, int ldu, cplx* Xp, int ldp, int mrows, cudaStream_t s);
+
 // ---- dense helpers ------------------------------------------------------------
 // B (m x k, ldb) = conj-transpose of the k x m matrix A (lda).
 cudaError_t conj_transpose(const cplx* A, int lda, int k, int m, cplx* B, int ldb,

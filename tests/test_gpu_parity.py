@@ -29,8 +29,13 @@ def B():
     return binding
 
 
-def ctx_for(B, d, n, nu=0.05, L=3.0, tol=1e-10, cap=16, nonlinear=True):
-    return B.Context(d=d, n=n, nu=nu, tol=tol, rank_cap=cap, L=L, nonlinear=nonlinear)
+def ctx_for(B, d, n, nu=0.05, L=3.0, tol=1e-10, cap=16, nonlinear=True, svd=0):
+    ctx = B.Context(d=d, n=n, nu=nu, tol=tol, rank_cap=cap, L=L, nonlinear=nonlinear)
+    ctx.hopf_set_svd_method(svd)
+    return ctx
+
+
+SVD_METHODS = pytest.mark.parametrize("svd", [0, 1], ids=["bidiag", "jacobi"])
 
 
 @pytest.mark.parametrize("d,n,r", [(3, 8, 2), (4, 12, 5), (6, 20, 11), (5, 33 - 1, 7)])
@@ -78,12 +83,13 @@ def test_sum_matches_oracle(B):
     (6, 20, [1, 20, 45, 70, 45, 20, 1], 1e-6, 33),  # several QR panels, ragged tail, cap
     (5, 40, [1, 17, 33, 33, 17, 1], 0.0, 100),  # tol = 0: exact
 ])
-def test_round_matches_oracle_with_rank_replay(B, d, n, ranks, tol, cap):
+@SVD_METHODS
+def test_round_matches_oracle_with_rank_replay(B, d, n, ranks, tol, cap, svd):
     base = synthetic.random_tt_cores(d, n, [1] + [min(4, r) for r in ranks[1:-1]] + [1], seed=7)
     noise = synthetic.random_tt_cores(d, n, ranks, seed=8, scale=1e-3)
     x = tt.tt_sum([(1.0, base), (1.0, noise)])
     want, wranks, wdisc = tt.round_tt(x, tol, cap)
-    ctx = ctx_for(B, d, n, tol=tol, cap=cap)
+    ctx = ctx_for(B, d, n, tol=tol, cap=cap, svd=svd)
     tx = ctx.tt_from_host(x, max_rank=max(tt.ranks(x)))
     disc, st = ctx.tt_round(tx, tol, cap, forced_ranks=wranks)
     assert ctx.tt_get_ranks(tx) == wranks
@@ -101,6 +107,51 @@ def test_round_matches_oracle_with_rank_replay(B, d, n, ranks, tol, cap):
     tx2 = ctx.tt_from_host(x, max_rank=max(tt.ranks(x)))
     ctx.tt_round(tx2, tol, cap)
     assert ctx.tt_get_ranks(tx2) == wranks
+
+
+@SVD_METHODS
+def test_round_rank_deficient_keeps_noise_level_values(B, svd):
+    """x + x/2 has numerically the ranks of x; with tol = 0 every singular
+    value is kept, the ones at the rounding level included.  Their vectors
+    are not determined by the data, but the rounded tensor and the
+    orthonormality of the cores are."""
+    d, n = 5, 12
+    base = synthetic.random_tt_cores(d, n, [1, 5, 9, 9, 5, 1], seed=17)
+    x = tt.tt_sum([(1.0, base), (0.5, base)])
+    want, wranks, _ = tt.round_tt(x, 0.0, 100)
+    assert max(wranks) > 9  # noise-level values are kept
+    ctx = ctx_for(B, d, n, tol=0.0, cap=100, svd=svd)
+    tx = ctx.tt_from_host(x, max_rank=max(tt.ranks(x)))
+    ctx.tt_round(tx, 0.0, 100, forced_ranks=wranks)
+    got = ctx.tt_to_host(tx)
+    assert rel(tt.full(got), tt.full(x)) < 1e-13
+    for C in got[:-1]:
+        V = tt.V(C)
+        assert np.abs(V.conj().T @ V - np.eye(V.shape[1])).max() < 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 33, 97, 160])
+def test_square_svd_paths_agree(B, n):
+    """Bidiagonal and Jacobi SVD give the oracle's rounding of a three-core
+    tensor whose bond factors are n x n triangles with a graded spectrum
+    (from a single element to many CTAs of the bidiagonalisation)."""
+    rng = np.random.default_rng(n)
+    d, m = 3, n + 2 + n % 2
+    Ul = np.linalg.qr(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))[0]
+    s = np.logspace(0, -12, n)
+    Vr = np.linalg.qr(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n)))[0]
+    Mid = (rng.standard_normal((n, m, n)) + 1j * rng.standard_normal((n, m, n))) / np.sqrt(m)
+    cores = [np.asfortranarray((Ul * s).reshape(1, m, n)), np.asfortranarray(Mid),
+             np.asfortranarray(Vr.conj().T.reshape(n, m, 1))]
+    want, wranks, wdisc = tt.round_tt(cores, 1e-9, n)
+    Fw = tt.full(want)
+    for svd in (0, 1):
+        ctx = ctx_for(B, d, m, tol=1e-9, cap=n, svd=svd)
+        tx = ctx.tt_from_host(cores, max_rank=n)
+        disc, _ = ctx.tt_round(tx, 1e-9, n)
+        assert ctx.tt_get_ranks(tx) == wranks
+        assert rel(tt.full(ctx.tt_to_host(tx)), Fw) < 1e-11
+        assert abs(disc - wdisc) <= 1e-6 * wdisc + 1e-14 * np.linalg.norm(Fw)
 
 
 def test_round_error_bound_and_cap_status(B):
@@ -179,7 +230,7 @@ def test_moments_match_oracle(B):
     assert ir < 1e-10
 
 
-def _step_parity(B, w, n, nsteps, cores, L):
+def _step_parity(B, w, n, nsteps, cores, L, svd=0):
     W = model.mpo_blocks(w.d, n, L, w.nu, w.nonlinear)
     bond = model.mpo_bond_dims(w.d)
     log = []
@@ -187,17 +238,19 @@ def _step_parity(B, w, n, nsteps, cores, L):
     for _ in range(nsteps):
         ocores, _ = tt.rk4_step(ocores, w.dt, W, bond, w.tol, w.cap, record=log)
     ctx = B.Context(d=w.d, n=n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L, nonlinear=w.nonlinear)
+    ctx.hopf_set_svd_method(svd)
     t = ctx.tt_from_host(cores, max_rank=w.cap)
     out = ctx.hopf_step(t, w.dt, nsteps, record=True, replay=np.array(log))
     assert np.array_equal(out["ranks"], np.array(log))
     return ctx, t, ocores
 
 
-def test_step_parity_c1_short(B):
+@SVD_METHODS
+def test_step_parity_c1_short(B, svd):
     """C1 parameters, 20 RK4 steps with ranks replayed: <= 1e-10 rel L2."""
     w, n, m0, C0, L = _c1_state()
     cores = tt.tt_svd(fullgrid.phi0_grid(m0, C0, n, L), w.tol, w.cap)
-    ctx, t, ocores = _step_parity(B, w, n, 20, cores, L)
+    ctx, t, ocores = _step_parity(B, w, n, 20, cores, L, svd=svd)
     err = rel(tt.full(ctx.tt_to_host(t)), tt.full(ocores))
     print(f"C1 20 steps: rel L2 err {err:.3e}")
     assert err < 1e-10
