@@ -52,23 +52,27 @@ DV void house_scalars(cplx alpha, double xnorm2, cplx* tau, cplx* scale, double*
 // ---- 1. bidiagonalisation -------------------------------------------------------
 // Column i, with H = I - tau v v^H the left reflector (v_i = 1,
 // v_r = A[r,i] * scale for r > i) and w_c = sum_r conj(v_r) A[r,c]:
-//   w_c = A[i,c] + conj(scale) * sum_{r>i} conj(A[r,i]) A[r,c],
-// so the CTAs exchange only their partial sums over their own rows plus
-// row i (published by its owner) and meet at ONE grid barrier.  After it,
-// every CTA forms the updated row i, A[i,c] - conj(tau) w_c, itself, hence
-// also the right reflector G = I - taup u u^H of that row, and applies
-// both reflectors to its own rows without further synchronisation.  The
-// partial-sum buffers alternate between two halves (a CTA writing column
-// i+1's partials has passed barrier i, so every reader of column i-1's
-// half is done).
+//   w_c = A[i,c] + conj(scale) * sum_{r>i} conj(A[r,i]) A[r,c].
+// Each CTA writes its partial sums over its own rows (and the owner of row
+// i publishes that row); after a grid barrier, CTA g reduces the columns
+// c = i+1+g (mod G) and publishes conj(tau) w_c and the updated row i,
+// A[i,c] - conj(tau) w_c; after a second barrier every CTA forms the right
+// reflector G = I - taup u u^H of that row itself and applies both
+// reflectors to its own rows.  (Reducing every column in every CTA would
+// save the second barrier but costs G times the FP64 additions, which on
+// this GPU's narrow FP64 pipe outweigh the barrier.)  The exchange buffers
+// alternate between two halves by column parity: a CTA writing column
+// i+2's data has passed both barriers of column i+1, so every reader of
+// column i's half is done.
 __global__ void __launch_bounds__(kBdThreads, 1)
 gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* tauq, cplx* taup,
              CoopWs ws) {
   extern __shared__ __align__(16) unsigned char bd_smem[];
   cplx* rows = reinterpret_cast<cplx*>(bd_smem);  // nloc x n, row-major
-  cplx* wv = rows + (size_t)nloc * n;            // w_c
-  cplx* nrow = wv + n;                           // updated row i
+  cplx* fv = rows + (size_t)nloc * n;            // conj(tau) w_c
+  cplx* nrow = fv + n;                           // updated row i
   cplx* uv = nrow + n;                           // right reflector u
+  cplx* vloc = uv + n;                           // v_r of own rows (nloc)
   __shared__ double dred[32];
   __shared__ cplx bc[4];
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
@@ -89,9 +93,13 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
     const int buf = i & 1;
     cplx* pc = ws.pc + (size_t)buf * G * pstride;
     double* pr = ws.pr + buf * G;
-    cplx* rowb = ws.wfin + (size_t)buf * n;
+    cplx* rowb = ws.wfin + (size_t)buf * 3 * n;  // row i as published by its owner
+    cplx* fvg = rowb + n;                        // conj(tau) w_c
+    cplx* nrg = fvg + n;                         // updated row i
+    const int C = n - i - 1;
     // first own local row strictly below i (rows of this CTA: g + lr G)
     const int lr0 = (i + 1 > g) ? (i + 1 - g + G - 1) / G : 0;
+    const bool owner = (i % G == g);
     // (a) partial sums over own rows r > i
     double sq = 0.0;
     for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) sq += cabs2(R(lr, i));
@@ -102,14 +110,11 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
       pc[(size_t)g * pstride + c] = acc;
     }
     if (tid == 0) pr[g] = sq;
-    const bool owner = (i % G == g);
-    if (owner) {
-      const int lri = i / G;
-      for (int c = i + tid; c < n; c += blockDim.x) rowb[c] = R(lri, c);
-    }
+    if (owner)
+      for (int c = i + tid; c < n; c += blockDim.x) rowb[c] = R(i / G, c);
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
-    // (b) left reflector of column i
+    // (b1) left reflector of column i (every CTA), reduction of its columns
     if (wid == 0) {
       double s2 = 0.0;
       for (int gg = lane; gg < G; gg += 32) s2 += __ldcg(pr + gg);
@@ -126,34 +131,37 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
     __syncthreads();
     const cplx tq = bc[0], scq = bc[1];
     const cplx ctq = cconj(tq), cscq = cconj(scq);
+    for (int cc = g + wid * G; cc < C; cc += nw * G) {
+      const int c = i + 1 + cc;
+      cplx acc = mk(0, 0);
+      for (int gg = lane; gg < G; gg += 32) acc = cadd(acc, __ldcg(pc + (size_t)gg * pstride + c));
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const cplx a_ic = __ldcg(rowb + c);
+        const cplx f = cmul(ctq, cadd(a_ic, cmul(cscq, acc)));
+        fvg[c] = f;
+        nrg[c] = csub(a_ic, f);
+      }
+    }
+    grid_sync(gs);
+    if (grid_failed(ws.bar)) return;
+    // (b2) left update of own rows r > i: A[r,c] -= v_r conj(tau) w_c;
+    // column i keeps v_r
+    for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) vloc[lr] = cmul(R(lr, i), scq);
     double sqp = 0.0;
     for (int c = i + 1 + tid; c < n; c += blockDim.x) {
-      cplx s0 = mk(0, 0), s1 = mk(0, 0), s2 = mk(0, 0), s3 = mk(0, 0);
-      int gg = 0;
-      for (; gg + 4 <= G; gg += 4) {
-        s0 = cadd(s0, __ldcg(pc + (size_t)(gg + 0) * pstride + c));
-        s1 = cadd(s1, __ldcg(pc + (size_t)(gg + 1) * pstride + c));
-        s2 = cadd(s2, __ldcg(pc + (size_t)(gg + 2) * pstride + c));
-        s3 = cadd(s3, __ldcg(pc + (size_t)(gg + 3) * pstride + c));
-      }
-      for (; gg < G; ++gg) s0 = cadd(s0, __ldcg(pc + (size_t)gg * pstride + c));
-      const cplx psum = cadd(cadd(s0, s1), cadd(s2, s3));
-      const cplx a_ic = __ldcg(rowb + c);
-      const cplx w = cadd(a_ic, cmul(cscq, psum));
-      const cplx nr = csub(a_ic, cmul(ctq, w));
-      wv[c] = w;
+      fv[c] = __ldcg(fvg + c);
+      const cplx nr = __ldcg(nrg + c);
       nrow[c] = nr;
       if (c >= i + 2) sqp += cabs2(nr);
     }
-    sqp = block_sum(sqp, dred);  // its barriers also publish wv / nrow
-    // left update of own rows r > i (A[r,c] -= v_r conj(tau) w_c); column i
-    // then keeps v_r = A[r,i] * scale
+    sqp = block_sum(sqp, dred);  // its barriers also publish fv / nrow / vloc
     for (int c = i + 1 + tid; c < n; c += blockDim.x) {
-      const cplx f = cmul(ctq, wv[c]);
-      for (int lr = lr0; lr < nact; ++lr) R(lr, c) = csub(R(lr, c), cmul(cmul(R(lr, i), scq), f));
+      const cplx f = fv[c];
+      const cplx nf = mk(-f.x, -f.y);
+      for (int lr = lr0; lr < nact; ++lr) R(lr, c) = cfma(vloc[lr], nf, R(lr, c));
     }
-    __syncthreads();
-    for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) R(lr, i) = cmul(R(lr, i), scq);
+    for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) R(lr, i) = vloc[lr];
     if (owner && tid == 0) {
       R(i / G, i) = bc[2];
       dg[i] = bc[2].x;
@@ -189,7 +197,8 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
       for (int c = i + 1 + lane; c < n; c += 32) dot = cfma(R(lr, c), uv[c], dot);
       dot = warp_sum(dot);
       const cplx f = cmul(tp, dot);
-      for (int c = i + 1 + lane; c < n; c += 32) R(lr, c) = csub(R(lr, c), cmul(f, cconj(uv[c])));
+      const cplx nf = mk(-f.x, -f.y);
+      for (int c = i + 1 + lane; c < n; c += 32) R(lr, c) = cfma(nf, cconj(uv[c]), R(lr, c));
     }
     __syncthreads();
   }
@@ -202,10 +211,10 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
 
 int gebrd_grid(int n, int* nloc_out, size_t* smem_out) {
   const DevInfo& di = dev_info();
-  int G = std::max(1, std::min(di.sm_count, (n + 3) / 4));
+  int G = std::max(1, std::min(di.sm_count, (n + 2) / 3));
   for (;;) {
     const int nloc = (n + G - 1) / G;
-    const size_t smem = ((size_t)nloc * n + 3 * (size_t)n) * sizeof(cplx);
+    const size_t smem = ((size_t)nloc * n + 3 * (size_t)n + nloc) * sizeof(cplx);
     if (smem + 8192 <= (size_t)di.max_smem_optin) {
       *nloc_out = nloc;
       *smem_out = smem;
@@ -229,7 +238,7 @@ cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cpl
   size_t smem;
   const int G = gebrd_grid(n, &nloc, &smem);
   if (G <= 0) return cudaErrorInvalidValue;
-  if ((size_t)2 * G * (n + 1) > ws.pc_elems || (size_t)2 * n > ws.wfin_elems || 2 * G > 1024)
+  if ((size_t)2 * G * (n + 1) > ws.pc_elems || (size_t)6 * n > ws.wfin_elems || 2 * G > 1024)
     return cudaErrorInvalidValue;
   cudaError_t err = cudaFuncSetAttribute(gebrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -370,38 +379,70 @@ cudaError_t bd_sigma(const double* d, const double* e, int n, float2* a2, double
   bd_sigma_kernel<<<(n + warps - 1) / warps, 32 * warps, 0, s>>>(a2, info, n, sig);
   return cudaGetLastError();
 }
-
-// Rank rule on the sorted values (the same rule as rank_select).
-__global__ void bd_rank_kernel(const double* sig, int n, const double* eps_hat, int cap, int forced,
-                               int* out_int, double* out_dbl, double* tail2) {
-  if (threadIdx.x != 0) return;
-  tail2[n] = 0.0;
-  for (int r = n - 1; r >= 0; --r) tail2[r] = tail2[r + 1] + sig[r] * sig[r];
+// Rank rule on the sorted values (the same rule as rank_select), one CTA:
+// suffix sums of sigma^2 by a block scan, the rank as the smallest index
+// that passes the test.
+constexpr int kRankThreads = 256;
+__global__ void __launch_bounds__(kRankThreads)
+bd_rank_kernel(const double* __restrict__ sig, int n, const double* __restrict__ eps_hat, int cap,
+               int forced, int* __restrict__ out_int, double* __restrict__ out_dbl,
+               double* __restrict__ tail2) {
+  __shared__ double wtot[kRankThreads / 32];
+  __shared__ int rmin[2];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int per = (n + kRankThreads - 1) / kRankThreads;
+  const int a = min(n, tid * per), b = min(n, a + per);
+  double own = 0.0;
+  for (int r = a; r < b; ++r) own += sig[r] * sig[r];
+  // suffix sum over threads: inclusive from the right within the warp
+  double suf = own;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double v = __shfl_down_sync(0xffffffffu, suf, o);
+    if (lane + o < 32) suf += v;
+  }
+  if (lane == 0) wtot[wid] = suf;
+  if (tid == 0) {
+    rmin[0] = n;
+    rmin[1] = n;
+  }
+  __syncthreads();
+  double after = 0.0;  // sum over later warps
+  for (int w = wid + 1; w < kRankThreads / 32; ++w) after += wtot[w];
+  // tail2[r] = sum_{q >= r} sig_q^2 for this thread's chunk
+  double run = suf - own + after;  // everything after this chunk
+  for (int r = b - 1; r >= a; --r) {
+    run += sig[r] * sig[r];
+    tail2[r] = run;
+  }
+  if (tid == 0) tail2[n] = 0.0;
+  __syncthreads();
   const double eh = *eps_hat;
-  int rho_tol = n;
-  for (int r = 1; r <= n; ++r)
-    if (sqrt(tail2[r]) <= eh) {
-      rho_tol = r;
-      break;
-    }
-  int rho = forced > 0 ? forced : (rho_tol < cap ? rho_tol : cap);
-  rho = rho < 1 ? 1 : (rho > n ? n : rho);
-  // kept values at the noise level of a factorisation of B (their vectors
-  // are not determined by B and are completed instead)
-  const double thr = 2.0 * n * DBL_EPSILON * sqrt(tail2[0]);
-  int kt = 0;
-  while (kt < rho && sig[kt] > thr) ++kt;
-  out_int[0] = rho;
-  out_int[1] = rho_tol;
-  out_int[2] = kt;
-  out_dbl[0] = sqrt(tail2[rho]);
-  out_dbl[1] = sig[rho - 1];
-  out_dbl[2] = tail2[0];
+  const double fro = sqrt(tail2[0]);
+  const double thr = 2.0 * n * DBL_EPSILON * fro;
+  for (int r = 1 + tid; r <= n; r += kRankThreads)
+    if (sqrt(tail2[r]) <= eh) atomicMin(&rmin[0], r);
+  for (int k = tid; k < n; k += kRankThreads)
+    if (!(sig[k] > thr)) atomicMin(&rmin[1], k);
+  __syncthreads();
+  if (tid == 0) {
+    const int rho_tol = rmin[0];
+    int rho = forced > 0 ? forced : (rho_tol < cap ? rho_tol : cap);
+    rho = rho < 1 ? 1 : (rho > n ? n : rho);
+    // kept values at the noise level of a factorisation of B (their vectors
+    // are not determined by B and are completed instead)
+    const int kt = min(rmin[1], rho);
+    out_int[0] = rho;
+    out_int[1] = rho_tol;
+    out_int[2] = kt;
+    out_dbl[0] = sqrt(tail2[rho]);
+    out_dbl[1] = sig[rho - 1];
+    out_dbl[2] = tail2[0];
+  }
 }
 
 cudaError_t bd_rank(const double* sig, int n, const double* eps_hat, int cap, int forced, int* out_int,
                     double* out_dbl, double* tail2, cudaStream_t s) {
-  bd_rank_kernel<<<1, 32, 0, s>>>(sig, n, eps_hat, cap, forced, out_int, out_dbl, tail2);
+  bd_rank_kernel<<<1, kRankThreads, 0, s>>>(sig, n, eps_hat, cap, forced, out_int, out_dbl, tail2);
   return cudaGetLastError();
 }
 
@@ -416,80 +457,92 @@ DV double hash_unit(unsigned a, unsigned b) {
   return (double)(h & 0xFFFFFFu) * (1.0 / 16777216.0) - 0.5;
 }
 
-// Per-thread scratch of the tridiagonal solver: six arrays of length N,
-// interleaved by lane so that a warp's accesses coalesce.
-struct LaneArrays {
-  double* base;
-  int N;
-  DV double& at(int arr, int i) const { return base[((size_t)arr * N + i) * 32]; }
-};
+// Solver arrays of T_GK - lam I (length N each) in shared memory.
 enum { L_DINV = 0, L_DU = 1, L_DU2 = 2, L_DL = 3, L_PV = 4, L_B = 5 };
-constexpr int kLaneArrays = 6;
+constexpr int kSolveArrays = 6;
 
-// LU with partial pivoting of T_GK - lam I (scaled: off-diagonals a_k / amax).
-DV void gk_factor(const double* d, const double* e, int n, double inv, double lam, LaneArrays w) {
+// LU with partial pivoting of T_GK - lam I (scaled: off-diagonals a_k / amax);
+// one thread.  Row i of U holds (1 / pivot, super, second super).
+DV void gk_factor(const double* d, const double* e, int n, double inv, double lam, double* w) {
   const int N = 2 * n;
+  double* Dinv = w + L_DINV * N;
+  double* DU = w + L_DU * N;
+  double* DU2 = w + L_DU2 * N;
+  double* DL = w + L_DL * N;
+  double* PV = w + L_PV * N;
   const double tiny = 4.0 * DBL_EPSILON;
   auto off = [&](int k) { return ((k & 1) ? e[k >> 1] : d[k >> 1]) * inv; };
   auto guard = [&](double p) { return fabs(p) < tiny ? (p < 0.0 ? -tiny : tiny) : p; };
   double di = -lam, dui = (N > 1) ? off(0) : 0.0;
+  double sub = (N > 1) ? off(0) : 0.0;
   for (int i = 0; i < N - 1; ++i) {
-    const double sub = off(i), dn = -lam, un = (i + 1 < N - 1) ? off(i + 1) : 0.0;
+    const double dn = -lam, un = (i + 1 < N - 1) ? off(i + 1) : 0.0;
     if (fabs(di) >= fabs(sub)) {
       const double piv = guard(di);
       const double f = sub / piv;
-      w.at(L_DINV, i) = 1.0 / piv;
-      w.at(L_DU, i) = dui;
-      w.at(L_DU2, i) = 0.0;
-      w.at(L_DL, i) = f;
-      w.at(L_PV, i) = 0.0;
+      Dinv[i] = 1.0 / piv;
+      DU[i] = dui;
+      DU2[i] = 0.0;
+      DL[i] = f;
+      PV[i] = 0.0;
       di = dn - f * dui;
       dui = un;
     } else {
       // rows i and i+1 swapped: new row i = (sub, dn, un)
       const double f = di / sub;
-      w.at(L_DINV, i) = 1.0 / sub;
-      w.at(L_DU, i) = dn;
-      w.at(L_DU2, i) = un;
-      w.at(L_DL, i) = f;
-      w.at(L_PV, i) = 1.0;
+      Dinv[i] = 1.0 / sub;
+      DU[i] = dn;
+      DU2[i] = un;
+      DL[i] = f;
+      PV[i] = 1.0;
       di = dui - f * dn;
       dui = -f * un;
     }
+    sub = un;  // the sub-diagonal of row i+2 equals the super-diagonal off(i+1)
   }
-  w.at(L_DINV, N - 1) = 1.0 / guard(di);
+  Dinv[N - 1] = 1.0 / guard(di);
 }
 
-DV void gk_solve(int N, LaneArrays w) {
+// Solve with the factors, in place on B; one thread.
+DV void gk_solve(int N, double* w) {
+  const double* Dinv = w + L_DINV * N;
+  const double* DU = w + L_DU * N;
+  const double* DU2 = w + L_DU2 * N;
+  const double* DL = w + L_DL * N;
+  const double* PV = w + L_PV * N;
+  double* B = w + L_B * N;
+  double cur = B[0];
   for (int i = 0; i < N - 1; ++i) {
-    const double bi = w.at(L_B, i), bn = w.at(L_B, i + 1), f = w.at(L_DL, i);
-    if (w.at(L_PV, i) != 0.0) {
-      w.at(L_B, i) = bn;
-      w.at(L_B, i + 1) = bi - f * bn;
+    const double bn = B[i + 1], f = DL[i];
+    if (PV[i] != 0.0) {
+      B[i] = bn;
+      cur = cur - f * bn;
     } else {
-      w.at(L_B, i + 1) = bn - f * bi;
+      B[i] = cur;
+      cur = bn - f * cur;
     }
   }
-  double x2 = 0.0, x1 = w.at(L_B, N - 1) * w.at(L_DINV, N - 1);
-  w.at(L_B, N - 1) = x1;
+  double x2 = 0.0, x1 = cur * Dinv[N - 1];
+  B[N - 1] = x1;
   for (int i = N - 2; i >= 0; --i) {
-    const double x = (w.at(L_B, i) - w.at(L_DU, i) * x1 - w.at(L_DU2, i) * x2) * w.at(L_DINV, i);
-    w.at(L_B, i) = x;
+    const double x = (B[i] - DU[i] * x1 - DU2[i] * x2) * Dinv[i];
+    B[i] = x;
     x2 = x1;
     x1 = x;
   }
 }
 
-// One thread per cluster of kept values (consecutive values closer than
+// One warp per cluster of kept values (consecutive values closer than
 // 1e-3 sigma_max): inverse iteration for each member, re-orthogonalised
-// against the members before it.  X (n x nvec, ldx) receives the
-// normalised left vectors u_k.  Every k < nvec is above the noise level
-// (the caller passes the count of such values).
+// against the members before it.  Lane 0 runs the tridiagonal recurrences
+// out of shared memory; the warp does the products and norms.  X (n x
+// nvec, ldx) receives the normalised left vectors u_k.  Every k < nvec is
+// above the noise level (the caller passes the count of such values).
 __global__ void bd_vectors_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
                                   const double* __restrict__ info, const double* __restrict__ sig,
-                                  int nvec, double* __restrict__ X, int ldx,
-                                  double* __restrict__ scratch, double* __restrict__ Zs) {
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+                                  int nvec, double* __restrict__ X, int ldx, double* __restrict__ Zs) {
+  extern __shared__ __align__(16) double vsm[];  // kSolveArrays * N
+  const int k0 = blockIdx.x, lane = threadIdx.x;
   const int N = 2 * n;
   if (k0 >= nvec) return;
   const double amax = info[0];
@@ -499,34 +552,40 @@ __global__ void bd_vectors_kernel(const double* __restrict__ d, const double* __
   int k1 = k0 + 1;
   while (k1 < nvec && sig[k1 - 1] - sig[k1] < gap_tol) ++k1;
   const double inv = 1.0 / amax;
-  const int lane = k0 & 31, warp = k0 >> 5;
-  LaneArrays w{scratch + (size_t)warp * kLaneArrays * N * 32 + lane, N};
+  double* B = vsm + L_B * N;
   for (int k = k0; k < k1; ++k) {
-    const double lam = sig[k] * inv;
-    gk_factor(d, e, n, inv, lam, w);
-    for (int i = 0; i < N; ++i) w.at(L_B, i) = 1.0 + 0.25 * hash_unit((unsigned)i, (unsigned)k);
+    if (lane == 0) gk_factor(d, e, n, inv, sig[k] * inv, vsm);
+    for (int i = lane; i < N; i += 32) B[i] = 1.0 + 0.25 * hash_unit((unsigned)i, (unsigned)k);
+    __syncwarp();
     for (int it = 0; it < 3; ++it) {
-      gk_solve(N, w);
+      if (lane == 0) gk_solve(N, vsm);
+      __syncwarp();
       for (int j = k0; j < k; ++j) {
         const double* zj = Zs + (size_t)j * N;
         double dot = 0.0;
-        for (int i = 0; i < N; ++i) dot += zj[i] * w.at(L_B, i);
-        for (int i = 0; i < N; ++i) w.at(L_B, i) -= dot * zj[i];
+        for (int i = lane; i < N; i += 32) dot += zj[i] * B[i];
+        dot = warp_sum(dot);
+        for (int i = lane; i < N; i += 32) B[i] -= dot * zj[i];
+        __syncwarp();
       }
       double nrm = 0.0;
-      for (int i = 0; i < N; ++i) nrm += w.at(L_B, i) * w.at(L_B, i);
+      for (int i = lane; i < N; i += 32) nrm += B[i] * B[i];
+      nrm = warp_sum(nrm);
       const double s = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-      for (int i = 0; i < N; ++i) w.at(L_B, i) *= s;
+      for (int i = lane; i < N; i += 32) B[i] *= s;
+      __syncwarp();
     }
     double* zk = Zs + (size_t)k * N;
     double un = 0.0;
-    for (int i = 0; i < N; ++i) {
-      const double z = w.at(L_B, i);
+    for (int i = lane; i < N; i += 32) {
+      const double z = B[i];
       zk[i] = z;
       if (i & 1) un += z * z;
     }
+    un = warp_sum(un);
     const double s = un > 0.0 ? 1.0 / sqrt(un) : 0.0;
-    for (int i = 0; i < n; ++i) X[i + (size_t)ldx * k] = zk[2 * i + 1] * s;
+    for (int i = lane; i < n; i += 32) X[i + (size_t)ldx * k] = B[2 * i + 1] * s;
+    __syncwarp();
   }
 }
 
@@ -566,16 +625,16 @@ __global__ void bd_complete_kernel(int n, int kt, int nvec, double* __restrict__
   }
 }
 
-size_t bd_scratch_doubles(int n, int nvec) {
-  return (size_t)kLaneArrays * 2 * n * 32 * (size_t)((nvec + 31) / 32);
-}
 
 cudaError_t bd_vectors(const double* d, const double* e, int n, const double* info, const double* sig,
-                       int kt, int nvec, double* X, int ldx, double* scratch, double* Zs, cudaStream_t s) {
+                       int kt, int nvec, double* X, int ldx, double* Zs, cudaStream_t s) {
   if (nvec <= 0) return cudaSuccess;
   if (kt > 0) {
-    bd_vectors_kernel<<<(kt + 31) / 32, 32, 0, s>>>(d, e, n, info, sig, kt, X, ldx, scratch, Zs);
-    cudaError_t err = cudaGetLastError();
+    const size_t smem = sizeof(double) * kSolveArrays * 2 * (size_t)n;
+    cudaError_t err = cudaFuncSetAttribute(bd_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    bd_vectors_kernel<<<kt, 32, smem, s>>>(d, e, n, info, sig, kt, X, ldx, Zs);
+    err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
   if (kt < nvec) {
@@ -587,36 +646,49 @@ cudaError_t bd_vectors(const double* d, const double* e, int n, const double* in
 
 // ---- 4. back-transformation -------------------------------------------------------------------
 // u_k <- Q u_k with Q = H_0 H_1 ... H_{n-1} (reflector j: unit entry at j,
-// tail A[j+1:n, j], tau[j]).  One warp per vector (the FP64 work of a
-// vector is small; spreading the vectors over SMs is what counts).  The
-// result goes to U (n x nvec, ldu) and to Xp (mrows x nvec, ldp, zero below
-// row n).
-__global__ void bd_back_kernel(const cplx* __restrict__ A, int lda, const cplx* __restrict__ tauq, int n,
-                               const double* __restrict__ Xr, int ldx, int nvec, cplx* __restrict__ U,
-                               int ldu, cplx* __restrict__ Xp, int ldp, int mrows) {
+// tail A[j+1:n, j], tau[j]).  One vector per CTA, so that the FP64 work
+// (about 10 n^2 / 2 operations per vector) spreads over many SMs; warp 0
+// applies reflector j while warp 1 stages reflector j-1 in shared memory.
+// The result goes to U (n x nvec, ldu) and to Xp (mrows x nvec, ldp, zero
+// below row n).
+__global__ void __launch_bounds__(64)
+bd_back_kernel(const cplx* __restrict__ A, int lda, const cplx* __restrict__ tauq, int n,
+               const double* __restrict__ Xr, int ldx, int nvec, cplx* __restrict__ U, int ldu,
+               cplx* __restrict__ Xp, int ldp, int mrows) {
   extern __shared__ __align__(16) unsigned char bk_smem[];
-  cplx* x = reinterpret_cast<cplx*>(bk_smem);
-  const int k = blockIdx.x, lane = threadIdx.x;
+  cplx* vb = reinterpret_cast<cplx*>(bk_smem);  // [2][n] staged reflectors
+  cplx* x = vb + 2 * (size_t)n;                 // [n]
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x;
   if (k >= nvec) return;
-  for (int i = lane; i < n; i += 32) x[i] = mk(Xr[i + (size_t)ldx * k], 0.0);
-  __syncwarp();
-  for (int j = n - 1; j >= 0; --j) {
-    const cplx t = tauq[j];
-    if (t.x == 0.0 && t.y == 0.0) continue;
-    cplx acc = mk(0, 0);
-    for (int i = j + lane; i < n; i += 32) {
-      const cplx v = (i == j) ? mk(1, 0) : A[i + (size_t)lda * j];
-      acc = cfmac(v, x[i], acc);
-    }
-    acc = warp_sum(acc);
-    const cplx f = cmul(t, acc);
-    for (int i = j + lane; i < n; i += 32) {
-      const cplx v = (i == j) ? mk(1, 0) : A[i + (size_t)lda * j];
-      x[i] = csub(x[i], cmul(v, f));
-    }
-    __syncwarp();
+  auto stage = [&](int j) {  // reflector j into vb[j & 1][j..n)
+    cplx* v = vb + (size_t)(j & 1) * n;
+    for (int i = j + lane; i < n; i += 32) v[i] = (i == j) ? mk(1, 0) : __ldg(A + i + (size_t)lda * j);
+  };
+  if (wid == 0) {
+    for (int i = lane; i < n; i += 32) x[i] = mk(Xr[i + (size_t)ldx * k], 0.0);
+  } else {
+    stage(n - 1);
   }
-  for (int i = lane; i < mrows; i += 32) {
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    if (wid == 1) {
+      if (j > 0) stage(j - 1);
+    } else {
+      const cplx t = __ldg(tauq + j);
+      if (t.x != 0.0 || t.y != 0.0) {
+        const cplx* v = vb + (size_t)(j & 1) * n;
+        cplx acc = mk(0, 0);
+        for (int i = j + lane; i < n; i += 32) acc = cfmac(v[i], x[i], acc);
+        acc = warp_sum(acc);
+        const cplx f = cmul(t, acc);
+        const cplx nf = mk(-f.x, -f.y);
+        for (int i = j + lane; i < n; i += 32) x[i] = cfma(v[i], nf, x[i]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < mrows; i += blockDim.x) {
     const cplx v = (i < n) ? x[i] : mk(0, 0);
     if (i < n) U[i + (size_t)ldu * k] = v;
     Xp[i + (size_t)ldp * k] = v;
@@ -626,7 +698,10 @@ __global__ void bd_back_kernel(const cplx* __restrict__ A, int lda, const cplx* 
 cudaError_t bd_back(const cplx* A, int lda, const cplx* tauq, int n, const double* X, int ldx, int nvec,
                     cplx* U, int ldu, cplx* Xp, int ldp, int mrows, cudaStream_t s) {
   if (nvec <= 0) return cudaSuccess;
-  bd_back_kernel<<<nvec, 32, sizeof(cplx) * (size_t)n, s>>>(A, lda, tauq, n, X, ldx, nvec, U, ldu, Xp, ldp, mrows);
+  const size_t smem = sizeof(cplx) * (size_t)n * 3;
+  cudaError_t err = cudaFuncSetAttribute(bd_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  bd_back_kernel<<<nvec, 64, smem, s>>>(A, lda, tauq, n, X, ldx, nvec, U, ldu, Xp, ldp, mrows);
   return cudaGetLastError();
 }
 

@@ -54,7 +54,6 @@ struct RoundWs {
   double* bd_info = nullptr;  // 4
   double* bd_X = nullptr;     // kcap * kcap
   double* bd_Zs = nullptr;    // kcap * 2 kcap
-  double* bd_scr = nullptr;   // bd_scratch_doubles(kcap, kcap)
 };
 
 struct hopf_ctx {
@@ -295,7 +294,7 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   cudaFree(w.Rb); cudaFree(w.Mb); cudaFree(w.Jb); cudaFree(w.Ub); cudaFree(w.Sb);
   cudaFree(w.sig); cudaFree(w.perm);
   cudaFree(w.bd_d); cudaFree(w.bd_e); cudaFree(w.bd_tauq); cudaFree(w.bd_taup); cudaFree(w.bd_a2);
-  cudaFree(w.bd_info); cudaFree(w.bd_X); cudaFree(w.bd_Zs); cudaFree(w.bd_scr);
+  cudaFree(w.bd_info); cudaFree(w.bd_X); cudaFree(w.bd_Zs);
   w = RoundWs{};
   const size_t elems = std::max(need, w.elems);
   const int d = t->d;
@@ -323,7 +322,6 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   CK(dalloc(&w.bd_info, 4));
   CK(dalloc(&w.bd_X, (size_t)K * K));
   CK(dalloc(&w.bd_Zs, (size_t)2 * K * K));
-  CK(dalloc(&w.bd_scr, hk::bd_scratch_doubles(K, K)));
   w.elems = elems;
   w.d = d;
   w.kcap = K;
@@ -524,7 +522,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     // new core c = Q [U_rho; 0]
     if (use_bd) {
       const int kt = std::min(ctx->h_int[2], rnew);
-      LAUNCH(HOPF_K_SVD, 0, 0, (kt > 0) + (kt < rnew), hk::bd_vectors(w.bd_d, w.bd_e, pp, w.bd_info, w.sig, kt, rnew, w.bd_X, pp, w.bd_scr, w.bd_Zs, ctx->stream));
+      LAUNCH(HOPF_K_SVD, 0, 0, (kt > 0) + (kt < rnew), hk::bd_vectors(w.bd_d, w.bd_e, pp, w.bd_info, w.sig, kt, rnew, w.bd_X, pp, w.bd_Zs, ctx->stream));
       LAUNCH(HOPF_K_SVD, 0, 0, 1, hk::bd_back(w.Mb, pp, w.bd_tauq, pp, w.bd_X, pp, rnew, w.Ub, pp, t->cores[c], Mrows, Mrows, ctx->stream));
     } else if (case1) {
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::gather_u(w.Mb, pp, pp, w.perm, w.sig, 1, rnew, t->cores[c], Mrows, Mrows, w.Ub, pp, ctx->stream));

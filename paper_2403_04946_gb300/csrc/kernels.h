@@ -86,9 +86,9 @@ cudaError_t bd_rank(const double* sig, int n, const double* eps_hat, int cap, in
                     double* out_dbl, double* tail2, cudaStream_t s);
 // Left singular vectors of B: columns k < kt by inverse iteration, columns
 // kt..nvec-1 by orthonormal completion; X (n x nvec, ldx), real.
-size_t bd_scratch_doubles(int n, int nvec);
+// Zs: nvec x 2n doubles of scratch (the T_GK eigenvectors).
 cudaError_t bd_vectors(const double* d, const double* e, int n, const double* info, const double* sig,
-                       int kt, int nvec, double* X, int ldx, double* scratch, double* Zs, cudaStream_t s);
+                       int kt, int nvec, double* X, int ldx, double* Zs, cudaStream_t s);
 // U = Q X -> U (n x nvec, ldu) and Xp (mrows x nvec, ldp, zero below row n).
 cudaError_t bd_back(const cplx* A, int lda, const cplx* tauq, int n, const double* X, int ldx, int nvec,
                     cplx* U, int ldu, cplx* Xp, int ldp, int mrows, cudaStream_t s);
