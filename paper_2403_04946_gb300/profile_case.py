@@ -5,7 +5,7 @@ operator apply (hopf_apply_op) and one rounding (tt_round) at rank 6r, plus
 one fused hopf_step when --step is given.  Sized by --d/--n/--r so a capture
 stays small (d=4, n=128, r=64 holds about 2.5 GB on the device).
 
-  python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64
+  python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64 [--mixed]
 """
 from __future__ import annotations
 
@@ -26,12 +26,14 @@ def main():
     ap.add_argument("--r", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--step", action="store_true")
+    ap.add_argument("--mixed", action="store_true", help="HOPF_MIXED precision")
     args = ap.parse_args()
     from paper_2403_04946_gb300 import binding
     import synthetic
 
     cores, _ = synthetic.saturated_tt_cores(args.d, args.n, args.r, seed=0)
-    ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r, L=12.4)
+    ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r, L=12.4,
+                          precision=binding.HOPF_MIXED if args.mixed else binding.HOPF_FP64)
     t = ctx.tt_from_host(cores, max_rank=args.r)
     big = ctx.tt_create(6 * args.r)
     t0 = time.time()
