@@ -87,6 +87,21 @@ DV void df_cmac(df2& acc, const df2& a, const df2& b) {
   df_mac(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
 }
 
+// a + b for complex double-float values (TwoSum on each part, then
+// renormalised).
+DV void df_add_part(float& h, float& l, float bh, float bl) {
+  const float s = h + bh;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (bh - bb) + l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+DV df2 df_cadd(df2 a, const df2& b) {
+  df_add_part(a.rh, a.rl, b.rh, b.rl);
+  df_add_part(a.ih, a.il, b.ih, b.il);
+  return a;
+}
+
 // Sum over a warp (all 32 lanes active).
 DV double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

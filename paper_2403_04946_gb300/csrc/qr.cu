@@ -90,26 +90,28 @@ __device__ void update_x(const cplx* P, int R, int r0, int lo, int hi, int nbk, 
   }
 }
 
-// Mixed-precision versions: the panel V in shared memory as double-float
-// values (hi, lo in FP32, same 16 bytes per complex as FP64), X stored in
-// FP64; products and sums in double-float arithmetic on the FP32 pipe,
-// partials handed on in FP64, and the update added to X in FP64.
+// Mixed-precision versions: the panel V in shared memory and the matrix X
+// both as double-float values (hi, lo in FP32, the same 16 bytes per
+// complex as FP64); products and sums in double-float arithmetic on the
+// FP32 pipe, partials handed on in FP64.  X stays in double-float form for
+// the whole kernel, so the FP64 pipe (1/64 of the FP32 rate on this GPU)
+// sees no per-element conversions.
 template <int NB>
 __device__ void partial_vhx_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
-                              const cplx* X, int ldx, int ncol, cplx* out) {
+                              const df2* X, int ldx, int ncol, cplx* out) {
   // 16 reflectors per pass over the rows keep the double-float accumulators
   // in registers
   constexpr int CH = NB < 16 ? NB : 16;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int l = w; l < ncol; l += nw) {
-    const cplx* x = X + (size_t)ldx * l;
+    const df2* x = X + (size_t)ldx * l;
     for (int s0 = 0; s0 < nbk; s0 += CH) {
       df2 acc[CH];
 #pragma unroll
       for (int s = 0; s < CH; ++s) acc[s] = df_zero();
-      cplx xn = (lo + lane < hi) ? x[lo + lane] : mk(0, 0);
+      df2 xn = (lo + lane < hi) ? x[lo + lane] : df_zero();
       for (int i = lo + lane; i < hi; i += 32) {
-        const df2 xi = df_from(xn);
+        const df2 xi = xn;
         if (i + 32 < hi) xn = x[i + 32];
         const df2* pv = P + (i - r0) + (size_t)s0 * R;
 #pragma unroll
@@ -128,7 +130,7 @@ __device__ void partial_vhx_f(const df2* P, int R, int r0, int lo, int hi, int n
 }
 
 template <int NB>
-__device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk, cplx* X,
+__device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk, df2* X,
                            int ldx, int ncol, const cplx* w2) {
   // the column's coefficients -W2[:, l] live in shared memory (every lane
   // reads the same one: broadcast), the running update in registers
@@ -142,20 +144,41 @@ __device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
     }
     __syncwarp();
     if (l < ncol) {
-      cplx* x = X + (size_t)ldx * l;
-      cplx xn = (lo + lane < hi) ? x[lo + lane] : mk(0, 0);
+      df2* x = X + (size_t)ldx * l;
+      df2 xn = (lo + lane < hi) ? x[lo + lane] : df_zero();
       for (int i = lo + lane; i < hi; i += 32) {
-        const cplx xi = xn;
+        const df2 xi = xn;
         if (i + 32 < hi) xn = x[i + 32];
         const df2* pv = P + (i - r0);
         df2 dlt = df_zero();
 #pragma unroll 8
         for (int s = 0; s < NB; ++s)
           if (s < nbk) df_cmac(dlt, pv[(size_t)s * R], wsh[w][s]);
-        x[i] = cadd(xi, df_to(dlt));
+        x[i] = df_cadd(xi, dlt);
       }
     }
     __syncwarp();
+  }
+}
+
+// Rows [r0, r1) of columns [c0, c1) of the column-major A (lda) between
+// FP64 and double-float form, in place (one CTA's rows).
+__device__ void rows_to_df(cplx* A, int lda, int r0, int r1, int c0, int c1) {
+  const int nr = r1 - r0;
+  if (nr <= 0) return;
+  for (long long e = threadIdx.x; e < (long long)nr * (c1 - c0); e += blockDim.x) {
+    const int c = c0 + (int)(e / nr), i = r0 + (int)(e % nr);
+    cplx* p = A + i + (size_t)lda * c;
+    *reinterpret_cast<df2*>(p) = df_from(*p);
+  }
+}
+__device__ void rows_to_fp64(cplx* A, int lda, int r0, int r1, int c0, int c1) {
+  const int nr = r1 - r0;
+  if (nr <= 0) return;
+  for (long long e = threadIdx.x; e < (long long)nr * (c1 - c0); e += blockDim.x) {
+    const int c = c0 + (int)(e / nr), i = r0 + (int)(e % nr);
+    cplx* p = A + i + (size_t)lda * c;
+    *p = df_to(*reinterpret_cast<const df2*>(p));
   }
 }
 
@@ -196,13 +219,22 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
   const int p = min(m, k);
   const size_t pstride = ws.pc_elems / G;
   GridSync gs{ws.bar, 0u};
+  // Mixed precision: this CTA's rows of A in double-float form until each
+  // column is factored (panel columns are written back in FP64).
+  if (MIXED) {
+    rows_to_df(A, lda, r0, r1, 0, k);
+    __syncthreads();
+  }
 
   for (int j0 = 0, panel = 0; j0 < p; j0 += nb, ++panel) {
     const int nbk = min(nb, p - j0);
     const int lo = max(r0, j0);  // rows of this CTA that the panel touches
-    // load panel rows [r0, r1) of columns j0..j0+nbk-1
+    // load panel rows [r0, r1) of columns j0..j0+nbk-1 (FP64 in shared memory)
     for (int t = 0; t < nbk; ++t)
-      for (int i = r0 + tid; i < r1; i += blockDim.x) P[(size_t)t * R + (i - r0)] = A[i + (size_t)lda * (j0 + t)];
+      for (int i = r0 + tid; i < r1; i += blockDim.x) {
+        const size_t e = i + (size_t)lda * (j0 + t);
+        P[(size_t)t * R + (i - r0)] = MIXED ? df_to(reinterpret_cast<const df2*>(A)[e]) : A[e];
+      }
     __syncthreads();
 
     for (int t = 0; t < nbk; ++t) {
@@ -299,7 +331,17 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     const int c0 = j0 + nbk;
     const int nt = k - c0;
     const int ncol = nbk + nt;
-    {
+    if (MIXED) {
+      cplx* out = ws.pc + (size_t)g * pstride;
+      // the panel in double-float form; the Gram block (its columns are the
+      // reflectors themselves) and the trailing products on the FP32 pipe
+      to_df_in_place(P, nbk * R);
+      const df2* Pd = reinterpret_cast<const df2*>(P);
+      partial_vhx_f<NB>(Pd, R, r0, lo, r1, nbk, Pd - r0, R, nbk, out);
+      if (nt > 0)
+        partial_vhx_f<NB>(Pd, R, r0, lo, r1, nbk, reinterpret_cast<const df2*>(A) + (size_t)lda * c0, lda, nt,
+                          out + (size_t)nbk * nbk);
+    } else {
       cplx* out = ws.pc + (size_t)g * pstride;
       // Gram block: columns are the reflectors themselves (from shared memory)
       for (int l = wid; l < nbk; l += nw) {
@@ -320,17 +362,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
           }
       }
       __syncthreads();
-      if (nt > 0) {
-        if (MIXED) {
-          // the reflector Gram above stays FP64 (it builds T); the trailing
-          // products run in double-float arithmetic on the FP32 pipe
-          to_df_in_place(P, nbk * R);
-          partial_vhx_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt,
-                            out + (size_t)nbk * nbk);
-        } else {
-          partial_vhx<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, out + (size_t)nbk * nbk);
-        }
-      }
+      if (nt > 0) partial_vhx<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, out + (size_t)nbk * nbk);
     }
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
@@ -388,13 +420,15 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     // S4: trailing update over this CTA's rows
     if (nt > 0) {
       if (MIXED)
-        update_x_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt,
-                       ws.wfin + (size_t)nbk * nbk);
+        update_x_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, reinterpret_cast<df2*>(A) + (size_t)lda * c0,
+                       lda, nt, ws.wfin + (size_t)nbk * nbk);
       else
         update_x<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, ws.wfin + (size_t)nbk * nbk);
     }
     __syncthreads();
   }
+  // columns never factored (k > m) go back to FP64
+  if (MIXED && k > p) rows_to_fp64(A, lda, r0, r1, p, k);
 }
 
 template <int NB, bool MIXED>
@@ -410,6 +444,11 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
   const size_t pstride = ws.pc_elems / G;
   const int npanel = (p + nb - 1) / nb;
   GridSync gs{ws.bar, 0u};
+  // Mixed precision: this CTA's rows of C in double-float form throughout
+  if (MIXED) {
+    rows_to_df(C, ldc, r0, r1, 0, q);
+    __syncthreads();
+  }
   for (int panel = npanel - 1; panel >= 0; --panel) {
     const int j0 = panel * nb;
     const int nbk = min(nb, p - j0);
@@ -427,7 +466,8 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
     for (int e = tid; e < nbk * nbk; e += blockDim.x) Ts[e] = Tg[(size_t)panel * nb * nb + e];
     __syncthreads();
     if (MIXED)
-      partial_vhx_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
+      partial_vhx_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, reinterpret_cast<const df2*>(C), ldc, q,
+                        ws.pc + (size_t)g * pstride);
     else
       partial_vhx<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
     grid_sync(gs);
@@ -454,13 +494,14 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
     if (MIXED)
-      update_x_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, C, ldc, q, ws.wfin);
+      update_x_f<NB>(reinterpret_cast<const df2*>(P), R, r0, lo, r1, nbk, reinterpret_cast<df2*>(C), ldc, q, ws.wfin);
     else
       update_x<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.wfin);
     __syncthreads();
     // No barrier needed here: the next panel writes wfin only after its
     // first grid_sync, which every CTA reaches after finishing this update.
   }
+  if (MIXED) rows_to_fp64(C, ldc, r0, r1, 0, q);
 }
 
 static void pick_layout(int m, int* G, int* R, int* nb, size_t* smem) {
