@@ -30,6 +30,62 @@ struct QrSmem {
 __device__ __forceinline__ cplx ld_cg(const cplx* p) { return __ldcg(p); }
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 
+// Warp reduce-scatter of CH per-lane values: afterwards a[0] of lane l
+// holds the sum over all 32 lanes of value number rs_index<CH>(l), with the
+// lanes that differ only in their low log2(32/CH) bits holding the same sum
+// (rs_writer picks one of them).  31 exchanges for 32 values instead of 5
+// per value: on this GPU the FP64 additions of a per-value warp sum cost
+// more than the products they reduce.
+template <int CH>
+DV int rs_index(int lane) {
+  int s = 0, o = 16;
+#pragma unroll
+  for (int h = CH / 2; h >= 1; h >>= 1, o >>= 1)
+    if (lane & o) s += h;
+  return s;
+}
+template <int CH>
+DV bool rs_writer(int lane) {
+  return (lane & (32 / CH - 1)) == 0;
+}
+template <int CH>
+DV void reduce_scatter(cplx (&a)[CH], int lane) {
+  int o = 16;
+#pragma unroll
+  for (int h = CH / 2; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const cplx send = up ? a[j] : a[j + h];
+      const cplx keep = up ? a[j + h] : a[j];
+      a[j] = mk(keep.x + __shfl_xor_sync(0xffffffffu, send.x, o), keep.y + __shfl_xor_sync(0xffffffffu, send.y, o));
+    }
+  }
+  for (; o >= 1; o >>= 1) {
+    a[0].x += __shfl_xor_sync(0xffffffffu, a[0].x, o);
+    a[0].y += __shfl_xor_sync(0xffffffffu, a[0].y, o);
+  }
+}
+DV df2 df_shfl_xor(const df2& v, int o) {
+  return df2{__shfl_xor_sync(0xffffffffu, v.rh, o), __shfl_xor_sync(0xffffffffu, v.ih, o),
+             __shfl_xor_sync(0xffffffffu, v.rl, o), __shfl_xor_sync(0xffffffffu, v.il, o)};
+}
+template <int CH>
+DV void reduce_scatter(df2 (&a)[CH], int lane) {
+  int o = 16;
+#pragma unroll
+  for (int h = CH / 2; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const df2 send = up ? a[j] : a[j + h];
+      const df2 keep = up ? a[j + h] : a[j];
+      a[j] = df_cadd(keep, df_shfl_xor(send, o));
+    }
+  }
+  for (; o >= 1; o >>= 1) a[0] = df_cadd(a[0], df_shfl_xor(a[0], o));
+}
+
 // Partial products V^H X over this CTA's rows [lo, hi) (global row index),
 // V in shared memory (P, leading dimension R, rows offset r0), X column l
 // given by a pointer.  One warp per column; results to out[s + nbk * l].
@@ -53,13 +109,9 @@ __device__ void partial_vhx(const cplx* P, int R, int r0, int lo, int hi, int nb
       for (int s = 0; s < NB; ++s)
         if (s < nbk) acc[s] = cfmac(pv[(size_t)s * R], xi, acc[s]);
     }
-#pragma unroll
-    for (int s = 0; s < NB; ++s) {
-      if (s < nbk) {
-        cplx v = warp_sum(acc[s]);
-        if (lane == 0) out[s + (size_t)nbk * l] = v;
-      }
-    }
+    reduce_scatter<NB>(acc, lane);
+    const int s = rs_index<NB>(lane);
+    if (rs_writer<NB>(lane) && s < nbk) out[s + (size_t)nbk * l] = acc[0];
   }
 }
 
@@ -118,13 +170,9 @@ __device__ void partial_vhx_f(const df2* P, int R, int r0, int lo, int hi, int n
         for (int s = 0; s < CH; ++s)
           if (s0 + s < nbk) df_cmac_conj(acc[s], pv[(size_t)s * R], xi);
       }
-#pragma unroll
-      for (int s = 0; s < CH; ++s) {
-        if (s0 + s < nbk) {
-          cplx v = warp_sum(df_to(acc[s]));
-          if (lane == 0) out[s0 + s + (size_t)nbk * l] = v;
-        }
-      }
+      reduce_scatter<CH>(acc, lane);
+      const int s = s0 + rs_index<CH>(lane);
+      if (rs_writer<CH>(lane) && s < nbk) out[s + (size_t)nbk * l] = df_to(acc[0]);
     }
   }
 }
@@ -354,12 +402,9 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
           for (int s = 0; s < NB; ++s)
             if (s < nbk) acc[s] = cfmac(P[(size_t)s * R + (i - r0)], xi, acc[s]);
         }
-#pragma unroll
-        for (int s = 0; s < NB; ++s)
-          if (s < nbk) {
-            cplx v = warp_sum(acc[s]);
-            if (lane == 0) out[s + (size_t)nbk * l] = v;
-          }
+        reduce_scatter<NB>(acc, lane);
+        const int s = rs_index<NB>(lane);
+        if (rs_writer<NB>(lane) && s < nbk) out[s + (size_t)nbk * l] = acc[0];
       }
       __syncthreads();
       if (nt > 0) partial_vhx<NB>(P, R, r0, lo, r1, nbk, A + (size_t)lda * c0, lda, nt, out + (size_t)nbk * nbk);
