@@ -30,6 +30,29 @@ struct QrSmem {
 __device__ __forceinline__ cplx ld_cg(const cplx* p) { return __ldcg(p); }
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 
+// Loads of values other CTAs wrote before a grid barrier go to L2 (ld.cg):
+// this SM's L1 may hold the line from the previous use of the buffer.
+DV df2 ld_cg_df(const cplx* p) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  return df2{v.x, v.y, v.z, v.w};
+}
+
+// Block sum of a real double-float value (every thread gets the result).
+DV void df_block_sum(float& h, float& l, float2* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o >= 1; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add_part(h, l, h2, l2);
+  }
+  __syncthreads();
+  if (lane == 0) red[w] = make_float2(h, l);
+  __syncthreads();
+  h = red[0].x;
+  l = red[0].y;
+  for (int i = 1; i < nw; ++i) df_add_part(h, l, red[i].x, red[i].y);
+  __syncthreads();
+}
+
 // Warp reduce-scatter of CH per-lane values: afterwards a[0] of lane l
 // holds the sum over all 32 lanes of value number rs_index<CH>(l), with the
 // lanes that differ only in their low log2(32/CH) bits holding the same sum
@@ -259,6 +282,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
   cplx* wl = Ts + (size_t)nb * nb;  // [2*kNbMax]
   cplx* red = wl + 2 * kNbMax;      // [32]
   __shared__ double dred[32];
+  __shared__ float2 fred[32];
   __shared__ cplx bc[4];
 
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
@@ -274,37 +298,88 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     __syncthreads();
   }
 
+  // Per-CTA tail of the partial buffer, beyond what S1 uses: the in-panel
+  // partial dot products (two parities x nb) and, for the CTA that owns the
+  // pivot row, that row (two parities x nb).
+  const size_t tail0 = pstride - (size_t)4 * nb;
+  __shared__ cplx praw[kNbMax];
+
   for (int j0 = 0, panel = 0; j0 < p; j0 += nb, ++panel) {
     const int nbk = min(nb, p - j0);
     const int lo = max(r0, j0);  // rows of this CTA that the panel touches
-    // load panel rows [r0, r1) of columns j0..j0+nbk-1 (FP64 in shared memory)
+    // load panel rows [r0, r1) of columns j0..j0+nbk-1 into shared memory
+    // (FP64, or double-float in mixed precision)
     for (int t = 0; t < nbk; ++t)
       for (int i = r0 + tid; i < r1; i += blockDim.x) {
         const size_t e = i + (size_t)lda * (j0 + t);
-        P[(size_t)t * R + (i - r0)] = MIXED ? df_to(reinterpret_cast<const df2*>(A)[e]) : A[e];
+        P[(size_t)t * R + (i - r0)] = A[e];  // same 16 bytes in either form
       }
     __syncthreads();
 
+    // Panel factorisation with one grid barrier per column.  For column jj
+    // with x its entries below the diagonal, v = [1; x * scale] and
+    //   v^H a_l = a_l[jj] + conj(scale) * sum_{i>jj} conj(x_i) a_l[i],
+    // so before the barrier each CTA publishes sum |x_i|^2 and the raw sums
+    // over its own rows (and the owner of row jj publishes that row); after
+    // it every CTA forms the reflector and updates its own rows.
     for (int t = 0; t < nbk; ++t) {
       const int jj = j0 + t;
-      cplx* pt = P + (size_t)t * R;
-      // (1) partial squared norm of rows > jj
-      double sq = 0.0;
-      for (int i = max(lo, jj + 1) + tid; i < r1; i += blockDim.x) sq += cabs2(pt[i - r0]);
-      sq = block_sum(sq, dred);
-      if (tid == 0) {
-        ws.pr[g] = sq;
-        if (jj >= r0 && jj < r1) ws.scal[0] = pt[jj - r0];
+      const int par = t & 1;
+      const int nrem = nbk - t - 1;
+      const int ilo = max(lo, jj + 1);  // own rows strictly below jj
+      const int gown = jj / R;         // CTA owning row jj
+      cplx* myp = ws.pc + (size_t)g * pstride + tail0 + (size_t)par * nb;
+      cplx* rowp = ws.pc + (size_t)gown * pstride + tail0 + 2 * (size_t)nb + (size_t)par * nb;
+      double* prp = ws.pr + par * G;
+      // (a) partial sums over own rows > jj
+      if constexpr (MIXED) {
+        const df2* Pd = reinterpret_cast<const df2*>(P);
+        const df2* xt = Pd + (size_t)t * R;
+        float h = 0.f, l = 0.f;
+        for (int i = ilo + tid; i < r1; i += blockDim.x) {
+          const df2 x = xt[i - r0];
+          df_mac(h, l, x.rh, x.rl, x.rh, x.rl);
+          df_mac(h, l, x.ih, x.il, x.ih, x.il);
+        }
+        df_block_sum(h, l, fred);
+        if (tid == 0) prp[g] = (double)h + (double)l;
+        for (int c = wid; c < nrem; c += nw) {
+          const df2* pl = Pd + (size_t)(t + 1 + c) * R;
+          df2 acc = df_zero();
+          for (int i = ilo + lane; i < r1; i += 32) df_cmac_conj(acc, xt[i - r0], pl[i - r0]);
+          for (int o = 16; o >= 1; o >>= 1) acc = df_cadd(acc, df_shfl_xor(acc, o));
+          if (lane == 0) reinterpret_cast<df2*>(myp)[c] = acc;
+        }
+        if (g == gown)
+          for (int c = tid; c < nbk - t; c += blockDim.x)
+            reinterpret_cast<df2*>(rowp)[c] = Pd[(size_t)(t + c) * R + (jj - r0)];
+      } else {
+        const cplx* xt = P + (size_t)t * R;
+        double sq = 0.0;
+        for (int i = ilo + tid; i < r1; i += blockDim.x) sq += cabs2(xt[i - r0]);
+        sq = block_sum(sq, dred);
+        if (tid == 0) prp[g] = sq;
+        for (int c = wid; c < nrem; c += nw) {
+          const cplx* pl = P + (size_t)(t + 1 + c) * R;
+          cplx acc = mk(0, 0);
+          for (int i = ilo + lane; i < r1; i += 32) acc = cfmac(xt[i - r0], pl[i - r0], acc);
+          acc = warp_sum(acc);
+          if (lane == 0) myp[c] = acc;
+        }
+        if (g == gown)
+          for (int c = tid; c < nbk - t; c += blockDim.x) rowp[c] = P[(size_t)(t + c) * R + (jj - r0)];
       }
       grid_sync(gs);
       if (grid_failed(ws.bar)) return;
-      // (2) Householder vector (zlarfg conventions: beta real, v_jj = 1)
+      // (b) the reflector (zlarfg conventions: beta real, v_jj = 1), in FP64
       if (wid == 0) {
         double s2 = 0.0;
-        for (int gg = lane; gg < G; gg += 32) s2 += ld_cg(ws.pr + gg);
+        for (int gg = lane; gg < G; gg += 32) s2 += ld_cg(prp + gg);
         s2 = warp_sum(s2);
         if (lane == 0) {
-          const cplx al = ld_cg(ws.scal);
+          cplx al;
+          if constexpr (MIXED) al = df_to(ld_cg_df(rowp));
+          else al = ld_cg(rowp);
           cplx tu, sc;
           double beta;
           if (s2 == 0.0 && al.y == 0.0) {
@@ -312,9 +387,11 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
             beta = al.x;
             sc = mk(0, 0);
           } else {
+            // one division for tau, one for the scale
             const double an = sqrt(al.x * al.x + al.y * al.y + s2);
             beta = (al.x >= 0.0) ? -an : an;
-            tu = mk((beta - al.x) / beta, -al.y / beta);
+            const double ib = 1.0 / beta;
+            tu = mk((beta - al.x) * ib, -al.y * ib);
             sc = cinv(mk(al.x - beta, al.y));
           }
           bc[0] = tu;
@@ -322,56 +399,113 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
           bc[2] = mk(beta, 0.0);
         }
       }
+      // raw sums over the CTAs of the dot products (tpc threads per column)
+      if (nrem > 0) {
+        int tpc = 32;
+        while (tpc > 1 && tpc * nrem > (int)blockDim.x) tpc >>= 1;
+        const int per = blockDim.x / tpc, sub = tid % tpc;
+        for (int base = 0; base < nrem; base += per) {
+          const int c = base + tid / tpc;
+          const bool valid = c < nrem;
+          if constexpr (MIXED) {
+            df2 acc = df_zero();
+            if (valid)
+              for (int gg = sub; gg < G; gg += tpc)
+                acc = df_cadd(acc, ld_cg_df(ws.pc + (size_t)gg * pstride + tail0 + (size_t)par * nb + c));
+            for (int o = 1; o < tpc; o <<= 1) acc = df_cadd(acc, df_shfl_xor(acc, o));
+            if (valid && sub == 0) reinterpret_cast<df2*>(praw)[c] = acc;
+          } else {
+            cplx acc = mk(0, 0);
+            if (valid)
+              for (int gg = sub; gg < G; gg += tpc) acc = cadd(acc, ld_cg(ws.pc + (size_t)gg * pstride + tail0 + (size_t)par * nb + c));
+            for (int o = 1; o < tpc; o <<= 1) {
+              acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+              acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (valid && sub == 0) praw[c] = acc;
+          }
+        }
+      }
       __syncthreads();
       const cplx tu = bc[0], sc = bc[1];
-      for (int i = max(lo, jj + 1) + tid; i < r1; i += blockDim.x) pt[i - r0] = cmul(pt[i - r0], sc);
-      if (tid == 0) {
-        if (jj >= r0 && jj < r1) pt[jj - r0] = bc[2];
-        if (g == 0) tau[jj] = tu;
+      // f_c = conj(tau) (a_c[jj] + conj(scale) raw_c) into wl; scale column t
+      if constexpr (MIXED) {
+        df2* Pd = reinterpret_cast<df2*>(P);
+        const df2 ctu = df_from(cconj(tu)), csc = df_from(cconj(sc)), scd = df_from(sc);
+        for (int c = tid; c < nrem; c += blockDim.x) {
+          df2 w = ld_cg_df(rowp + 1 + c);
+          df_cmac(w, csc, reinterpret_cast<const df2*>(praw)[c]);
+          df2 f = df_zero();
+          df_cmac(f, ctu, w);
+          f = df_cadd(f, df_zero());
+          reinterpret_cast<df2*>(wl)[c] = df2{-f.rh, -f.ih, -f.rl, -f.il};  // -f
+        }
+        df2* xt = Pd + (size_t)t * R;
+        for (int i = ilo + tid; i < r1; i += blockDim.x) {
+          df2 v = df_zero();
+          df_cmac(v, xt[i - r0], scd);
+          xt[i - r0] = df_cadd(v, df_zero());
+        }
+        if (tid == 0 && jj >= r0 && jj < r1) xt[jj - r0] = df_from(bc[2]);
+      } else {
+        for (int c = tid; c < nrem; c += blockDim.x) {
+          const cplx w = cadd(ld_cg(rowp + 1 + c), cmul(cconj(sc), praw[c]));
+          const cplx f = cmul(cconj(tu), w);
+          wl[c] = mk(-f.x, -f.y);  // -f
+        }
+        cplx* xt = P + (size_t)t * R;
+        for (int i = ilo + tid; i < r1; i += blockDim.x) xt[i - r0] = cmul(xt[i - r0], sc);
+        if (tid == 0 && jj >= r0 && jj < r1) xt[jj - r0] = bc[2];
+      }
+      if (tid == 0 && g == 0) tau[jj] = tu;
+      __syncthreads();
+      // apply H^H = I - conj(tau) v v^H to panel columns t+1..nbk-1 of own
+      // rows >= jj (v_jj = 1)
+      if (nrem > 0) {
+        const int ifrom = max(lo, jj);
+        const int nrow = r1 - ifrom;
+        if constexpr (MIXED) {
+          df2* Pd = reinterpret_cast<df2*>(P);
+          const df2* xt = Pd + (size_t)t * R;
+          const df2* nf = reinterpret_cast<const df2*>(wl);
+          for (int e = tid; e < nrow * nrem; e += blockDim.x) {
+            const int c = e / nrow, i = ifrom + e % nrow;
+            const df2 v = (i == jj) ? df2{1.f, 0.f, 0.f, 0.f} : xt[i - r0];
+            df2& a = Pd[(size_t)(t + 1 + c) * R + (i - r0)];
+            df2 dlt = df_zero();
+            df_cmac(dlt, v, nf[c]);
+            a = df_cadd(a, dlt);
+          }
+        } else {
+          const cplx* xt = P + (size_t)t * R;
+          for (int e = tid; e < nrow * nrem; e += blockDim.x) {
+            const int c = e / nrow, i = ifrom + e % nrow;
+            const cplx v = (i == jj) ? mk(1, 0) : xt[i - r0];
+            cplx& a = P[(size_t)(t + 1 + c) * R + (i - r0)];
+            a = cfma(v, wl[c], a);
+          }
+        }
       }
       __syncthreads();
-      // (3) apply H^H = I - conj(tau) v v^H to panel columns t+1..nbk-1
-      const int nrem = nbk - t - 1;
-      if (nrem > 0) {
-        // v_jj = 1 is implicit: the stored diagonal holds beta.
-        for (int l = wid; l < nrem; l += nw) {
-          const cplx* pl = P + (size_t)(t + 1 + l) * R;
-          cplx acc = mk(0, 0);
-          for (int i = max(lo, jj) + lane; i < r1; i += 32) {
-            const cplx vi = (i == jj) ? mk(1, 0) : pt[i - r0];
-            acc = cfmac(vi, pl[i - r0], acc);
-          }
-          acc = warp_sum(acc);
-          if (lane == 0) ws.pc[(size_t)g * pstride + l] = acc;
-        }
-        grid_sync(gs);
-        if (grid_failed(ws.bar)) return;
-        for (int l = wid; l < nrem; l += nw) {
-          cplx sum = reduce_partials(ws.pc, pstride, G, l);
-          if (lane == 0) wl[l] = cmul(cconj(tu), sum);
-        }
-        __syncthreads();
-        for (int l = 0; l < nrem; ++l) {
-          cplx* pl = P + (size_t)(t + 1 + l) * R;
-          const cplx f = wl[l];
-          for (int i = max(lo, jj) + tid; i < r1; i += blockDim.x) {
-            const cplx vi = (i == jj) ? mk(1, 0) : pt[i - r0];
-            pl[i - r0] = csub(pl[i - r0], cmul(vi, f));
-          }
-        }
-        __syncthreads();
-      }
     }
-    // write the factored panel back (R on/above the diagonal, V below)
+    // write the factored panel back in FP64 (R on/above the diagonal, V below)
     for (int t = 0; t < nbk; ++t)
-      for (int i = r0 + tid; i < r1; i += blockDim.x) A[i + (size_t)lda * (j0 + t)] = P[(size_t)t * R + (i - r0)];
+      for (int i = r0 + tid; i < r1; i += blockDim.x) {
+        const size_t e = (size_t)t * R + (i - r0);
+        A[i + (size_t)lda * (j0 + t)] = MIXED ? df_to(reinterpret_cast<const df2*>(P)[e]) : P[e];
+      }
     __syncthreads();
     // fix up P to hold pure reflectors: zero above, one on the diagonal
     for (int t = 0; t < nbk; ++t)
       for (int i = r0 + tid; i < r1; i += blockDim.x) {
-        const int gi = i;
-        if (gi < j0 + t) P[(size_t)t * R + (i - r0)] = mk(0, 0);
-        else if (gi == j0 + t) P[(size_t)t * R + (i - r0)] = mk(1, 0);
+        const size_t e = (size_t)t * R + (i - r0);
+        if (i < j0 + t) {
+          if (MIXED) reinterpret_cast<df2*>(P)[e] = df_zero();
+          else P[e] = mk(0, 0);
+        } else if (i == j0 + t) {
+          if (MIXED) reinterpret_cast<df2*>(P)[e] = df2{1.f, 0.f, 0.f, 0.f};
+          else P[e] = mk(1, 0);
+        }
       }
     __syncthreads();
 
@@ -381,9 +515,8 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     const int ncol = nbk + nt;
     if (MIXED) {
       cplx* out = ws.pc + (size_t)g * pstride;
-      // the panel in double-float form; the Gram block (its columns are the
-      // reflectors themselves) and the trailing products on the FP32 pipe
-      to_df_in_place(P, nbk * R);
+      // the Gram block (its columns are the reflectors themselves) and the
+      // trailing products from the double-float panel, on the FP32 pipe
       const df2* Pd = reinterpret_cast<const df2*>(P);
       partial_vhx_f<NB>(Pd, R, r0, lo, r1, nbk, Pd - r0, R, nbk, out);
       if (nt > 0)
@@ -568,7 +701,8 @@ cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_ou
   int G, R, nb;
   size_t smem;
   pick_layout(m, &G, &R, &nb, &smem);
-  if ((size_t)G * nb * (size_t)(nb + k) > ws.pc_elems || (size_t)nb * (nb + k) > ws.wfin_elems)
+  // per CTA: S1 partials nb (nb + k), then the panel's exchange tail 4 nb
+  if ((size_t)G * ((size_t)nb * (nb + k) + 4 * (size_t)nb) > ws.pc_elems || (size_t)nb * (nb + k) > ws.wfin_elems)
     return cudaErrorInvalidValue;
   *nb_out = nb;
   void* fn;
