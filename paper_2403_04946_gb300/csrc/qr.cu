@@ -233,24 +233,63 @@ __device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
 }
 
 // Rows [r0, r1) of columns [c0, c1) of the column-major A (lda) between
-// FP64 and double-float form, in place (one CTA's rows).
-__device__ void rows_to_df(cplx* A, int lda, int r0, int r1, int c0, int c1) {
+// FP64 and double-float form, in place (one CTA's rows), with a power-of-two
+// scale: df = A * 2^-E on the way in, A = df * 2^E on the way out.  The
+// scale keeps every entry below 1 in magnitude, so the FP32 exponent range
+// of the double-float parts (and of their products) is never exceeded.
+__device__ void rows_to_df(cplx* A, int lda, int r0, int r1, int c0, int c1, int E) {
   const int nr = r1 - r0;
   if (nr <= 0) return;
   for (long long e = threadIdx.x; e < (long long)nr * (c1 - c0); e += blockDim.x) {
     const int c = c0 + (int)(e / nr), i = r0 + (int)(e % nr);
     cplx* p = A + i + (size_t)lda * c;
-    *reinterpret_cast<df2*>(p) = df_from(*p);
+    const cplx v = *p;
+    *reinterpret_cast<df2*>(p) = df_from(mk(scalbn(v.x, -E), scalbn(v.y, -E)));
   }
 }
-__device__ void rows_to_fp64(cplx* A, int lda, int r0, int r1, int c0, int c1) {
+__device__ void rows_to_fp64(cplx* A, int lda, int r0, int r1, int c0, int c1, int E) {
   const int nr = r1 - r0;
   if (nr <= 0) return;
   for (long long e = threadIdx.x; e < (long long)nr * (c1 - c0); e += blockDim.x) {
     const int c = c0 + (int)(e / nr), i = r0 + (int)(e % nr);
     cplx* p = A + i + (size_t)lda * c;
-    *p = df_to(*reinterpret_cast<const df2*>(p));
+    const cplx v = df_to(*reinterpret_cast<const df2*>(p));
+    *p = mk(scalbn(v.x, E), scalbn(v.y, E));
   }
+}
+
+// Power-of-two exponent E with max |entry| * 2^-E < 1 over rows [r0, r1) of
+// columns [0, k) of every CTA: one grid barrier; the per-CTA maxima go to
+// slot[0..G).  Returns E (0 for an all-zero matrix).
+__device__ int grid_scale_exponent(const cplx* A, int lda, int r0, int r1, int k, double* slot,
+                                   double* red, GridSync& gs, const GridBar* bar) {
+  const int nr = r1 - r0;
+  double mx = 0.0;
+  if (nr > 0)
+    for (long long e = threadIdx.x; e < (long long)nr * k; e += blockDim.x) {
+      const cplx v = A[r0 + (int)(e % nr) + (size_t)lda * (int)(e / nr)];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  for (int o = 16; o >= 1; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, red[w]);
+    slot[blockIdx.x] = b;
+  }
+  grid_sync(gs);
+  if (grid_failed(bar)) return 0;
+  double g = 0.0;
+  for (int c = 0; c < (int)gridDim.x; ++c) g = fmax(g, __ldcg(slot + c));
+  return (g > 0.0) ? ilogb(g) + 1 : 0;
+}
+
+// a * 2^e for a double-float value (exact unless the result leaves the
+// FP32 range).
+DV df2 df_scalb(const df2& a, int e) {
+  return df2{scalbnf(a.rh, e), scalbnf(a.ih, e), scalbnf(a.rl, e), scalbnf(a.il, e)};
 }
 
 // Rewrites each of the first n FP64 complex values of buf as a double-float
@@ -291,10 +330,15 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
   const int p = min(m, k);
   const size_t pstride = ws.pc_elems / G;
   GridSync gs{ws.bar, 0u};
-  // Mixed precision: this CTA's rows of A in double-float form until each
-  // column is factored (panel columns are written back in FP64).
+  // Mixed precision: this CTA's rows of A in double-float form, scaled by
+  // 2^-E, until each column is factored (panel columns are written back in
+  // FP64, the R part rescaled by 2^E; reflectors are scale-free).
+  int E = 0;
+  __shared__ int esc_sh;
   if (MIXED) {
-    rows_to_df(A, lda, r0, r1, 0, k);
+    E = grid_scale_exponent(A, lda, r0, r1, k, ws.pr + 2 * G, dred, gs, ws.bar);
+    if (grid_failed(ws.bar)) return;
+    rows_to_df(A, lda, r0, r1, 0, k, E);
     __syncthreads();
   }
 
@@ -335,14 +379,12 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
       if constexpr (MIXED) {
         const df2* Pd = reinterpret_cast<const df2*>(P);
         const df2* xt = Pd + (size_t)t * R;
-        float h = 0.f, l = 0.f;
-        for (int i = ilo + tid; i < r1; i += blockDim.x) {
-          const df2 x = xt[i - r0];
-          df_mac(h, l, x.rh, x.rl, x.rh, x.rl);
-          df_mac(h, l, x.ih, x.il, x.ih, x.il);
-        }
-        df_block_sum(h, l, fred);
-        if (tid == 0) prp[g] = (double)h + (double)l;
+        // the squared norm in FP64: squares of small entries would leave
+        // the FP32 range
+        double sq = 0.0;
+        for (int i = ilo + tid; i < r1; i += blockDim.x) sq += cabs2(df_to(xt[i - r0]));
+        sq = block_sum(sq, dred);
+        if (tid == 0) prp[g] = sq;
         for (int c = wid; c < nrem; c += nw) {
           const df2* pl = Pd + (size_t)(t + 1 + c) * R;
           df2 acc = df_zero();
@@ -394,6 +436,14 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
             tu = mk((beta - al.x) * ib, -al.y * ib);
             sc = cinv(mk(al.x - beta, al.y));
           }
+          if (MIXED) {
+            // the scale can leave the FP32 range (tiny columns): keep it as
+            // mantissa x 2^esc
+            const double smax = fmax(fabs(sc.x), fabs(sc.y));
+            const int es = (smax > 0.0) ? ilogb(smax) : 0;
+            sc = mk(scalbn(sc.x, -es), scalbn(sc.y, -es));
+            esc_sh = es;
+          }
           bc[0] = tu;
           bc[1] = sc;
           bc[2] = mk(beta, 0.0);
@@ -432,9 +482,11 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
       if constexpr (MIXED) {
         df2* Pd = reinterpret_cast<df2*>(P);
         const df2 ctu = df_from(cconj(tu)), csc = df_from(cconj(sc)), scd = df_from(sc);
+        const int es = esc_sh;
         for (int c = tid; c < nrem; c += blockDim.x) {
-          df2 w = ld_cg_df(rowp + 1 + c);
-          df_cmac(w, csc, reinterpret_cast<const df2*>(praw)[c]);
+          df2 cr = df_zero();
+          df_cmac(cr, csc, reinterpret_cast<const df2*>(praw)[c]);
+          const df2 w = df_cadd(ld_cg_df(rowp + 1 + c), df_scalb(cr, es));
           df2 f = df_zero();
           df_cmac(f, ctu, w);
           f = df_cadd(f, df_zero());
@@ -444,7 +496,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         for (int i = ilo + tid; i < r1; i += blockDim.x) {
           df2 v = df_zero();
           df_cmac(v, xt[i - r0], scd);
-          xt[i - r0] = df_cadd(v, df_zero());
+          xt[i - r0] = df_scalb(df_cadd(v, df_zero()), es);
         }
         if (tid == 0 && jj >= r0 && jj < r1) xt[jj - r0] = df_from(bc[2]);
       } else {
@@ -492,7 +544,13 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     for (int t = 0; t < nbk; ++t)
       for (int i = r0 + tid; i < r1; i += blockDim.x) {
         const size_t e = (size_t)t * R + (i - r0);
-        A[i + (size_t)lda * (j0 + t)] = MIXED ? df_to(reinterpret_cast<const df2*>(P)[e]) : P[e];
+        if (MIXED) {
+          const cplx v = df_to(reinterpret_cast<const df2*>(P)[e]);
+          const int sh = (i <= j0 + t) ? E : 0;  // R part scaled back, reflector tails scale-free
+          A[i + (size_t)lda * (j0 + t)] = mk(scalbn(v.x, sh), scalbn(v.y, sh));
+        } else {
+          A[i + (size_t)lda * (j0 + t)] = P[e];
+        }
       }
     __syncthreads();
     // fix up P to hold pure reflectors: zero above, one on the diagonal
@@ -606,7 +664,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     __syncthreads();
   }
   // columns never factored (k > m) go back to FP64
-  if (MIXED && k > p) rows_to_fp64(A, lda, r0, r1, p, k);
+  if (MIXED && k > p) rows_to_fp64(A, lda, r0, r1, p, k, E);
 }
 
 template <int NB, bool MIXED>
@@ -622,9 +680,14 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
   const size_t pstride = ws.pc_elems / G;
   const int npanel = (p + nb - 1) / nb;
   GridSync gs{ws.bar, 0u};
-  // Mixed precision: this CTA's rows of C in double-float form throughout
+  // Mixed precision: this CTA's rows of C in double-float form (scaled by
+  // 2^-E) throughout
+  __shared__ double dred[32];
+  int E = 0;
   if (MIXED) {
-    rows_to_df(C, ldc, r0, r1, 0, q);
+    E = grid_scale_exponent(C, ldc, r0, r1, q, ws.pr, dred, gs, ws.bar);
+    if (grid_failed(ws.bar)) return;
+    rows_to_df(C, ldc, r0, r1, 0, q, E);
     __syncthreads();
   }
   for (int panel = npanel - 1; panel >= 0; --panel) {
@@ -679,7 +742,7 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
     // No barrier needed here: the next panel writes wfin only after its
     // first grid_sync, which every CTA reaches after finishing this update.
   }
-  if (MIXED) rows_to_fp64(C, ldc, r0, r1, 0, q);
+  if (MIXED) rows_to_fp64(C, ldc, r0, r1, 0, q, E);
 }
 
 static void pick_layout(int m, int* G, int* R, int* nb, size_t* smem) {
