@@ -35,11 +35,12 @@ struct CoopWs {
 };
 
 // Householder QR of the column-major m x k matrix A (lda >= m), in place:
-// R on and above the diagonal, reflector tails below, tau[min(m,k)], and the
-// compact-WY T factor of every panel of width `nb` in T (npanel x nb x nb).
-// Returns the panel width used through *nb_out.
-// mixed != 0: panels (reflectors, T factors) in FP64, trailing products in
-// FP32 added to the FP64 matrix as corrections.
+// R on and above the diagonal, reflector tails below, tau[min(m,k)], and for
+// every panel of width `nb` its reflectors' Gram matrix v_u^H v_s (strict
+// upper triangle) with tau on the diagonal, in T (npanel x nb x nb); ormqr
+// applies the panel from these.  Returns the panel width used through
+// *nb_out.  mixed != 0: the matrix is held in double-float form (scaled by a
+// power of two) during the factorisation, the Householder scalars in FP64.
 cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_out,
                   const CoopWs& ws, cudaStream_t s, int mixed = 0);
 // C <- Q C with Q = H_0 H_1 ... H_{p-1} from geqrf (A, lda, m, p, tau, T, nb);

@@ -611,44 +611,33 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
     }
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
-    // S3: T from the reflector Gram (zlarft, forward, columnwise), then
-    // W2 = T^H W for the trailing columns this CTA reduced.
-    // The build below is a serial recurrence over the panel's columns; each
-    // Gram column is loaded once per lane and broadcast by shuffles, so no L2
-    // latency sits inside the recurrence.
-    for (int e = tid; e < nbk * nbk; e += blockDim.x) Ts[e] = mk(0, 0);
-    __syncthreads();
-    if (wid == 0) {
-      for (int i = 0; i < nbk; ++i) {
-        const cplx ti = ld_cg(tau + j0 + i);
-        // Gram column i held by lanes: g_l = v_l^H v_i for l = lane
-        const cplx gcol = (lane < i) ? ld_cg(ws.wfin + lane + (size_t)nbk * i) : mk(0, 0);
-        // T[0:i, i] = -tau_i * T[0:i, 0:i] * Gram[0:i, i]
-        cplx y = mk(0, 0);
-        for (int l = 0; l < i; ++l) {
-          const cplx gl = make_double2(__shfl_sync(0xffffffffu, gcol.x, l), __shfl_sync(0xffffffffu, gcol.y, l));
-          if (lane <= l) y = cfma(Ts[lane + nbk * l], gl, y);
-        }
-        __syncwarp();
-        if (lane < i) Ts[lane + nbk * i] = cmul(mk(-ti.x, -ti.y), y);
-        if (lane == 0) Ts[i + nbk * i] = ti;
-        __syncwarp();
-      }
+    // S3: W2 = T^H W for the trailing columns this CTA reduced, without
+    // forming T: applying H_0^H, H_1^H, ... in turn gives, with
+    // Gram[s,u] = v_s^H v_u,
+    //   w2_s = conj(tau_s) (W[s] - sum_{u<s} Gram[s,u] w2_u),
+    // a chain of nbk steps per column (lanes = s; one warp per column).  The
+    // panel's Gram (strict upper triangle) and tau (diagonal) are kept in
+    // Tg for ormqr, which runs the mirrored recurrence.
+    for (int e = tid; e < nbk * nbk; e += blockDim.x) {
+      const int u = e % nbk, c = e / nbk;
+      Ts[e] = (u < c) ? ld_cg(ws.wfin + e) : (u == c ? ld_cg(tau + j0 + c) : mk(0, 0));
     }
     __syncthreads();
     if (g == 0)
       for (int e = tid; e < nbk * nbk; e += blockDim.x) Tg[(size_t)panel * nb * nb + e] = Ts[e];
-    for (int l = nbk + g; l < ncol; l += G) {
-      // W2[s] = sum_{u <= s} conj(T[u, s]) W[u]
-      if (wid == 0) {
-        cplx wv = mk(0, 0);
-        if (lane < nbk) wv = ld_cg(ws.wfin + lane + (size_t)nbk * l);
-        cplx acc = mk(0, 0);
+    {
+      const cplx ctl = (lane < nbk) ? cconj(Ts[lane + nbk * lane]) : mk(0, 0);  // conj(tau_lane)
+      for (int l = nbk + g + wid * G; l < ncol; l += nw * G) {
+        cplx acc = (lane < nbk) ? ld_cg(ws.wfin + lane + (size_t)nbk * l) : mk(0, 0);
+        cplx mine = mk(0, 0);
         for (int u = 0; u < nbk; ++u) {
-          const cplx wu = make_double2(__shfl_sync(0xffffffffu, wv.x, u), __shfl_sync(0xffffffffu, wv.y, u));
-          if (lane < nbk && u <= lane) acc = cfmac(Ts[u + nbk * lane], wu, acc);
+          const cplx wu = cmul(ctl, acc);  // valid on lane u
+          const cplx w2u = make_double2(__shfl_sync(0xffffffffu, wu.x, u), __shfl_sync(0xffffffffu, wu.y, u));
+          if (lane == u) mine = w2u;
+          // Gram[lane, u] = conj(v_u^H v_lane) for u < lane
+          if (lane > u && lane < nbk) acc = csub(acc, cmulc(Ts[u + nbk * lane], w2u));
         }
-        if (lane < nbk) ws.wfin[lane + (size_t)nbk * l] = acc;
+        if (lane < nbk) ws.wfin[lane + (size_t)nbk * l] = mine;
       }
     }
     grid_sync(gs);
@@ -703,7 +692,8 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
         if (MIXED) reinterpret_cast<df2*>(P)[(size_t)t * R + (i - r0)] = df_from(v);
         else P[(size_t)t * R + (i - r0)] = v;
       }
-    // T of a panel is stored packed (leading dimension nbk).
+    // the panel's Gram (strict upper triangle) and tau (diagonal), packed
+    // with leading dimension nbk
     for (int e = tid; e < nbk * nbk; e += blockDim.x) Ts[e] = Tg[(size_t)panel * nb * nb + e];
     __syncthreads();
     if (MIXED)
@@ -713,24 +703,30 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
       partial_vhx<NB>(P, R, r0, lo, r1, nbk, C, ldc, q, ws.pc + (size_t)g * pstride);
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
-    // reduce and multiply by T: W2 = T W (apply Q, not Q^H)
+    // reduce, then W2 = T W (apply Q, not Q^H) from the stored Gram and tau:
+    // applying H_{nbk-1}, ..., H_0 in turn gives
+    //   w2_s = tau_s (W[s] - sum_{u>s} Gram[s,u] w2_u),  Gram[s,u] = v_s^H v_u
     for (int l = g; l < q; l += G) {
       for (int s = wid; s < nbk; s += nw) {
         cplx v = reduce_partials(ws.pc, pstride, G, s + (size_t)nbk * l);
         if (lane == 0) ws.wfin[s + (size_t)nbk * l] = v;
       }
-      __syncthreads();
-      if (wid == 0) {
-        // W2[s] = sum_{u >= s} T[s, u] W[u]; W held by lanes, broadcast by shuffles
-        const cplx wv = (lane < nbk) ? ws.wfin[lane + (size_t)nbk * l] : mk(0, 0);
-        cplx acc = mk(0, 0);
-        for (int u = 0; u < nbk; ++u) {
-          const cplx wu = make_double2(__shfl_sync(0xffffffffu, wv.x, u), __shfl_sync(0xffffffffu, wv.y, u));
-          if (lane < nbk && u >= lane) acc = cfma(Ts[lane + nbk * u], wu, acc);
+    }
+    __syncthreads();
+    {
+      const cplx tl = (lane < nbk) ? Ts[lane + nbk * lane] : mk(0, 0);  // tau_lane
+      for (int l = g + wid * G; l < q; l += nw * G) {
+        cplx acc = (lane < nbk) ? ws.wfin[lane + (size_t)nbk * l] : mk(0, 0);
+        cplx mine = mk(0, 0);
+        for (int u = nbk - 1; u >= 0; --u) {
+          const cplx wu = cmul(tl, acc);  // valid on lane u
+          const cplx w2u = make_double2(__shfl_sync(0xffffffffu, wu.x, u), __shfl_sync(0xffffffffu, wu.y, u));
+          if (lane == u) mine = w2u;
+          // Gram[lane, u] = v_lane^H v_u, stored for lane < u
+          if (lane < u) acc = csub(acc, cmul(Ts[lane + nbk * u], w2u));
         }
-        if (lane < nbk) ws.wfin[lane + (size_t)nbk * l] = acc;
+        if (lane < nbk) ws.wfin[lane + (size_t)nbk * l] = mine;
       }
-      __syncthreads();
     }
     grid_sync(gs);
     if (grid_failed(ws.bar)) return;
