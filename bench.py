@@ -6,7 +6,7 @@ roundings (right-to-left Householder orthogonalisation + left-to-right
 truncated SVD) and 4 TT sums, on the d=32, n=128, rank<=64 workload, in the
 "saturated" state (every interior rank at the cap 64: a seeded TT with random
 orthonormal cores), complex values in FP64 storage.  ``value`` is the mixed-
-precision solver (FP64 panels and SVD, double-float updates); the FP64 solver
+precision solver (FP64 Householder scalars and SVD, double-float QR arithmetic); the FP64 solver
 is timed on the same state under the ``fp64`` key, and the mixed-vs-FP64
 error is measured on a physical state.
 
@@ -209,7 +209,7 @@ def roofline(prof, mixed, peaks):
     if mixed:
         peak = FP32_PEAK_TFLOPS / DF_OPS_PER_FLOP
         src = ("double-float on the FP32 pipe: 152 SMs x 256 FLOP/clk x 2.07 GHz / 6.5 FP32 ops per "
-               "FP64-equivalent FLOP (derived); FP64 panels inside the same kernel")
+               "FP64-equivalent FLOP (derived); Householder scalars in FP64 inside the same kernel")
     else:
         peak = FP64_PEAK_TFLOPS
         src = "FP64 FMA: 152 SMs x 4 FLOP/clk x 2.07 GHz (derived; DFMA microbenchmark measured 1.19)"
@@ -283,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
     except Exception:
         pass
 
-    # primary arm: mixed precision (FP64 panels and SVD, double-float updates)
+    # primary arm: mixed precision (FP64 Householder scalars and SVD, double-float QR arithmetic)
     ctx = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L,
                           stream=stream.cuda_stream, precision=binding.HOPF_MIXED)
     t = ctx.tt_from_host(cores, max_rank=w.cap)
@@ -346,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 storage; f64 Householder panels and Jacobi SVD; double-float (2 x f32) updates",
+            "dtype": "f64 storage; QR/apply-Q/merges in double-float (2 x f32) arithmetic; f64 Householder scalars and SVD",
             "data": "synthetic", "config": config_dict(w),
             "roofline": roofline(prof, True, peaks),
             "kernel_shares": shares,
@@ -354,7 +354,7 @@ def run_ours(args, rank, world, local_rank):
                      "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},
             "mixed_vs_fp64_error": err,
             "apply_gbs": apply_gbs,
-            "svd_sweeps_per_svd": prof["svd"].get("sweeps", 0) / max(1, prof["svd"].get("count", 0)),
+            "jacobi_sweeps_per_svd": prof["svd"].get("sweeps", 0) / max(1, prof["svd"].get("count", 0)),
             "cpu_baseline": cpu,
             "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s",
                     "h2d_bytes_per_step": int(nd * 8), "d2h_bytes_per_step": int(out_bytes)},
