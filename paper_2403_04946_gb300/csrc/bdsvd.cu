@@ -42,10 +42,15 @@ DV void house_scalars(cplx alpha, double xnorm2, cplx* tau, cplx* scale, double*
     *beta = alpha.x;
     return;
   }
+  // two FP64 divisions (each ~640 cycles of latency on this GPU), issued
+  // independently of each other
   const double an = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
   const double b = (alpha.x >= 0.0) ? -an : an;
-  *tau = mk((b - alpha.x) / b, -alpha.y / b);
-  *scale = cinv(mk(alpha.x - b, alpha.y));
+  const double ib = 1.0 / b;
+  const double dr = alpha.x - b, di = alpha.y;
+  const double id2 = 1.0 / (dr * dr + di * di);
+  *tau = mk((b - alpha.x) * ib, -alpha.y * ib);
+  *scale = mk(dr * id2, -di * id2);
   *beta = b;
 }
 

@@ -215,17 +215,31 @@ __device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
     }
     __syncwarp();
     if (l < ncol) {
+      // four rows per lane at a time: four independent accumulation chains
+      // (a double-float multiply-add is a chain of ~16 dependent FP32
+      // operations, and only 8 warps share the SM)
       df2* x = X + (size_t)ldx * l;
-      df2 xn = (lo + lane < hi) ? x[lo + lane] : df_zero();
-      for (int i = lo + lane; i < hi; i += 32) {
-        const df2 xi = xn;
-        if (i + 32 < hi) xn = x[i + 32];
-        const df2* pv = P + (i - r0);
-        df2 dlt = df_zero();
-#pragma unroll 8
-        for (int s = 0; s < NB; ++s)
-          if (s < nbk) df_cmac(dlt, pv[(size_t)s * R], wsh[w][s]);
-        x[i] = df_cadd(xi, dlt);
+      for (int i0 = lo + lane; i0 < hi; i0 += 128) {
+        df2 xi[4], dlt[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = i0 + 32 * q;
+          xi[q] = (i < hi) ? x[i] : df_zero();
+          dlt[q] = df_zero();
+        }
+        const df2* pv = P + (i0 - r0);
+#pragma unroll 4
+        for (int s = 0; s < NB; ++s) {
+          if (s < nbk) {
+            const df2 ws = wsh[w][s];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (i0 + 32 * q < hi) df_cmac(dlt[q], pv[(size_t)s * R + 32 * q], ws);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (i0 + 32 * q < hi) x[i0 + 32 * q] = df_cadd(xi[q], dlt[q]);
       }
     }
     __syncwarp();
@@ -385,12 +399,22 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         for (int i = ilo + tid; i < r1; i += blockDim.x) sq += cabs2(df_to(xt[i - r0]));
         sq = block_sum(sq, dred);
         if (tid == 0) prp[g] = sq;
-        for (int c = wid; c < nrem; c += nw) {
-          const df2* pl = Pd + (size_t)(t + 1 + c) * R;
-          df2 acc = df_zero();
-          for (int i = ilo + lane; i < r1; i += 32) df_cmac_conj(acc, xt[i - r0], pl[i - r0]);
-          for (int o = 16; o >= 1; o >>= 1) acc = df_cadd(acc, df_shfl_xor(acc, o));
-          if (lane == 0) reinterpret_cast<df2*>(myp)[c] = acc;
+        // up to four columns per warp, interleaved (independent chains)
+        for (int cb = wid; cb < nrem; cb += 4 * nw) {
+          df2 acc[4] = {df_zero(), df_zero(), df_zero(), df_zero()};
+          for (int i = ilo + lane; i < r1; i += 32) {
+            const df2 x = xt[i - r0];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (cb + q * nw < nrem) df_cmac_conj(acc[q], x, Pd[(size_t)(t + 1 + cb + q * nw) * R + (i - r0)]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (cb + q * nw < nrem) {
+              for (int o = 16; o >= 1; o >>= 1) acc[q] = df_cadd(acc[q], df_shfl_xor(acc[q], o));
+              if (lane == 0) reinterpret_cast<df2*>(myp)[cb + q * nw] = acc[q];
+            }
+          }
         }
         if (g == gown)
           for (int c = tid; c < nbk - t; c += blockDim.x)
@@ -401,12 +425,21 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         for (int i = ilo + tid; i < r1; i += blockDim.x) sq += cabs2(xt[i - r0]);
         sq = block_sum(sq, dred);
         if (tid == 0) prp[g] = sq;
-        for (int c = wid; c < nrem; c += nw) {
-          const cplx* pl = P + (size_t)(t + 1 + c) * R;
-          cplx acc = mk(0, 0);
-          for (int i = ilo + lane; i < r1; i += 32) acc = cfmac(xt[i - r0], pl[i - r0], acc);
-          acc = warp_sum(acc);
-          if (lane == 0) myp[c] = acc;
+        for (int cb = wid; cb < nrem; cb += 4 * nw) {
+          cplx acc[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
+          for (int i = ilo + lane; i < r1; i += 32) {
+            const cplx x = xt[i - r0];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (cb + q * nw < nrem) acc[q] = cfmac(x, P[(size_t)(t + 1 + cb + q * nw) * R + (i - r0)], acc[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (cb + q * nw < nrem) {
+              acc[q] = warp_sum(acc[q]);
+              if (lane == 0) myp[cb + q * nw] = acc[q];
+            }
+          }
         }
         if (g == gown)
           for (int c = tid; c < nbk - t; c += blockDim.x) rowp[c] = P[(size_t)(t + c) * R + (jj - r0)];
