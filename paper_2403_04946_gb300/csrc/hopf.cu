@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <set>
 #include <vector>
 
 #include "../../include/hopf.h"
@@ -728,6 +729,175 @@ std::vector<double> gauss_legendre01(int q) {
   return out;
 }
 
+// ---- TT-cross construction of a correlated Gaussian initial state ------------
+// Index sets are tuples of grid indices (row-major, one tuple per rank
+// index).  A left-to-right sweep over the modes in `order` builds, at each
+// bond, the next left set from the pivots of the fiber matrix and, when
+// `cores` is set, the interpolating core.  The right-to-left sweeps are
+// left-to-right sweeps of the mode-reversed problem.
+struct CrossBufs {
+  cplx* A = nullptr;     // fiber matrix, cap n x cap
+  cplx* W = nullptr;     // pivoting copy
+  cplx* Gw = nullptr;    // cap x cap
+  cplx* Gi = nullptr;    // cap x cap
+  int* il = nullptr;     // cap x d
+  int* jr = nullptr;     // cap x d
+  int* piv = nullptr;    // rows[cap], cols[cap], count
+  double* mc = nullptr;  // m (d), C (d x d)
+  void release() {
+    cudaFree(A); cudaFree(W); cudaFree(Gw); cudaFree(Gi); cudaFree(il); cudaFree(jr); cudaFree(piv); cudaFree(mc);
+  }
+};
+
+hopf_status cross_sweep(hopf_ctx* ctx, CrossBufs& B, int cap, const std::vector<double>& m,
+                        const std::vector<double>& C, const std::vector<std::vector<int>>& R,
+                        std::vector<std::vector<int>>& L, hopf_tt* cores) {
+  const int d = ctx->p.d, n = ctx->p.n;
+  CK(cudaMemcpyAsync(B.mc, m.data(), d * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(B.mc + d, C.data(), (size_t)d * d * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  L.assign(d + 1, {});
+  std::vector<int> ranks(d + 1, 1);
+  std::vector<int> hp(2 * cap + 1);
+  for (int k = 0; k < d; ++k) {
+    const int rl = (k == 0) ? 1 : (int)(L[k].size() / k);
+    const int kr = d - k - 1;
+    const int rr = (k == d - 1) ? 1 : (int)(R[k + 1].size() / kr);
+    if (k > 0) CK(cudaMemcpyAsync(B.il, L[k].data(), L[k].size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    if (kr > 0) CK(cudaMemcpyAsync(B.jr, R[k + 1].data(), R[k + 1].size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    const int M = rl * n;
+    if (rl < 1 || rl > cap || rr < 1 || rr > cap)
+      return fail(ctx, HOPF_EINVAL, "cross: index set of size %d x %d at mode %d outside [1, %d]", rl, rr, k, cap);
+    if (k == d - 1) {
+      if (cores) CK(hk::gauss_fibers(ctx->d_agrid, n, d, B.mc, B.mc + d, B.il, rl, k, B.jr, 1, cores->cores[k], ctx->stream));
+      ranks[k] = rl;
+      break;
+    }
+    CK(hk::gauss_fibers(ctx->d_agrid, n, d, B.mc, B.mc + d, B.il, rl, k, B.jr, rr, B.A, ctx->stream));
+    CK(hk::cross_pivots(B.A, M, rr, 1e-14, B.W, B.piv, B.piv + cap, B.piv + 2 * cap, ctx->coop, ctx->stream));
+    CK(cudaMemcpyAsync(hp.data(), B.piv, (2 * cap + 1) * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    TRY(check_barrier(ctx));
+    const int cnt = hp[2 * cap];
+    if (cnt < 1) return fail(ctx, HOPF_ENUMERIC, "cross: no pivot at bond %d", k + 1);
+    if (cores) {
+      if ((size_t)M * cnt > cores->core_cap[k]) return fail(ctx, HOPF_EINVAL, "cross: core %d exceeds capacity", k);
+      CK(hk::cross_core(B.A, M, B.piv, B.piv + cap, cnt, B.Gw, B.Gi, cores->cores[k], ctx->stream));
+    }
+    ranks[k] = rl;
+    // next left set: (L[k][alpha], i) for each pivot row alpha + rl i
+    std::vector<int> nl((size_t)cnt * (k + 1));
+    for (int b = 0; b < cnt; ++b) {
+      const int row = hp[b], alpha = row % rl, i = row / rl;
+      for (int t = 0; t < k; ++t) nl[(size_t)b * (k + 1) + t] = L[k][(size_t)alpha * k + t];
+      nl[(size_t)b * (k + 1) + k] = i;
+    }
+    L[k + 1] = std::move(nl);
+  }
+  if (cores) {
+    std::vector<int> r(d + 1, 1);
+    for (int k = 1; k < d; ++k) r[k] = (int)(L[k].size() / k);
+    cores->ranks = r;
+    TRY(sync_meta(ctx, cores));
+  }
+  return HOPF_OK;
+}
+
+// reverses the mode order of tuple sets: set over modes k..d-1 of the
+// forward problem <-> set over modes 0..d-k-1 of the reversed problem
+std::vector<std::vector<int>> cross_mirror(const std::vector<std::vector<int>>& S, int d, bool from_left) {
+  std::vector<std::vector<int>> out(d + 1);
+  for (int k = 1; k < d; ++k) {
+    const int len = from_left ? k : d - k;  // tuple length in S at bond k
+    const std::vector<int>& src = S[k];
+    if (src.empty() || len == 0) continue;
+    const int cnt = (int)(src.size() / len);
+    std::vector<int> t((size_t)cnt * len);
+    for (int b = 0; b < cnt; ++b)
+      for (int q = 0; q < len; ++q) t[(size_t)b * len + q] = src[(size_t)b * len + (len - 1 - q)];
+    out[d - k] = std::move(t);
+  }
+  return out;
+}
+
+// Pads every set S[k] (tuples of length d-k) with distinct pseudo-random
+// tuples up to min(cap, (n-1)^(d-k)), so that the ranks found by the next
+// sweep can grow up to the cap (pivoting alone can only keep or lower them).
+void cross_pad(std::vector<std::vector<int>>& S, int d, int n, int cap, unsigned long long& st) {
+  for (int k = 1; k < d; ++k) {
+    const int len = d - k;
+    double full = 1.0;
+    for (int q = 0; q < len && full <= cap; ++q) full *= (n - 1);
+    const size_t want = (size_t)std::min<double>(cap, full);
+    // keep the distinct tuples already present (first occurrence, at most
+    // `want`), then add fresh ones
+    std::set<std::vector<int>> have;
+    std::vector<int> v;
+    const std::vector<int>& old = S[k];
+    for (size_t b = 0; b < old.size() / len && have.size() < want; ++b) {
+      std::vector<int> t(old.begin() + b * len, old.begin() + (b + 1) * len);
+      if (have.insert(t).second) v.insert(v.end(), t.begin(), t.end());
+    }
+    size_t guard = 0;
+    while (have.size() < want && guard++ < 100 * want + 100) {
+      std::vector<int> t(len);
+      for (auto& x : t) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        x = 1 + (int)((st >> 33) % (unsigned long long)(n - 1));
+      }
+      if (have.insert(t).second) v.insert(v.end(), t.begin(), t.end());
+    }
+    S[k] = std::move(v);
+  }
+}
+
+hopf_status init_cross(hopf_ctx* ctx, const double* m0, const double* C0, hopf_tt** out, bool* capped) {
+  const int d = ctx->p.d, n = ctx->p.n, cap = ctx->p.rank_cap;
+  if (cap > 256) return fail(ctx, HOPF_EINVAL, "cross construction supports rank_cap <= 256");
+  TRY(coop_reserve(ctx, 64));
+  CrossBufs B;
+  auto done = [&](hopf_status st) {
+    B.release();
+    return st;
+  };
+  const size_t Acap = (size_t)cap * n * cap;
+  if (dalloc(&B.A, Acap) != cudaSuccess || dalloc(&B.W, Acap) != cudaSuccess ||
+      dalloc(&B.Gw, (size_t)cap * cap) != cudaSuccess || dalloc(&B.Gi, (size_t)cap * cap) != cudaSuccess ||
+      dalloc(&B.il, (size_t)cap * d) != cudaSuccess || dalloc(&B.jr, (size_t)cap * d) != cudaSuccess ||
+      dalloc(&B.piv, (size_t)2 * cap + 1) != cudaSuccess || dalloc(&B.mc, (size_t)d + (size_t)d * d) != cudaSuccess) {
+    cudaGetLastError();
+    return done(fail(ctx, HOPF_ENOMEM, "cross: workspace allocation failed"));
+  }
+  std::vector<double> m(m0, m0 + d), C(C0, C0 + (size_t)d * d), mr(d), Cr((size_t)d * d);
+  for (int s = 0; s < d; ++s) {
+    mr[s] = m[d - 1 - s];
+    for (int t = 0; t < d; ++t) Cr[s + (size_t)d * t] = C[(d - 1 - s) + (size_t)d * (d - 1 - t)];
+  }
+  // initial right sets: distinct pseudo-random tuples (cross_pad)
+  std::vector<std::vector<int>> R(d + 1), L, Lm;
+  unsigned long long st = 0x9E3779B97F4A7C15ull;
+  hopf_status s = HOPF_OK;
+  for (int it = 0; it < 2 && s == HOPF_OK; ++it) {
+    cross_pad(R, d, n, cap, st);
+    s = cross_sweep(ctx, B, cap, m, C, R, L, nullptr);  // left sets
+    if (s != HOPF_OK) break;
+    std::vector<std::vector<int>> Rm = cross_mirror(L, d, true);
+    cross_pad(Rm, d, n, cap, st);
+    s = cross_sweep(ctx, B, cap, mr, Cr, Rm, Lm, nullptr);
+    if (s == HOPF_OK) R = cross_mirror(Lm, d, true);  // right sets
+  }
+  if (s == HOPF_OK) cross_pad(R, d, n, cap, st);
+  hopf_tt* t = nullptr;
+  if (s == HOPF_OK) s = tt_alloc(ctx, cap, &t);
+  if (s == HOPF_OK) s = cross_sweep(ctx, B, cap, m, C, R, L, t);
+  if (s == HOPF_OK) s = round_impl(ctx, t, ctx->p.tol, cap, nullptr, nullptr, capped);
+  if (s != HOPF_OK) {
+    tt_free(t);
+    return done(s);
+  }
+  *out = t;
+  return done(HOPF_OK);
+}
+
 }  // namespace
 
 // Accessors for the allocation-free entry point (noalloc.cu).
@@ -1188,12 +1358,16 @@ hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0, const double* C0
     *out = t;
     return HOPF_OK;
   }
-  // exact TT of the full grid: identity cores around one data core, then round
+  // small grids: exact TT of the full grid (identity cores around one data
+  // core), then round; larger grids: TT-cross interpolation, then round
   const int c = (d - 1) / 2;
   double total = 1.0;
   for (int k = 0; k < d; ++k) total *= n;
-  if (total > (double)(1 << 26))
-    return fail(ctx, HOPF_EINVAL, "correlated Gaussian initial state needs n^d <= 2^26 (got %g)", total);
+  if (total > (double)(1 << 20)) {
+    bool capped = false;
+    TRY(init_cross(ctx, m0, C0, out, &capped));
+    return capped ? HOPF_ERANKCAP : HOPF_OK;
+  }
   size_t A = 1, B = 1;
   for (int k = 0; k < c; ++k) A *= n;
   for (int k = c + 1; k < d; ++k) B *= n;

@@ -94,6 +94,19 @@ cudaError_t bd_vectors(const double* d, const double* e, int n, const double* in
 cudaError_t bd_back(const cplx* A, int lda, const cplx* tauq, int n, const double* X, int ldx, int nvec,
                     cplx* U, int ldu, cplx* Xp, int ldp, int mrows, cudaStream_t s);
 
+// ---- TT-cross construction of a Gaussian (cross.cu) --------------------------
+// A (rl n x rr, column-major, row alpha + rl i) = Phi0(Il[alpha], i, Jr[beta])
+// with the free index on mode kl; Il rl x kl, Jr rr x (d-kl-1) tuples.
+cudaError_t gauss_fibers(const double* agrid, int n, int d, const double* m, const double* C, const int* Il,
+                         int rl, int kl, const int* Jr, int rr, cplx* A, cudaStream_t s);
+// Complete-pivoting elimination (cooperative): pivot rows[cnt], cols[cnt],
+// *count = cnt, stopping at rel_tol of the first pivot; W: M x c scratch.
+cudaError_t cross_pivots(const cplx* A, int M, int c, double rel_tol, cplx* W, int* rows, int* cols, int* count,
+                         const CoopWs& ws, cudaStream_t s);
+// core (M x cnt) = A[:, cols] * A[rows, cols]^-1; Gw, Gi: cnt x cnt scratch.
+cudaError_t cross_core(const cplx* A, int M, const int* rows, const int* cols, int cnt, cplx* Gw, cplx* Gi,
+                       cplx* core, cudaStream_t s);
+
 // ---- dense helpers ------------------------------------------------------------
 // B (m x k, ldb) = conj-transpose of the k x m matrix A (lda).
 cudaError_t conj_transpose(const cplx* A, int lda, int k, int m, cplx* B, int ldb,
