@@ -307,6 +307,23 @@ __global__ void cross_core_kernel(const cplx* __restrict__ A, int M, const int* 
   core[e] = acc;
 }
 
+__global__ void cross_gather_kernel(const cplx* __restrict__ A, int M, const int* __restrict__ cols, int cnt,
+                                    cplx* __restrict__ out, cplx* __restrict__ eye, int* __restrict__ seq) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)M * cnt) return;
+  const int i = (int)(e % M), j = (int)(e / M);
+  out[e] = A[i + (size_t)M * cols[j]];
+  eye[e] = (i == j) ? mk(1, 0) : mk(0, 0);
+  if (e < cnt) seq[e] = (int)e;
+}
+
+cudaError_t cross_gather(const cplx* A, int M, const int* cols, int cnt, cplx* out, cplx* eye, int* seq,
+                         cudaStream_t s) {
+  const long long total = (long long)M * cnt;
+  cross_gather_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(A, M, cols, cnt, out, eye, seq);
+  return cudaGetLastError();
+}
+
 cudaError_t cross_core(const cplx* A, int M, const int* rows, const int* cols, int cnt, cplx* Gw, cplx* Gi,
                        cplx* core, cudaStream_t s) {
   if (cnt < 1) return cudaErrorInvalidValue;

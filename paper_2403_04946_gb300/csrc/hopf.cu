@@ -743,9 +743,14 @@ struct CrossBufs {
   int* il = nullptr;     // cap x d
   int* jr = nullptr;     // cap x d
   int* piv = nullptr;    // rows[cap], cols[cap], count
+  int* seq = nullptr;    // 0..cap-1
   double* mc = nullptr;  // m (d), C (d x d)
+  cplx* Q = nullptr;     // chosen columns, then their orthonormal basis (cap n x cap)
+  cplx* tau = nullptr;   // cap
+  cplx* T = nullptr;     // panel Grams of the QR
   void release() {
     cudaFree(A); cudaFree(W); cudaFree(Gw); cudaFree(Gi); cudaFree(il); cudaFree(jr); cudaFree(piv); cudaFree(mc);
+    cudaFree(seq); cudaFree(Q); cudaFree(tau); cudaFree(T);
   }
 };
 
@@ -780,8 +785,16 @@ hopf_status cross_sweep(hopf_ctx* ctx, CrossBufs& B, int cap, const std::vector<
     const int cnt = hp[2 * cap];
     if (cnt < 1) return fail(ctx, HOPF_ENUMERIC, "cross: no pivot at bond %d", k + 1);
     if (cores) {
+      // core = A[:, cols] A[rows, cols]^-1, formed stably as Q Q[rows, :]^-1
+      // with Q an orthonormal basis of A[:, cols] (the same matrix: the
+      // triangular factor cancels), so near-singular pivots cost no accuracy
       if ((size_t)M * cnt > cores->core_cap[k]) return fail(ctx, HOPF_EINVAL, "cross: core %d exceeds capacity", k);
-      CK(hk::cross_core(B.A, M, B.piv, B.piv + cap, cnt, B.Gw, B.Gi, cores->cores[k], ctx->stream));
+      CK(hk::cross_gather(B.A, M, B.piv + cap, cnt, B.Q, B.W, B.seq, ctx->stream));
+      int nb = 32;
+      CK(hk::geqrf(B.Q, M, M, cnt, B.tau, B.T, &nb, ctx->coop, ctx->stream, 0));
+      CK(hk::ormqr(B.Q, M, M, cnt, B.tau, B.T, nb, B.W, M, cnt, ctx->coop, ctx->stream, 0));
+      TRY(check_barrier(ctx));
+      CK(hk::cross_core(B.W, M, B.piv, B.seq, cnt, B.Gw, B.Gi, cores->cores[k], ctx->stream));
     }
     ranks[k] = rl;
     // next left set: (L[k][alpha], i) for each pivot row alpha + rl i
@@ -853,7 +866,7 @@ void cross_pad(std::vector<std::vector<int>>& S, int d, int n, int cap, unsigned
 hopf_status init_cross(hopf_ctx* ctx, const double* m0, const double* C0, hopf_tt** out, bool* capped) {
   const int d = ctx->p.d, n = ctx->p.n, cap = ctx->p.rank_cap;
   if (cap > 256) return fail(ctx, HOPF_EINVAL, "cross construction supports rank_cap <= 256");
-  TRY(coop_reserve(ctx, 64));
+  TRY(coop_reserve(ctx, std::max(64, cap)));
   CrossBufs B;
   auto done = [&](hopf_status st) {
     B.release();
@@ -863,7 +876,9 @@ hopf_status init_cross(hopf_ctx* ctx, const double* m0, const double* C0, hopf_t
   if (dalloc(&B.A, Acap) != cudaSuccess || dalloc(&B.W, Acap) != cudaSuccess ||
       dalloc(&B.Gw, (size_t)cap * cap) != cudaSuccess || dalloc(&B.Gi, (size_t)cap * cap) != cudaSuccess ||
       dalloc(&B.il, (size_t)cap * d) != cudaSuccess || dalloc(&B.jr, (size_t)cap * d) != cudaSuccess ||
-      dalloc(&B.piv, (size_t)2 * cap + 1) != cudaSuccess || dalloc(&B.mc, (size_t)d + (size_t)d * d) != cudaSuccess) {
+      dalloc(&B.piv, (size_t)2 * cap + 1) != cudaSuccess || dalloc(&B.mc, (size_t)d + (size_t)d * d) != cudaSuccess ||
+      dalloc(&B.seq, (size_t)cap) != cudaSuccess || dalloc(&B.Q, Acap) != cudaSuccess ||
+      dalloc(&B.tau, (size_t)cap) != cudaSuccess || dalloc(&B.T, (size_t)(cap / 8 + 2) * 32 * 32) != cudaSuccess) {
     cudaGetLastError();
     return done(fail(ctx, HOPF_ENOMEM, "cross: workspace allocation failed"));
   }

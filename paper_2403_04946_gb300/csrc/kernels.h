@@ -103,6 +103,9 @@ cudaError_t gauss_fibers(const double* agrid, int n, int d, const double* m, con
 // *count = cnt, stopping at rel_tol of the first pivot; W: M x c scratch.
 cudaError_t cross_pivots(const cplx* A, int M, int c, double rel_tol, cplx* W, int* rows, int* cols, int* count,
                          const CoopWs& ws, cudaStream_t s);
+// out = A[:, cols] (M x cnt), eye = [I; 0] (M x cnt), seq = 0..cnt-1.
+cudaError_t cross_gather(const cplx* A, int M, const int* cols, int cnt, cplx* out, cplx* eye, int* seq,
+                         cudaStream_t s);
 // core (M x cnt) = A[:, cols] * A[rows, cols]^-1; Gw, Gi: cnt x cnt scratch.
 cudaError_t cross_core(const cplx* A, int M, const int* rows, const int* cols, int cnt, cplx* Gw, cplx* Gi,
                        cplx* core, cudaStream_t s);
