@@ -832,10 +832,18 @@ std::vector<std::vector<int>> cross_mirror(const std::vector<std::vector<int>>& 
   return out;
 }
 
-// Pads every set S[k] (tuples of length d-k) with distinct pseudo-random
+// Pads every set S[k] (tuples over modes k..d-1) with distinct pseudo-random
 // tuples up to min(cap, (n-1)^(d-k)), so that the ranks found by the next
 // sweep can grow up to the cap (pivoting alone can only keep or lower them).
-void cross_pad(std::vector<std::vector<int>>& S, int d, int n, int cap, unsigned long long& st) {
+// Index q of a tuple is drawn around the grid centre with standard
+// deviation sd[k+q] grid points, where |Phi0| is not negligible: uniform
+// tuples in many modes land where Phi0 underflows to zero.
+void cross_pad(std::vector<std::vector<int>>& S, int d, int n, int cap, const std::vector<double>& sd,
+               unsigned long long& st) {
+  auto unif = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return ((double)(st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
   for (int k = 1; k < d; ++k) {
     const int len = d - k;
     double full = 1.0;
@@ -853,9 +861,11 @@ void cross_pad(std::vector<std::vector<int>>& S, int d, int n, int cap, unsigned
     size_t guard = 0;
     while (have.size() < want && guard++ < 100 * want + 100) {
       std::vector<int> t(len);
-      for (auto& x : t) {
-        st = st * 6364136223846793005ull + 1442695040888963407ull;
-        x = 1 + (int)((st >> 33) % (unsigned long long)(n - 1));
+      for (int q = 0; q < len; ++q) {
+        // Box-Muller normal deviate
+        const double g = std::sqrt(-2.0 * std::log(unif())) * std::cos(6.283185307179586 * unif());
+        int x = n / 2 + (int)std::lround(g * sd[k + q]);
+        t[q] = std::min(n - 1, std::max(1, x));
       }
       if (have.insert(t).second) v.insert(v.end(), t.begin(), t.end());
     }
@@ -887,20 +897,25 @@ hopf_status init_cross(hopf_ctx* ctx, const double* m0, const double* C0, hopf_t
     mr[s] = m[d - 1 - s];
     for (int t = 0; t < d; ++t) Cr[s + (size_t)d * t] = C[(d - 1 - s) + (size_t)d * (d - 1 - t)];
   }
+  // sampling widths in grid points: |Phi0| ~ exp(-C_kk a_k^2 / 2) along mode k
+  const double da = 2.0 * ctx->L / n;
+  std::vector<double> sd(d), sdr(d);
+  for (int k = 0; k < d; ++k) sd[k] = 1.0 / (std::sqrt(C[k + (size_t)d * k]) * da);
+  for (int k = 0; k < d; ++k) sdr[k] = sd[d - 1 - k];
   // initial right sets: distinct pseudo-random tuples (cross_pad)
   std::vector<std::vector<int>> R(d + 1), L, Lm;
   unsigned long long st = 0x9E3779B97F4A7C15ull;
   hopf_status s = HOPF_OK;
   for (int it = 0; it < 2 && s == HOPF_OK; ++it) {
-    cross_pad(R, d, n, cap, st);
+    cross_pad(R, d, n, cap, sd, st);
     s = cross_sweep(ctx, B, cap, m, C, R, L, nullptr);  // left sets
     if (s != HOPF_OK) break;
     std::vector<std::vector<int>> Rm = cross_mirror(L, d, true);
-    cross_pad(Rm, d, n, cap, st);
+    cross_pad(Rm, d, n, cap, sdr, st);
     s = cross_sweep(ctx, B, cap, mr, Cr, Rm, Lm, nullptr);
     if (s == HOPF_OK) R = cross_mirror(Lm, d, true);  // right sets
   }
-  if (s == HOPF_OK) cross_pad(R, d, n, cap, st);
+  if (s == HOPF_OK) cross_pad(R, d, n, cap, sd, st);
   hopf_tt* t = nullptr;
   if (s == HOPF_OK) s = tt_alloc(ctx, cap, &t);
   if (s == HOPF_OK) s = cross_sweep(ctx, B, cap, m, C, R, L, t);
