@@ -134,11 +134,14 @@ void tt_free(hopf_tt* t);
 /* ---- the hot path (Sec. 4.1 and App. A) ---------------------------------- */
 
 /* Builds the TT of Phi0(a) = exp(i a.m0 - a^T C0 a / 2), zero on the
- * boundary slot, rounded to the context's tol and rank_cap.  m0: host [d],
- * C0: host [d*d] (column-major, symmetric positive definite).  If the
- * context's L <= 0 it is set first to sqrt(36.8 / min_k C0_kk).  Diagonal
- * C0 gives the exact rank-1 product for any d; a correlated C0 is built by
- * rounding the full grid, which needs n^d <= 2^26 (else HOPF_EINVAL).
+ * boundary slot, rounded to the context's tol and rank_cap (Sec. 5's
+ * Gaussian random initial state).  m0: host [d], C0: host [d*d]
+ * (column-major, symmetric positive definite).  If the context's L <= 0 it
+ * is set first to sqrt(36.8 / min_k C0_kk).  Diagonal C0 gives the exact
+ * rank-1 product for any d.  A correlated C0 is built by rounding the exact
+ * full-grid TT when n^d <= 2^20, and otherwise by TT-cross interpolation
+ * (exact at the cross points, ranks up to rank_cap <= 256, two alternating
+ * sweeps) followed by the rounding.  HOPF_ERANKCAP: the cap bound.
  * *out is allocated with capacity rank_cap. */
 hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0,
                                const double* C0, hopf_tt** out);

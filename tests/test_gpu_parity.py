@@ -202,6 +202,43 @@ def test_init_gaussian_matches_full_grid(B):
     assert ctx.tt_get_ranks(t) == tt.ranks(tt.tt_svd(F, 1e-10, 200))
 
 
+def test_init_gaussian_cross_matches_full_grid(B):
+    """d = 5, n = 24 (24^5 > 2^20 grid points): the TT-cross construction
+    against the full-grid Gaussian (C2's correlated covariance)."""
+    w = synthetic.C2
+    d, n = 5, 24
+    m0, C0 = model.cell_moments(d, w.alpha, w.beta, w.sigma, w.ell)
+    L = model.default_L(C0)
+    ctx = B.Context(d=d, n=n, nu=w.nu, tol=1e-10, rank_cap=200, L=L)
+    t = ctx.hopf_init_gaussian(m0, C0)
+    F = fullgrid.phi0_grid(m0, C0, n, L)
+    err = rel(tt.full(ctx.tt_to_host(t)), F)
+    print(f"cross d=5: ranks {ctx.tt_get_ranks(t)}, rel err {err:.2e}")
+    assert err < 1e-9
+
+
+def test_init_gaussian_cross_pointwise_d10(B):
+    """d = 10, n = 16 (10^12 grid points, no full grid): the cross TT at
+    tol = 0 reproduces exp(i a.m0 - a^T C0 a / 2) pointwise, and its error
+    falls as the rank cap grows."""
+    d, n = 10, 16
+    m0, C0 = model.cell_moments(d, (0.0, 0.5), (1.0, 0.0), 0.4, 0.3)
+    L = model.default_L(C0)
+    a, _ = model.a_grid(n, L)
+    rng = np.random.default_rng(2)
+    idx = (n // 2 + rng.integers(-3, 4, size=(500, d))).astype(np.int32)
+    pts = a[idx]
+    want = np.exp(1j * pts @ m0 - 0.5 * np.einsum("pj,jk,pk->p", pts, C0, pts))
+    errs = []
+    for cap in (64, 128):
+        ctx = B.Context(d=d, n=n, nu=0.02, tol=0.0, rank_cap=cap, L=L)
+        t = ctx.hopf_init_gaussian(m0, C0)
+        errs.append(np.abs(ctx.hopf_eval_points(t, idx) - want).max())
+        ctx.close()
+    print(f"cross d=10 max abs err: cap 64 {errs[0]:.2e}, cap 128 {errs[1]:.2e}")
+    assert errs[1] < 1e-7 and errs[1] < errs[0]
+
+
 def test_init_gaussian_diagonal_is_rank_one(B):
     d, n = 8, 16
     m0 = np.linspace(-0.3, 0.4, d)
