@@ -217,25 +217,26 @@ def roofline(prof, mixed, peaks):
             "frac": achieved / peak, "peak_source": src, "traffic": None}
 
 
-def natural_state_error(w, stream, nsteps=5):
-    """Mixed vs FP64 after nsteps on a physical C3-size state: the Gaussian
-    initial state with the C3 mean and cell variances (diagonal covariance,
-    exact rank-1 TT), errors in Phi (TT difference norm), mean, covariance."""
+def natural_state_error(w, stream, nsteps=2):
+    """Mixed vs FP64 after nsteps from the physical C3 initial state: the
+    Gaussian with the C3 mean and cell covariance (correlated), built by
+    hopf_init_gaussian (TT-cross at this size; every interior rank at the
+    cap), errors in Phi (TT difference norm), mean and covariance."""
     import numpy as np
     from paper_2403_04946_gb300 import binding as B
     c0 = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=1.0, stream=stream)
     m0, C0 = c0.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
     c0.close()
-    C0d = np.diag(np.diag(C0))
     out = {}
     for prec in (B.HOPF_FP64, B.HOPF_MIXED):
         ctx = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=0.0, stream=stream, precision=prec)
-        t = ctx.hopf_init_gaussian(m0, C0d)
+        t = ctx.hopf_init_gaussian(m0, C0)
+        r0 = ctx.tt_get_ranks(t)
         ctx.hopf_step(t, w.dt, nsteps)
         mean, cov, _ = ctx.hopf_eval_moments(t)
-        out[prec] = (ctx.tt_to_host(t), mean, cov, ctx.tt_get_ranks(t))
+        out[prec] = (ctx.tt_to_host(t), mean, cov, ctx.tt_get_ranks(t), r0)
         ctx.close()
-    (cf, mf, vf, rf), (cm, mm, vm, rm) = out[B.HOPF_FP64], out[B.HOPF_MIXED]
+    (cf, mf, vf, rf, r0), (cm, mm, vm, rm, _) = out[B.HOPF_FP64], out[B.HOPF_MIXED]
     ctx = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=12.4, stream=stream)
     a = ctx.tt_from_host(cf, max_rank=max(rf))
     b = ctx.tt_from_host(cm, max_rank=max(rm))
@@ -245,8 +246,9 @@ def natural_state_error(w, stream, nsteps=5):
     ctx.close()
     return {"phi_rel_l2": phi, "mean_rel_max": float(np.abs(mm - mf).max() / np.abs(mf).max()),
             "cov_rel_max": float(np.abs(vm - vf).max() / np.abs(vf).max()), "steps": nsteps,
-            "state": "Gaussian initial state, C3 mean and cell variances, diagonal covariance (exact rank 1)",
-            "max_rank": int(max(rm))}
+            "state": "C3 Gaussian initial state (correlated cell covariance), TT-cross construction rounded to "
+                     "tol 1e-7 / cap 64",
+            "initial_max_rank": int(max(r0)), "max_rank": int(max(rm))}
 
 
 def run_ours(args, rank, world, local_rank):
