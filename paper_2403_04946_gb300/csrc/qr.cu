@@ -16,6 +16,11 @@
 namespace hk {
 
 constexpr int kQrThreads = 256;
+// Mixed-precision kernels run 16 warps per SM: their double-float chains
+// are latency-bound with 8 (each FP32 operation waits ~4.5 cycles on the
+// previous one), and they need fewer registers than the FP64 variants.
+constexpr int kQrThreadsMixed = 512;
+constexpr int qr_threads(bool mixed) { return mixed ? kQrThreadsMixed : kQrThreads; }
 constexpr int kNbMax = 32;
 
 struct QrSmem {
@@ -205,7 +210,7 @@ __device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
                            int ldx, int ncol, const cplx* w2) {
   // the column's coefficients -W2[:, l] live in shared memory (every lane
   // reads the same one: broadcast), the running update in registers
-  __shared__ df2 wsh[8][kNbMax];
+  __shared__ df2 wsh[kQrThreadsMixed / 32][kNbMax];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int l0 = 0; l0 < ncol; l0 += nw) {
     const int l = l0 + w;
@@ -326,7 +331,7 @@ __device__ __forceinline__ cplx reduce_partials(const cplx* pc, size_t pstride, 
 }
 
 template <int NB, bool MIXED>
-__global__ void __launch_bounds__(kQrThreads, 1)
+__global__ void __launch_bounds__(qr_threads(MIXED), 1)
 geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
              CoopWs ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -690,7 +695,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
 }
 
 template <int NB, bool MIXED>
-__global__ void __launch_bounds__(kQrThreads, 1)
+__global__ void __launch_bounds__(qr_threads(MIXED), 1)
 ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx* C, int ldc,
              int q, int R, CoopWs ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -779,7 +784,7 @@ static void pick_layout(int m, int* G, int* R, int* nb, size_t* smem) {
   int g = std::max(1, std::min(di.sm_count, (m + 63) / 64));
   int r = (m + g - 1) / g;
   int b = kNbMax;
-  const size_t lim = (size_t)di.max_smem_optin - 8192;  // static shared memory too
+  const size_t lim = (size_t)di.max_smem_optin - 16384;  // static shared memory too
   while (b > 4 && QrSmem::bytes(r, b) > lim) b >>= 1;
   *G = g;
   *R = r;
@@ -813,7 +818,7 @@ cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_ou
   e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A, &lda, &m, &k, &tau, &T, &nb, &R, &w};
-  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(qr_threads(mixed != 0)), args, smem, s);
 }
 
 cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* T,
@@ -845,7 +850,7 @@ cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const c
   e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&A, &lda, &m, &p, (void*)&T, &nb, &C, &ldc, &q, &R, &w};
-  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(qr_threads(mixed != 0)), args, smem, s);
 }
 
 }  // namespace hk
