@@ -217,7 +217,7 @@ def roofline(prof, mixed, peaks):
             "frac": achieved / peak, "peak_source": src, "traffic": None}
 
 
-def natural_state_error(w, stream, nsteps=2):
+def natural_state_error(w, stream, nsteps=3):
     """Mixed vs FP64 after nsteps from the physical C3 initial state: the
     Gaussian with the C3 mean and cell covariance (correlated), built by
     hopf_init_gaussian (TT-cross at this size; every interior rank at the
@@ -227,12 +227,21 @@ def natural_state_error(w, stream, nsteps=2):
     c0 = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=1.0, stream=stream)
     m0, C0 = c0.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
     c0.close()
-    out = {}
+    import torch
+    out, rate = {}, {}
     for prec in (B.HOPF_FP64, B.HOPF_MIXED):
         ctx = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=0.0, stream=stream, precision=prec)
         t = ctx.hopf_init_gaussian(m0, C0)
         r0 = ctx.tt_get_ranks(t)
-        ctx.hopf_step(t, w.dt, nsteps)
+        ctx.hopf_step(t, w.dt, 1)  # first step: workspace set-up, untimed
+        st = torch.cuda.ExternalStream(stream) if isinstance(stream, int) else torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        ctx.hopf_step(t, w.dt, nsteps - 1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        rate[prec] = (nsteps - 1) / (e0.elapsed_time(e1) / 1e3)
         mean, cov, _ = ctx.hopf_eval_moments(t)
         out[prec] = (ctx.tt_to_host(t), mean, cov, ctx.tt_get_ranks(t), r0)
         ctx.close()
@@ -248,7 +257,9 @@ def natural_state_error(w, stream, nsteps=2):
             "cov_rel_max": float(np.abs(vm - vf).max() / np.abs(vf).max()), "steps": nsteps,
             "state": "C3 Gaussian initial state (correlated cell covariance), TT-cross construction rounded to "
                      "tol 1e-7 / cap 64",
-            "initial_max_rank": int(max(r0)), "max_rank": int(max(rm))}
+            "initial_max_rank": int(max(r0)), "max_rank": int(max(rm)),
+            "natural_steps_per_s": {"mixed": rate[B.HOPF_MIXED], "fp64": rate[B.HOPF_FP64],
+                                    "note": "one RK4 step timed after one untimed step from the same state"}}
 
 
 def run_ours(args, rank, world, local_rank):
