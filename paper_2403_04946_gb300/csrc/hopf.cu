@@ -233,8 +233,6 @@ hopf_status build_ops(hopf_ctx* ctx) {
     set(hk::OP_Z, 0, i, cplx{-2.0 * e * a * dlo, 0.0});
     set(hk::OP_Z, 2, i, cplx{-2.0 * e * a * dup, 0.0});
   }
-  hopf_ctx* c = ctx;
-  (void)c;
   CK(cudaMemcpyAsync(ctx->d_coef, coef.data(), coef.size() * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_agrid, ctx->agrid.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

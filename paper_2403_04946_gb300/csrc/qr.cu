@@ -42,22 +42,6 @@ DV df2 ld_cg_df(const cplx* p) {
   return df2{v.x, v.y, v.z, v.w};
 }
 
-// Block sum of a real double-float value (every thread gets the result).
-DV void df_block_sum(float& h, float& l, float2* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = 16; o >= 1; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
-    df_add_part(h, l, h2, l2);
-  }
-  __syncthreads();
-  if (lane == 0) red[w] = make_float2(h, l);
-  __syncthreads();
-  h = red[0].x;
-  l = red[0].y;
-  for (int i = 1; i < nw; ++i) df_add_part(h, l, red[i].x, red[i].y);
-  __syncthreads();
-}
-
 // Warp reduce-scatter of CH per-lane values: afterwards a[0] of lane l
 // holds the sum over all 32 lanes of value number rs_index<CH>(l), with the
 // lanes that differ only in their low log2(32/CH) bits holding the same sum
@@ -338,9 +322,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
   cplx* P = reinterpret_cast<cplx*>(smem_raw);
   cplx* Ts = P + (size_t)nb * R;
   cplx* wl = Ts + (size_t)nb * nb;  // [2*kNbMax]
-  cplx* red = wl + 2 * kNbMax;      // [32]
   __shared__ double dred[32];
-  __shared__ float2 fred[32];
   __shared__ cplx bc[4];
 
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;

@@ -42,7 +42,6 @@ __global__ void __launch_bounds__(kJacThreads, 1)
 jacobi_kernel(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int accumJ, double tol,
               int max_sweeps, const double* eps_hat, CoopWs ws) {
   __shared__ double red[2][4][2];  // [group][warp][ga.x, ga.y]
-  __shared__ double fro_red[32];
   const int G = gridDim.x, g = blockIdx.x;
   const int grp = threadIdx.x / kGroup, gt = threadIdx.x % kGroup;
   const int lane = gt & 31, gw = gt >> 5;
