@@ -198,9 +198,18 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
     __syncthreads();
     // right update of own rows r > i: A[r,:] -= taup (A[r,:] . u) u^H
     for (int lr = lr0 + wid; lr < nact; lr += nw) {
-      cplx dot = mk(0, 0);
-      for (int c = i + 1 + lane; c < n; c += 32) dot = cfma(R(lr, c), uv[c], dot);
-      dot = warp_sum(dot);
+      // four interleaved partial dot products (a dependent FP64 FMA chain
+      // costs 64-128 cycles per step on this GPU)
+      cplx d0 = mk(0, 0), d1 = mk(0, 0), d2 = mk(0, 0), d3 = mk(0, 0);
+      int c = i + 1 + lane;
+      for (; c + 96 < n; c += 128) {
+        d0 = cfma(R(lr, c), uv[c], d0);
+        d1 = cfma(R(lr, c + 32), uv[c + 32], d1);
+        d2 = cfma(R(lr, c + 64), uv[c + 64], d2);
+        d3 = cfma(R(lr, c + 96), uv[c + 96], d3);
+      }
+      for (; c < n; c += 32) d0 = cfma(R(lr, c), uv[c], d0);
+      cplx dot = warp_sum(cadd(cadd(d0, d1), cadd(d2, d3)));
       const cplx f = cmul(tp, dot);
       const cplx nf = mk(-f.x, -f.y);
       for (int c = i + 1 + lane; c < n; c += 32) R(lr, c) = cfma(nf, cconj(uv[c]), R(lr, c));
