@@ -262,6 +262,46 @@ def natural_state_error(w, stream, nsteps=3):
                                     "note": "one RK4 step timed after one untimed step from the same state"}}
 
 
+def ensemble_rate(stream_int, nsteps=1):
+    """An ensemble of uneven instances (saturated states, ranks at their
+    caps), one RK4 step each: one instance at a time on the whole GPU versus
+    all at once (hopf_step_ensemble, each context limited to its share of
+    the SMs).  Steps per second of the whole ensemble, wall clock."""
+    import torch
+    from paper_2403_04946_gb300 import binding as B
+    import synthetic
+    specs = [(16, 64, 32), (12, 96, 32), (16, 64, 24), (8, 128, 32)]
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    share = sms // len(specs)
+    out = {}
+    for mode in ("sequential", "concurrent"):
+        members = []
+        for i, (d, n, r) in enumerate(specs):
+            cores, _ = synthetic.saturated_tt_cores(d, n, r, seed=40 + i)
+            s = torch.cuda.Stream() if mode == "concurrent" else None
+            ctx = B.Context(d=d, n=n, nu=0.02, tol=1e-7, rank_cap=r, L=12.4,
+                            stream=s.cuda_stream if s is not None else stream_int, precision=B.HOPF_MIXED)
+            if mode == "concurrent":
+                ctx.hopf_set_max_ctas(share)
+            members.append((ctx, ctx.tt_from_host(cores, max_rank=r), s))
+        run = (lambda: B.hopf_step_ensemble([(c, t) for c, t, _ in members], 1.2e-5, nsteps)) \
+            if mode == "concurrent" else \
+            (lambda: [c.hopf_step(t, 1.2e-5, nsteps) for c, t, _ in members])
+        run()  # warm-up: workspaces
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run()
+        torch.cuda.synchronize()
+        out[mode] = len(specs) * nsteps / (time.perf_counter() - t0)
+        for c, t, _ in members:
+            c.tt_free(t)
+            c.close()
+    return {"instances": [{"d": d, "n": n, "rank": r} for d, n, r in specs],
+            "sms_per_instance_concurrent": share, "precision": "mixed",
+            "steps_per_s_sequential": out["sequential"], "steps_per_s_concurrent": out["concurrent"],
+            "speedup": out["concurrent"] / out["sequential"]}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -338,6 +378,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
     err = natural_state_error(w, stream.cuda_stream) if not args.no_error_check else None
+    ens = ensemble_rate(stream.cuda_stream) if not args.no_error_check else None
 
     result = None
     if rank == 0:
@@ -366,6 +407,7 @@ def run_ours(args, rank, world, local_rank):
             "fp64": {"value": world * args.steps / el64, "unit": "steps/s", "ms_per_step": el64 / args.steps * 1e3,
                      "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},
             "mixed_vs_fp64_error": err,
+            "ensemble": ens,
             "apply_gbs": apply_gbs,
             "jacobi_sweeps_per_svd": prof["svd"].get("sweeps", 0) / max(1, prof["svd"].get("count", 0)),
             "cpu_baseline": cpu,

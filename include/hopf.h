@@ -96,6 +96,14 @@ hopf_status hopf_get_L(const hopf_ctx* ctx, double* L);
  * truncation up to rounding.  Errors: HOPF_EINVAL (unknown method). */
 enum { HOPF_SVD_AUTO = 0, HOPF_SVD_JACOBI = 1 };
 hopf_status hopf_set_svd_method(hopf_ctx* ctx, int method);
+/* Limits every cooperative kernel launched by this context to max_ctas
+ * CTAs, one per SM (0, the default: all SMs).  Several contexts whose
+ * limits add up to at most the SM count run their solves concurrently on
+ * their own streams (one host thread per context): an ensemble of
+ * independent initial states, each too small to fill the GPU, advances in
+ * parallel.  The paper solves one state at a time; this is a scheduling
+ * option only, results are unchanged.  Errors: HOPF_EINVAL (negative). */
+hopf_status hopf_set_max_ctas(hopf_ctx* ctx, int max_ctas);
 
 /* ---- model set-up -------------------------------------------------------- */
 
@@ -180,6 +188,16 @@ hopf_status tt_sum(hopf_ctx* ctx, int nterms, const hopf_tt* const* terms,
  * rank_log (may be NULL): host [8 * nsteps * (d+1)] ints receiving the ranks
  * after every rounding (for ranks replay).  forced_log (may be NULL): host
  * ranks to replay, same layout.  Returns HOPF_ERANKCAP if the cap bound. */
+/* Advances an ensemble of independent states (Sec. 5: the Gaussian random
+ * initial states are solved one at a time in the paper; here several are in
+ * flight at once): hopf_step(ctxs[a], tts[a], dt[a], nsteps) for every a,
+ * each on its own host thread and its context's stream and device.  The
+ * contexts must be distinct and should have hopf_set_max_ctas limits that
+ * add up to at most the SM count so that their cooperative kernels run
+ * side by side.  statuses: host [count], per-member status.  Returns the
+ * first failure, else HOPF_ERANKCAP if any cap bound, else HOPF_OK. */
+hopf_status hopf_step_ensemble(int count, hopf_ctx* const* ctxs, hopf_tt* const* tts,
+                               const double* dt, int nsteps, hopf_status* statuses);
 hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* inout, double dt, int nsteps,
                       double* discarded_norm_sum, int* rank_log,
                       const int* forced_log);

@@ -35,6 +35,8 @@ SIGNATURES = {
     "hopf_set_L": (_i, [_vp, _d]),
     "hopf_get_L": (_i, [_vp, _pd]),
     "hopf_set_svd_method": (_i, [_vp, _i]),
+    "hopf_set_max_ctas": (_i, [_vp, _i]),
+    "hopf_step_ensemble": (_i, [_i, _vp, _vp, _vp, _i, _vp]),
     "hopf_cell_moments": (_i, [_vp, _i, _pd, _pd, _d, _d, _pd, _pd]),
     "tt_from_host": (_i, [_vp, _pi, _pd, _i, C.POINTER(_vp)]),
     "tt_create": (_i, [_vp, _i, C.POINTER(_vp)]),
@@ -166,6 +168,9 @@ class Context:
     # -- calls ----------------------------------------------------------------
     def hopf_set_L(self, L):
         self._check(self.lib.hopf_set_L(self.h, float(L)))
+
+    def hopf_set_max_ctas(self, max_ctas):
+        self._check(self.lib.hopf_set_max_ctas(self.h, int(max_ctas)))
 
     def hopf_set_svd_method(self, method):
         self._check(self.lib.hopf_set_svd_method(self.h, int(method)))
@@ -308,3 +313,22 @@ class Context:
         v = C.c_double()
         self._check(self.lib.tt_norm(self.h, t, C.byref(v)))
         return v.value
+
+
+def hopf_step_ensemble(members, dt, nsteps):
+    """hopf_step_ensemble: advances every (Context, tt) member by nsteps RK4
+    steps, all members at once (one host thread per member inside the
+    library, each on its context's stream).  dt: one value or one per
+    member.  Returns the per-member statuses; raises on a failure."""
+    lib = load()
+    k = len(members)
+    ctxs = (C.c_void_p * k)(*[m[0].h.value for m in members])
+    tts = (C.c_void_p * k)(*[t.value if isinstance(t, C.c_void_p) else t for _, t in members])
+    dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (k,)))
+    sts = np.zeros(k, dtype=np.int32)
+    st = lib.hopf_step_ensemble(k, ctxs, tts, _dptr(dts), int(nsteps), _iptr(sts))
+    if st not in (HOPF_OK, HOPF_ERANKCAP):
+        bad = [i for i in range(k) if sts[i] not in (HOPF_OK, HOPF_ERANKCAP)]
+        msg = members[bad[0]][0].lib.hopf_last_error(members[bad[0]][0].h).decode() if bad else ""
+        raise HopfError(st, msg)
+    return [int(x) for x in sts]

@@ -223,9 +223,9 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
   }
 }
 
-int gebrd_grid(int n, int* nloc_out, size_t* smem_out) {
+int gebrd_grid(int n, int sms, int* nloc_out, size_t* smem_out) {
   const DevInfo& di = dev_info();
-  int G = std::max(1, std::min(di.sm_count, (n + 2) / 3));
+  int G = std::max(1, std::min(sms, (n + 2) / 3));
   for (;;) {
     const int nloc = (n + G - 1) / G;
     const size_t smem = ((size_t)nloc * n + 3 * (size_t)n + nloc) * sizeof(cplx);
@@ -234,15 +234,15 @@ int gebrd_grid(int n, int* nloc_out, size_t* smem_out) {
       *smem_out = smem;
       return G;
     }
-    if (G >= di.sm_count) return 0;
-    G = std::min(di.sm_count, G + 8);
+    if (G >= sms) return 0;
+    G = std::min(sms, G + 8);
   }
 }
 
-bool gebrd_fits(int n) {
+bool gebrd_fits(int n, const CoopWs& ws) {
   int nloc;
   size_t smem;
-  return n >= 1 && gebrd_grid(n, &nloc, &smem) > 0;
+  return n >= 1 && gebrd_grid(n, coop_sms(ws), &nloc, &smem) > 0;
 }
 
 cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cplx* taup,
@@ -250,7 +250,7 @@ cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cpl
   if (n <= 0) return cudaSuccess;
   int nloc;
   size_t smem;
-  const int G = gebrd_grid(n, &nloc, &smem);
+  const int G = gebrd_grid(n, coop_sms(ws), &nloc, &smem);
   if (G <= 0) return cudaErrorInvalidValue;
   if ((size_t)2 * G * (n + 1) > ws.pc_elems || (size_t)6 * n > ws.wfin_elems || 2 * G > 1024)
     return cudaErrorInvalidValue;

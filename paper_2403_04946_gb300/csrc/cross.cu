@@ -196,12 +196,13 @@ cudaError_t cross_pivots(const cplx* A, int M, int c, double rel_tol, cplx* W, i
                          const CoopWs& ws, cudaStream_t s) {
   if (c > 256 || M < 1 || c < 1) return cudaErrorInvalidValue;
   const DevInfo& di = dev_info();
-  int G = std::max(1, std::min(di.sm_count, (M + 63) / 64));
+  const int sms = coop_sms(ws);
+  int G = std::max(1, std::min(sms, (M + 63) / 64));
   int R = (M + G - 1) / G;
   if (R > 1024) {
     R = 1024;
     G = (M + R - 1) / R;
-    if (G > di.sm_count) return cudaErrorInvalidValue;
+    if (G > sms) return cudaErrorInvalidValue;
   }
   if ((size_t)2 * G > ws.pc_elems) return cudaErrorInvalidValue;
   cudaError_t err = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);

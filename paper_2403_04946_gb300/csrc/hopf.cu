@@ -11,6 +11,7 @@
 #include <new>
 #include <string>
 #include <set>
+#include <thread>
 #include <vector>
 
 #include "../../include/hopf.h"
@@ -70,6 +71,7 @@ struct hopf_ctx {
   // cooperative-kernel workspace
   hk::CoopWs coop{};
   int coop_kcap = 0;
+  int device = 0;
   int svd_method = HOPF_SVD_AUTO;
   // small device scalars and pinned mirrors
   double* d_dbl = nullptr;  // [16]
@@ -472,7 +474,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     if (forced && (forced_c < 1 || forced_c > nsv))
       return fail(ctx, HOPF_EINVAL, "forced rank %d at bond %d outside [1, %d]", forced_c, c + 1, nsv);
     // Square factors: bidiagonalisation, bisection and inverse iteration.
-    const bool use_bd = case1 && ctx->svd_method != HOPF_SVD_JACOBI && hk::gebrd_fits(pp);
+    const bool use_bd = case1 && ctx->svd_method != HOPF_SVD_JACOBI && hk::gebrd_fits(pp, ctx->coop);
     if (use_bd) {
       CK(cudaMemcpyAsync(w.Mb, w.Rb, (size_t)pp * cols * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
       LAUNCH(HOPF_K_SVD, gebrd_flops(pp), 0, 1, hk::gebrd(w.Mb, pp, pp, w.bd_d, w.bd_e, w.bd_tauq, w.bd_taup, ctx->coop, ctx->stream));
@@ -959,6 +961,7 @@ hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out) {
   if (!ctx) return HOPF_ENOMEM;
   ctx->p = *p;
   ctx->stream = (cudaStream_t)stream;
+  cudaGetDevice(&ctx->device);
   ctx->L = p->L;
   auto bad = [&](hopf_status st) {
     hopf_destroy(ctx);
@@ -1024,6 +1027,13 @@ hopf_status hopf_set_L(hopf_ctx* ctx, double L) {
   if (!(L > 0.0) || !std::isfinite(L)) return fail(ctx, HOPF_EINVAL, "L must be positive");
   ctx->L = L;
   return build_ops(ctx);
+}
+
+hopf_status hopf_set_max_ctas(hopf_ctx* ctx, int max_ctas) {
+  if (!ctx) return HOPF_EINVAL;
+  if (max_ctas < 0) return fail(ctx, HOPF_EINVAL, "max_ctas must be >= 0");
+  ctx->coop.max_ctas = max_ctas;
+  return HOPF_OK;
 }
 
 hopf_status hopf_set_svd_method(hopf_ctx* ctx, int method) {
@@ -1448,6 +1458,33 @@ hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0, const double* C0
   }
   *out = t;
   return capped ? HOPF_ERANKCAP : HOPF_OK;
+}
+
+hopf_status hopf_step_ensemble(int count, hopf_ctx* const* ctxs, hopf_tt* const* tts, const double* dt,
+                               int nsteps, hopf_status* statuses) {
+  if (count < 0 || (count > 0 && (!ctxs || !tts || !dt || !statuses))) return HOPF_EINVAL;
+  for (int a = 0; a < count; ++a) {
+    if (!ctxs[a] || !tts[a]) return HOPF_EINVAL;
+    for (int b = 0; b < a; ++b)
+      if (ctxs[a] == ctxs[b]) return fail(ctxs[a], HOPF_EINVAL, "hopf_step_ensemble: a context appears twice");
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(count);
+  for (int a = 0; a < count; ++a) {
+    pool.emplace_back([=]() {
+      if (cudaSetDevice(ctxs[a]->device) != cudaSuccess) {
+        statuses[a] = fail(ctxs[a], HOPF_ECUDA, "hopf_step_ensemble: cudaSetDevice failed");
+        return;
+      }
+      statuses[a] = hopf_step(ctxs[a], tts[a], dt[a], nsteps, nullptr, nullptr, nullptr);
+    });
+  }
+  for (auto& th : pool) th.join();
+  hopf_status worst = HOPF_OK;
+  for (int a = 0; a < count; ++a)
+    if (statuses[a] != HOPF_OK && statuses[a] != HOPF_ERANKCAP) return statuses[a];
+    else if (statuses[a] == HOPF_ERANKCAP) worst = HOPF_ERANKCAP;
+  return worst;
 }
 
 }  // extern "C"

@@ -32,7 +32,13 @@ struct CoopWs {
   unsigned int* colver;
   unsigned long long* pairchk;
   int jac_cap;
+  // upper bound on the CTAs (one per SM) of every cooperative launch that
+  // uses this workspace; 0 = all SMs.  Contexts limited to disjoint shares
+  // of the SMs run their cooperative kernels concurrently.
+  int max_ctas;
 };
+// SMs available to a cooperative launch on this workspace.
+int coop_sms(const CoopWs& ws);
 
 // Householder QR of the column-major m x k matrix A (lda >= m), in place:
 // R on and above the diagonal, reflector tails below, tau[min(m,k)], and for
@@ -75,7 +81,7 @@ cudaError_t rank_select(const cplx* M, int ldm, int nr, int nc, const double* ep
 // Cooperative launch, one grid barrier per column.
 cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cplx* taup,
                   const CoopWs& ws, cudaStream_t s);
-bool gebrd_fits(int n);  // shared-memory resident rows fit on this device
+bool gebrd_fits(int n, const CoopWs& ws);  // shared-memory resident rows fit
 // All singular values of B, sorted descending, into sig[n]; a2 (float2
 // [2n]) and info (double [4]) are scratch kept for bd_vectors.
 cudaError_t bd_sigma(const double* d, const double* e, int n, float2* a2, double* info, double* sig,

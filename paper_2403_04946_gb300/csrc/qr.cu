@@ -761,9 +761,9 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
   if (MIXED) rows_to_fp64(C, ldc, r0, r1, 0, q, E);
 }
 
-static void pick_layout(int m, int* G, int* R, int* nb, size_t* smem) {
+static void pick_layout(int m, const CoopWs& ws, int* G, int* R, int* nb, size_t* smem) {
   const DevInfo& di = dev_info();
-  int g = std::max(1, std::min(di.sm_count, (m + 63) / 64));
+  int g = std::max(1, std::min(coop_sms(ws), (m + 63) / 64));
   int r = (m + g - 1) / g;
   int b = kNbMax;
   const size_t lim = (size_t)di.max_smem_optin - 16384;  // static shared memory too
@@ -779,7 +779,7 @@ cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_ou
   if (m <= 0 || k <= 0) return cudaSuccess;
   int G, R, nb;
   size_t smem;
-  pick_layout(m, &G, &R, &nb, &smem);
+  pick_layout(m, ws, &G, &R, &nb, &smem);
   // per CTA: S1 partials nb (nb + k), then the panel's exchange tail 4 nb
   if ((size_t)G * ((size_t)nb * (nb + k) + 4 * (size_t)nb) > ws.pc_elems || (size_t)nb * (nb + k) > ws.wfin_elems)
     return cudaErrorInvalidValue;
@@ -809,7 +809,7 @@ cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const c
   if (m <= 0 || p <= 0 || q <= 0) return cudaSuccess;
   int G, R, nb2;
   size_t smem;
-  pick_layout(m, &G, &R, &nb2, &smem);
+  pick_layout(m, ws, &G, &R, &nb2, &smem);
   if (nb2 != nb) {
     // the layout depends only on m, so geqrf and ormqr agree
     return cudaErrorInvalidValue;

@@ -227,7 +227,7 @@ cudaError_t jacobi_svd(cplx* M, int ldm, int nr, int nc, cplx* J, int ldj, int a
   const DevInfo& di = dev_info();
   const int npairs = (nc + 1) / 2;
   // two pairs per CTA, as many CTAs as SMs allow
-  const int G = std::max(1, std::min(di.sm_count, (npairs + 1) / 2));
+  const int G = std::max(1, std::min(coop_sms(ws), (npairs + 1) / 2));
   // Stop rotating a pair once |a_i^H a_j| <= tol |a_i| |a_j|.  The computed
   // inner product of two length-nr columns carries a rounding error of up
   // to about nr * eps relative to |a_i| |a_j|, so a threshold below that

@@ -7,6 +7,11 @@
 
 namespace hk {
 
+int coop_sms(const CoopWs& ws) {
+  const int sm = dev_info().sm_count;
+  return ws.max_ctas > 0 ? std::min(ws.max_ctas, sm) : sm;
+}
+
 const DevInfo& dev_info() {
   static DevInfo di = [] {
     DevInfo d{};

@@ -154,6 +154,35 @@ def test_square_svd_paths_agree(B, n):
         assert abs(disc - wdisc) <= 1e-6 * wdisc + 1e-14 * np.linalg.norm(Fw)
 
 
+def test_max_ctas_and_ensemble_match_solo_runs(B):
+    """Three independent states advanced together by hopf_step_ensemble,
+    each context limited to 40 CTAs, give the same tensors as each state
+    advanced alone on the whole GPU (different CTA counts change only the
+    order of floating-point sums)."""
+    specs = [(5, 12, 10, 31), (6, 10, 8, 32), (4, 16, 12, 33)]
+    solo, members, ctxs = [], [], []
+    for d, n, r, seed in specs:
+        cores, _ = synthetic.saturated_tt_cores(d, n, r, seed=seed)
+        cores = [0.3 * c for c in cores]
+        ctx = ctx_for(B, d, n, tol=1e-9, cap=3 * r, L=2.5)
+        t = ctx.tt_from_host(cores, max_rank=3 * r)
+        ctx.hopf_step(t, 1e-4, 2)
+        solo.append(tt.full(ctx.tt_to_host(t)))
+        ctx.close()
+        ectx = ctx_for(B, d, n, tol=1e-9, cap=3 * r, L=2.5)
+        ectx.hopf_set_max_ctas(40)
+        members.append((ectx, ectx.tt_from_host(cores, max_rank=3 * r)))
+        ctxs.append(ectx)
+    st = B.hopf_step_ensemble(members, 1e-4, 2)
+    assert all(x in (B.HOPF_OK, B.HOPF_ERANKCAP) for x in st)
+    for (ectx, t), want in zip(members, solo):
+        assert rel(tt.full(ectx.tt_to_host(t)), want) < 1e-11
+    with pytest.raises(B.HopfError):
+        B.hopf_step_ensemble([members[0], members[0]], 1e-4, 1)  # a context twice
+    for c in ctxs:
+        c.close()
+
+
 def test_round_error_bound_and_cap_status(B):
     d, n = 5, 16
     x = synthetic.random_tt_cores(d, n, [1, 10, 20, 20, 10, 1], 9)
