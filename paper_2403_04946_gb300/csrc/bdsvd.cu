@@ -254,7 +254,7 @@ cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cpl
   if (G <= 0) return cudaErrorInvalidValue;
   if ((size_t)2 * G * (n + 1) > ws.pc_elems || (size_t)6 * n > ws.wfin_elems || 2 * G > 1024)
     return cudaErrorInvalidValue;
-  cudaError_t err = cudaFuncSetAttribute(gebrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = allow_smem((const void*)gebrd_kernel, smem);
   if (err != cudaSuccess) return err;
   err = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
   if (err != cudaSuccess) return err;
@@ -645,7 +645,7 @@ cudaError_t bd_vectors(const double* d, const double* e, int n, const double* in
   if (nvec <= 0) return cudaSuccess;
   if (kt > 0) {
     const size_t smem = sizeof(double) * kSolveArrays * 2 * (size_t)n;
-    cudaError_t err = cudaFuncSetAttribute(bd_vectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = allow_smem((const void*)bd_vectors_kernel, smem);
     if (err != cudaSuccess) return err;
     bd_vectors_kernel<<<kt, 32, smem, s>>>(d, e, n, info, sig, kt, X, ldx, Zs);
     err = cudaGetLastError();
@@ -713,7 +713,7 @@ cudaError_t bd_back(const cplx* A, int lda, const cplx* tauq, int n, const doubl
                     cplx* U, int ldu, cplx* Xp, int ldp, int mrows, cudaStream_t s) {
   if (nvec <= 0) return cudaSuccess;
   const size_t smem = sizeof(cplx) * (size_t)n * 3;
-  cudaError_t err = cudaFuncSetAttribute(bd_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = allow_smem((const void*)bd_back_kernel, smem);
   if (err != cudaSuccess) return err;
   bd_back_kernel<<<nvec, 64, smem, s>>>(A, lda, tauq, n, X, ldx, nvec, U, ldu, Xp, ldp, mrows);
   return cudaGetLastError();

@@ -39,6 +39,11 @@ struct CoopWs {
 };
 // SMs available to a cooperative launch on this workspace.
 int coop_sms(const CoopWs& ws);
+// Raises the kernel's dynamic shared-memory limit to the device maximum
+// (opt-in size minus its static shared memory) once per function and
+// checks that `need` bytes fit.  The attribute is process-wide, so it is
+// never lowered: contexts on several host threads launch concurrently.
+cudaError_t allow_smem(const void* fn, size_t need);
 
 // Householder QR of the column-major m x k matrix A (lda >= m), in place:
 // R on and above the diagonal, reflector tails below, tau[min(m,k)], and for

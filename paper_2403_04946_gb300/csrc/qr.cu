@@ -794,7 +794,7 @@ cudaError_t geqrf(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb_ou
     else if (nb == 16) fn = (void*)geqrf_kernel<16, false>;
     else fn = (void*)geqrf_kernel<8, false>;
   }
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   CoopWs w = ws;
   e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
@@ -826,7 +826,7 @@ cudaError_t ormqr(const cplx* A, int lda, int m, int p, const cplx* tau, const c
     else if (nb == 16) fn = (void*)ormqr_kernel<16, false>;
     else fn = (void*)ormqr_kernel<8, false>;
   }
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
   CoopWs w = ws;
   e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);

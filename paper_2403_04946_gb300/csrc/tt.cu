@@ -3,9 +3,29 @@
 // FP64 helpers (transposes, norms, small GEMMs) the rounding sweep uses.
 #include <algorithm>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "kernels.h"
 
 namespace hk {
+
+cudaError_t allow_smem(const void* fn, size_t need) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(fn);
+  if (it == done.end()) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const size_t cap = (size_t)dev_info().max_smem_optin - fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    if (e != cudaSuccess) return e;
+    it = done.emplace(fn, cap).first;
+  }
+  return need <= it->second ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 int coop_sms(const CoopWs& ws) {
   const int sm = dev_info().sm_count;
