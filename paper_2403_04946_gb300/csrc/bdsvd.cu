@@ -80,6 +80,7 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
   cplx* vloc = uv + n;                           // v_r of own rows (nloc)
   __shared__ double dred[32];
   __shared__ cplx bc[4];
+  __shared__ cplx bcr[4];
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const size_t pstride = (size_t)n + 1;
@@ -161,38 +162,43 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
       if (c >= i + 2) sqp += cabs2(nr);
     }
     sqp = block_sum(sqp, dred);  // its barriers also publish fv / nrow / vloc
-    for (int c = i + 1 + tid; c < n; c += blockDim.x) {
-      const cplx f = fv[c];
-      const cplx nf = mk(-f.x, -f.y);
-      for (int lr = lr0; lr < nact; ++lr) R(lr, c) = cfma(vloc[lr], nf, R(lr, c));
-    }
-    for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) R(lr, i) = vloc[lr];
     if (owner && tid == 0) {
       R(i / G, i) = bc[2];
       dg[i] = bc[2].x;
       tauq[i] = tq;
     }
+    // warp 0 forms the right reflector of the updated row i (every CTA
+    // does; it zeroes the row beyond i+1) while warps 1.. apply the left
+    // reflector to the own rows: A[r,c] -= v_r conj(tau) w_c, column i
+    // keeps v_r
+    if (wid == 0) {
+      if (lane == 0 && i + 1 < n) {
+        cplx tp, sp;
+        double beta;
+        house_scalars(cconj(nrow[i + 1]), sqp, &tp, &sp, &beta);
+        bcr[0] = tp;
+        bcr[1] = sp;
+        bcr[2] = mk(beta, 0.0);
+      }
+    } else {
+      const int t1 = tid - 32, nt1 = blockDim.x - 32;
+      for (int c = i + 1 + t1; c < n; c += nt1) {
+        const cplx f = fv[c];
+        const cplx nf = mk(-f.x, -f.y);
+        for (int lr = lr0; lr < nact; ++lr) R(lr, c) = cfma(vloc[lr], nf, R(lr, c));
+      }
+      for (int lr = lr0 + t1; lr < nact; lr += nt1) R(lr, i) = vloc[lr];
+    }
     if (i + 1 >= n) break;
     __syncthreads();
-    // right reflector of the updated row i (computed by every CTA): it
-    // zeroes the row beyond i+1
-    if (tid == 0) {
-      cplx tp, sp;
-      double beta;
-      house_scalars(cconj(nrow[i + 1]), sqp, &tp, &sp, &beta);
-      bc[0] = tp;
-      bc[1] = sp;
-      bc[2] = mk(beta, 0.0);
-    }
-    __syncthreads();
-    const cplx tp = bc[0], scp = bc[1];
+    const cplx tp = bcr[0], scp = bcr[1];
     for (int c = i + 1 + tid; c < n; c += blockDim.x) {
       const cplx u = (c == i + 1) ? mk(1, 0) : cmul(cconj(nrow[c]), scp);
       uv[c] = u;
-      if (owner) R(i / G, c) = (c == i + 1) ? bc[2] : cconj(u);
+      if (owner) R(i / G, c) = (c == i + 1) ? bcr[2] : cconj(u);
     }
     if (owner && tid == 0) {
-      eg[i] = bc[2].x;
+      eg[i] = bcr[2].x;
       taup[i] = tp;
     }
     __syncthreads();

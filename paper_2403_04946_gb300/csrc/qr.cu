@@ -763,7 +763,9 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
 
 static void pick_layout(int m, const CoopWs& ws, int* G, int* R, int* nb, size_t* smem) {
   const DevInfo& di = dev_info();
-  int g = std::max(1, std::min(coop_sms(ws), (m + 63) / 64));
+  // row blocks of >= 64 rows, but small matrices (the wide first and last
+  // cores) still spread over up to 16 CTAs of >= 8 rows
+  int g = std::max(1, std::min(coop_sms(ws), std::max((m + 63) / 64, std::min(16, (m + 7) / 8))));
   int r = (m + g - 1) / g;
   int b = kNbMax;
   const size_t lim = (size_t)di.max_smem_optin - 16384;  // static shared memory too
