@@ -21,6 +21,8 @@ differential equations" (arXiv 2403.04946) that it follows:
                   TT-SVD of a full tensor, moments, point evaluation.
 * ``reference``   the linear closed form (nonlinear term off) and a Monte-Carlo
                   estimate from the discrete Burgers ODE.
+* ``mlp``         the learned surrogate's network (not in the paper): forward
+                  and backward passes, Adam, normalisation, ensemble bound.
 
 Parity status of each function is listed in its docstring ("pinned by ..." or
 "parity unpinned").
