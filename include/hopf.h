@@ -68,11 +68,12 @@ typedef struct {
                   /* hopf_init_gaussian to sqrt(36.8 / min_k C0_kk)       */
   double tol;     /* relative rounding tolerance used by hopf_step        */
   int rank_cap;   /* rank cap used by hopf_step                           */
-  int precision;  /* HOPF_FP64: every step in FP64.  HOPF_MIXED: the     */
-                  /* Householder panels (reflectors, T factors) and the   */
-                  /* Jacobi SVD that sets the ranks stay FP64; trailing   */
-                  /* QR updates, Q applications and merge products run in */
-                  /* FP32 and are added to FP64 storage as corrections.   */
+  int precision;  /* HOPF_FP64: every step in FP64.  HOPF_MIXED: QR     */
+                  /* panels and trailing updates, Q applications and      */
+                  /* merge products run in double-float arithmetic (each  */
+                  /* value an unevaluated sum of two FP32 numbers, about  */
+                  /* 1e-13 relative); Householder scalars, the SVD that   */
+                  /* sets the ranks and all storage stay FP64.            */
   int nonlinear;  /* 1: full Burgers generator; 0: drop the (i/2) D1 term */
 } hopf_params;
 
@@ -248,6 +249,83 @@ hopf_status tt_norm(hopf_ctx* ctx, const hopf_tt* t, double* norm);
 /* Overwrites t with host cores (same layout and rules as tt_from_host; the
  * ranks must fit t's capacity).  No device allocation. */
 hopf_status tt_set_from_host(hopf_tt* t, const int* ranks, const double* cores);
+
+/* ---- learned surrogate: a small multilayer perceptron ------------------- */
+/* Not part of the paper's method: a network that maps the parameters of a
+ * Gaussian initial state (nu, sigma, ell, Fourier coefficients of the mean,
+ * horizon T) to the mean and covariance of the cell averages at T, trained
+ * only on outputs of this solver, with the solver as its fallback.
+ *
+ * Network.  Linear layers l = 0..depth over the widths
+ * [n_in, width (depth times), n_out]; every hidden layer is followed by
+ * GELU(z) = z Phi(z) (Phi the standard normal CDF, Hendrycks & Gimpel 2016),
+ * the last layer is linear.  Parameters of one member, packed: for each
+ * layer W_l (fan_out x fan_in, row-major) then b_l (fan_out); P floats per
+ * member, `members` members back to back ([members][P]).  The library keeps
+ * FP32 master parameters and Adam moments; products read BF16 copies of the
+ * weights (round to nearest even) with FP32 activations and FP32
+ * accumulation; biases stay FP32.
+ *
+ * Normalisation.  hopf_mlp_set_data stores a data set and its per-column
+ * mean and population standard deviation (1 for a constant column).  The
+ * network sees x_hat = (x - mu_x) / sd_x and is trained on
+ * y_hat = (y - mu_y) / sd_y with the mean-squared error over batch and
+ * outputs; predictions are mapped back to y = mu_y + sd_y * net(x_hat).
+ *
+ * Ensemble and error bound.  The members are trained independently (their
+ * own initial parameters and batches) in the same launches.  A prediction
+ * is the member mean ybar, and its error bound is
+ * kappa * ||s||_2 / ||ybar||_2, s the per-output standard deviation over the
+ * members: the caller calibrates kappa on held-out solves and sends every
+ * query whose bound is too large to the solver.
+ *
+ * Training runs Adam (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8)
+ * as one CUDA graph per step, replayed `iters` times on the library's own
+ * stream (ordered after the context's stream; the call returns when done).
+ * Random draws (initial parameters, batch indices) are inputs. */
+typedef struct hopf_mlp hopf_mlp;
+typedef struct {
+  int n_in, width, depth, n_out; /* depth >= 0 hidden layers; sizes 1..4096 */
+  int members;                   /* 1..64 networks in the ensemble         */
+  int max_batch;                 /* largest training batch, and the chunk  */
+                                 /* size of hopf_mlp_predict               */
+} hopf_mlp_params;
+
+/* Creates a network on the context's device with initial parameters `init`
+ * (host [members][P] floats, P from hopf_mlp_param_count).  Errors:
+ * HOPF_EINVAL, HOPF_ENOMEM, HOPF_ECUDA. */
+hopf_status hopf_mlp_create(hopf_ctx* ctx, const hopf_mlp_params* p,
+                            const float* init, hopf_mlp** out);
+/* P, the number of parameters of one member. */
+hopf_status hopf_mlp_param_count(const hopf_mlp_params* p, long long* P);
+/* Copies the FP32 master parameters to host [members][P]. */
+hopf_status hopf_mlp_get_params(hopf_mlp* m, float* out);
+/* Stores nsamples (x, y) pairs (host, row-major [nsamples][n_in] and
+ * [nsamples][n_out], doubles) on the device and computes the normalisation
+ * statistics from them; stats (may be NULL) receives host
+ * [2 (n_in + n_out)] = mu_x, sd_x, mu_y, sd_y.  Errors: HOPF_EINVAL for
+ * nsamples < 1 or non-finite data. */
+hopf_status hopf_mlp_set_data(hopf_mlp* m, int nsamples, const double* x,
+                              const double* y, double* stats);
+/* Runs `iters` Adam steps.  idx: host [iters][members][batch] sample
+ * indices in [0, nsamples); lr: host [iters] learning rates; loss (may be
+ * NULL): host [iters][members], the batch loss before each step.  Errors:
+ * HOPF_EINVAL (no data, batch outside [1, max_batch], index out of range),
+ * HOPF_ECUDA. */
+hopf_status hopf_mlp_train(hopf_mlp* m, int iters, int batch, const int* idx,
+                           const float* lr, float* loss);
+/* Loss and gradient at the current parameters for one batch per member
+ * (idx: host [members][batch]), without an update.  loss: host [members];
+ * grad: host [members][P] (FP32). */
+hopf_status hopf_mlp_loss_grad(hopf_mlp* m, int batch, const int* idx,
+                               float* loss, float* grad);
+/* Ensemble prediction for nq queries x (host [nq][n_in]): y host
+ * [nq][n_out] (the member mean, physical units), bound host [nq],
+ * members_y (may be NULL) host [members][nq][n_out].  Errors: HOPF_EINVAL
+ * (no statistics yet, nq < 0). */
+hopf_status hopf_mlp_predict(hopf_mlp* m, int nq, const double* x, double kappa,
+                             double* y, double* bound, double* members_y);
+void hopf_mlp_free(hopf_mlp* m);
 
 /* ---- instrumentation ----------------------------------------------------- */
 

@@ -57,6 +57,14 @@ SIGNATURES = {
     "hopf_profile_enable": (_i, [_vp, _i]),
     "hopf_profile_read": (_i, [_vp, _vp, _i]),
     "hopf_eval_points_noalloc": (_i, [_vp, _i, _pi, _pd]),
+    "hopf_mlp_create": (_i, [_vp, _vp, _vp, C.POINTER(_vp)]),
+    "hopf_mlp_param_count": (_i, [_vp, C.POINTER(C.c_longlong)]),
+    "hopf_mlp_get_params": (_i, [_vp, _vp]),
+    "hopf_mlp_set_data": (_i, [_vp, _i, _pd, _pd, _pd]),
+    "hopf_mlp_train": (_i, [_vp, _i, _i, _pi, _vp, _vp]),
+    "hopf_mlp_loss_grad": (_i, [_vp, _i, _pi, _vp, _vp]),
+    "hopf_mlp_predict": (_i, [_vp, _i, _pd, _d, _pd, _pd, _pd]),
+    "hopf_mlp_free": (None, [_vp]),
 }
 
 KERNEL_CLASSES = ["qr", "apply_q", "svd", "apply", "gemm", "sum", "small", "unused"]
@@ -72,6 +80,11 @@ class HopfParams(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.c_int), ("nu", C.c_double), ("L", C.c_double),
                 ("tol", C.c_double), ("rank_cap", C.c_int), ("precision", C.c_int),
                 ("nonlinear", C.c_int)]
+
+
+class HopfMlpParams(C.Structure):
+    _fields_ = [("n_in", C.c_int), ("width", C.c_int), ("depth", C.c_int), ("n_out", C.c_int),
+                ("members", C.c_int), ("max_batch", C.c_int)]
 
 
 class HopfError(RuntimeError):
@@ -332,3 +345,82 @@ def hopf_step_ensemble(members, dt, nsteps):
         msg = members[bad[0]][0].lib.hopf_last_error(members[bad[0]][0].h).decode() if bad else ""
         raise HopfError(st, msg)
     return [int(x) for x in sts]
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Mlp:
+    """hopf_mlp_*: the surrogate network ensemble of the library (BF16
+    weights, FP32 activations and accumulation, Adam).  Parameters cross
+    the boundary as float32 arrays [members][P] in the header's packed
+    layout; data and predictions as float64."""
+
+    def __init__(self, ctx, n_in, width, depth, n_out, members, max_batch, init):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.p = HopfMlpParams(n_in, width, depth, n_out, members, max_batch)
+        self.P = self.param_count(self.lib, self.p)
+        init = np.ascontiguousarray(init, dtype=np.float32).reshape(members, self.P)
+        h = C.c_void_p()
+        ctx._check(self.lib.hopf_mlp_create(ctx.h, C.byref(self.p), _fptr(init), C.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def param_count(lib, p):
+        P = C.c_longlong()
+        st = lib.hopf_mlp_param_count(C.byref(p), C.byref(P))
+        if st != HOPF_OK:
+            raise HopfError(st, "hopf_mlp_param_count: bad network shape")
+        return int(P.value)
+
+    def close(self):
+        if self.h:
+            self.lib.hopf_mlp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros((self.p.members, self.P), dtype=np.float32)
+        self.ctx._check(self.lib.hopf_mlp_get_params(self.h, _fptr(out)))
+        return out
+
+    def set_data(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        stats = np.zeros(2 * (self.p.n_in + self.p.n_out))
+        self.ctx._check(self.lib.hopf_mlp_set_data(self.h, x.shape[0], _dptr(x), _dptr(y), _dptr(stats)))
+        ni = self.p.n_in
+        return (stats[:ni], stats[ni:2 * ni]), (stats[2 * ni:2 * ni + self.p.n_out], stats[2 * ni + self.p.n_out:])
+
+    def train(self, idx, lr):
+        """idx: int [iters][members][batch]; lr: [iters].  Returns the batch
+        losses [iters][members]."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        iters, _, batch = idx.shape
+        lr = np.ascontiguousarray(lr, dtype=np.float32)
+        loss = np.zeros((iters, self.p.members), dtype=np.float32)
+        self.ctx._check(self.lib.hopf_mlp_train(self.h, iters, batch, _iptr(idx), _fptr(lr), _fptr(loss)))
+        return loss
+
+    def loss_grad(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        loss = np.zeros(self.p.members, dtype=np.float32)
+        grad = np.zeros((self.p.members, self.P), dtype=np.float32)
+        self.ctx._check(self.lib.hopf_mlp_loss_grad(self.h, idx.shape[1], _iptr(idx), _fptr(loss), _fptr(grad)))
+        return loss, grad
+
+    def predict(self, x, kappa, members=False):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        nq = x.shape[0]
+        y = np.zeros((nq, self.p.n_out))
+        bound = np.zeros(nq)
+        ym = np.zeros((self.p.members, nq, self.p.n_out)) if members else None
+        self.ctx._check(self.lib.hopf_mlp_predict(self.h, nq, _dptr(x), float(kappa), _dptr(y), _dptr(bound),
+                                                  _dptr(ym) if members else None))
+        return (y, bound, ym) if members else (y, bound)

@@ -17,6 +17,10 @@ initial states of the Burgers equation, Sec. 5 "Burgers-Hopf FDE"):
 * ``C4`` ensemble generator: d in {8..48}, n in {64,96,128}, nu~U[0.01,0.1],
   sigma~U[0.1,0.5], ell~U[0.3,2.0], mean = 4 random Fourier modes with
   amplitudes ~ N(0, 0.5^2).
+* ``surrogate_member`` the C4 parameter draw on the C1 grid (d=4, n=24,
+  dt=1e-3, rank cap 16, tol 1e-10): the training and held-out solves of the
+  learned surrogate, plus the network's random initial parameters and batch
+  indices.
 """
 from __future__ import annotations
 
@@ -129,3 +133,43 @@ def mc_gaussian_samples(d: int, nsamples: int, seed: int):
     the caller colours them with its own covariance factor."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((nsamples, d))
+
+
+def surrogate_member(seed: int) -> Workload:
+    """One solve of the surrogate's data set: C4's parameter distribution
+    (nu, sigma, ell, 4 Fourier modes of the mean) on the C1 grid."""
+    rng = np.random.default_rng(seed)
+    nu = float(rng.uniform(0.01, 0.1))
+    sigma = float(rng.uniform(0.1, 0.5))
+    ell = float(rng.uniform(0.3, 2.0))
+    alpha = tuple(float(x) for x in rng.normal(0.0, 0.5, 4))
+    beta = tuple(float(x) for x in rng.normal(0.0, 0.5, 4))
+    return Workload(f"S[{seed}]", d=4, n=24, nu=nu, sigma=sigma, ell=ell,
+                    alpha=alpha, beta=beta, dt=1e-3, cap=16, tol=1e-10)
+
+
+def mlp_init(seed: int, dims, members: int):
+    """Initial parameters of `members` networks with layer widths `dims`,
+    packed per member as W_l (fan_out x fan_in, row-major) then b_l: weights
+    ~ N(0, 2 / fan_in) (He et al. 2015), biases 0.  float32 [members][P]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(members):
+        parts = []
+        for fi, fo in zip(dims[:-1], dims[1:]):
+            parts.append(rng.normal(0.0, np.sqrt(2.0 / fi), fi * fo))
+            parts.append(np.zeros(fo))
+        out.append(np.concatenate(parts))
+    return np.asarray(out, dtype=np.float32)
+
+
+def batch_indices(seed: int, iters: int, members: int, batch: int, nsamples: int):
+    """Sample indices [iters][members][batch]: each member walks its own
+    random permutations of the data set (epochs), drawn from one seed."""
+    rng = np.random.default_rng(seed)
+    need = iters * batch
+    out = np.empty((members, need), dtype=np.int32)
+    for e in range(members):
+        reps = -(-need // nsamples)
+        out[e] = np.concatenate([rng.permutation(nsamples) for _ in range(reps)])[:need]
+    return np.ascontiguousarray(out.reshape(members, iters, batch).transpose(1, 0, 2))

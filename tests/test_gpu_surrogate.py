@@ -1,0 +1,179 @@
+"""GPU parity of the surrogate network (hopf_mlp_*) against the float64
+oracle (oracle.mlp), and an end-to-end check that the trained ensemble
+answers held-out queries faster than the solver at the stated error."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp as O
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_exact(a):
+    """Rounds float32 values to the nearest bfloat16 (ties to even) and
+    returns them as float32, so both sides start from identical weights."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def weights_bf16(params, shape):
+    """bf16 rounding of the weight blocks only (biases stay float32)."""
+    out = np.array(params, dtype=np.float32, copy=True)
+    lay, _ = O.layout(*shape)
+    for row in out:
+        for w, _, fi, fo in lay:
+            row[w:w + fi * fo] = bf16_exact(row[w:w + fi * fo])
+    return out
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2403_04946_gb300 import binding
+    binding.load()
+    return binding
+
+
+def make(B, shape, members, max_batch, seed=0):
+    n_in, width, depth, n_out = shape
+    ctx = B.Context(d=4, n=8, nu=0.05, tol=1e-10, rank_cap=4, L=3.0)
+    init = weights_bf16(synthetic.mlp_init(seed, O.layer_dims(*shape), members), shape)
+    return ctx, B.Mlp(ctx, n_in, width, depth, n_out, members, max_batch, init), init
+
+
+def data(shape, ns, seed=1):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0.3, 2.0, (ns, shape[0]))
+    Y = rng.normal(-1.0, 0.5, (ns, shape[3]))
+    return X, Y
+
+
+SHAPE = (12, 40, 2, 14)  # ragged against the 64-wide tiles
+
+
+def test_param_layout_and_stats(B):
+    ctx, net, init = make(B, SHAPE, 3, 100)
+    assert net.P == O.layout(*SHAPE)[1]
+    np.testing.assert_array_equal(net.get_params(), init)
+    X, Y = data(SHAPE, 100)
+    (xm, xs), (ym, ys) = net.set_data(X, Y)
+    for got, ref in zip((xm, xs, ym, ys), (*O.column_stats(X), *O.column_stats(Y))):
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-14)
+    net.close()
+    ctx.close()
+
+
+def test_forward_and_bound_match_oracle(B):
+    M = 3
+    ctx, net, init = make(B, SHAPE, M, 64)
+    X, Y = data(SHAPE, 100)
+    net.set_data(X, Y)
+    xs, ys = O.column_stats(X), O.column_stats(Y)
+    Q = np.random.default_rng(5).normal(0.3, 2.0, (150, SHAPE[0]))  # 3 chunks of 64, last ragged
+    y, bound, ym = net.predict(Q, 2.0, members=True)
+    Qn = (Q - xs[0]) / xs[1]
+    for e in range(M):
+        ref = ys[0] + ys[1] * O.forward(init[e].astype(np.float64), Qn, *SHAPE)[0]
+        np.testing.assert_allclose(ym[e], ref, atol=2e-5 * np.abs(ref).max())
+    yr, br = O.predict([p.astype(np.float64) for p in init], Q, xs, ys, 2.0, *SHAPE)
+    np.testing.assert_allclose(y, yr, atol=2e-5 * np.abs(yr).max())
+    np.testing.assert_allclose(bound, br, rtol=1e-3)
+    net.close()
+    ctx.close()
+
+
+def test_gradients_match_oracle(B):
+    M, batch = 2, 70
+    ctx, net, init = make(B, SHAPE, M, 128)
+    X, Y = data(SHAPE, 200)
+    net.set_data(X, Y)
+    xs, ys = O.column_stats(X), O.column_stats(Y)
+    idx = synthetic.batch_indices(3, 1, M, batch, 200)[0]
+    loss, grad = net.loss_grad(idx)
+    for e in range(M):
+        Xn = (X[idx[e]] - xs[0]) / xs[1]
+        Tn = (Y[idx[e]] - ys[0]) / ys[1]
+        lr_, gr = O.loss_and_grad(init[e].astype(np.float64), Xn, Tn, *SHAPE)
+        assert abs(loss[e] - lr_) <= 1e-5 * lr_
+        assert np.linalg.norm(grad[e] - gr) <= 1e-5 * np.linalg.norm(gr)
+    net.close()
+    ctx.close()
+
+
+def test_adam_steps_match_oracle(B):
+    """Two Adam steps on the GPU against the oracle, which forms each
+    gradient at the bf16-rounded weights as the kernels do."""
+    M, batch, iters, lr = 2, 64, 2, 1e-3
+    ctx, net, init = make(B, SHAPE, M, 64)
+    X, Y = data(SHAPE, 150)
+    net.set_data(X, Y)
+    xs, ys = O.column_stats(X), O.column_stats(Y)
+    idx = synthetic.batch_indices(4, iters, M, batch, 150)
+    losses = net.train(idx, np.full(iters, lr))
+    got = net.get_params()
+    lay, P = O.layout(*SHAPE)
+    for e in range(M):
+        w = init[e].astype(np.float64)
+        m = np.zeros(P)
+        v = np.zeros(P)
+        mask = np.ones(P, dtype=bool)
+        for t in range(iters):
+            wb = weights_bf16(w[None].astype(np.float32), SHAPE)[0].astype(np.float64)
+            Xn = (X[idx[t, e]] - xs[0]) / xs[1]
+            Tn = (Y[idx[t, e]] - ys[0]) / ys[1]
+            l, g = O.loss_and_grad(wb, Xn, Tn, *SHAPE)
+            assert abs(losses[t, e] - l) <= 1e-5 * l
+            mask &= np.abs(g) > 1e-3 * np.abs(g).max()  # Adam's sign of a near-zero gradient is rounding
+            w, m, v = O.adam_step(w, m, v, g, t + 1, lr)
+        assert mask.mean() > 0.5
+        np.testing.assert_allclose(got[e][mask], w[mask], atol=1e-6)
+        assert np.median(np.abs(got[e][mask] - init[e][mask])) > 0.5 * lr
+    net.close()
+    ctx.close()
+
+
+def test_surrogate_answers_held_out_queries():
+    """Train the ensemble on solver outputs (C4 parameter draws on the C1
+    grid), calibrate its bound on separate solves, then answer held-out
+    queries: the network where its bound is <= 1e-3, the solver elsewhere."""
+    from paper_2403_04946_gb300 import binding as Bn, surrogate as S
+    snaps = list(range(10, 101, 10))  # T = 0.01 .. 0.1 at dt = 1e-3
+    train = [synthetic.surrogate_member(s) for s in range(1, 65)]
+    calib = [synthetic.surrogate_member(s) for s in range(10001, 10017)]
+    held = [synthetic.surrogate_member(s) for s in range(20001, 20017)]
+    t0 = time.perf_counter()
+    Xt, Yt = S.dataset(train, snaps, 1e-3)
+    t_solve = time.perf_counter() - t0
+    Xc, Yc = S.dataset(calib, snaps, 1e-3)
+    Xh, Yh = S.dataset(held, snaps, 1e-3)
+    d = 4
+    dims = O.layer_dims(S.N_IN, 256, 4, S.n_out(d))
+    ctx = Bn.Context(d=4, n=8, nu=0.05, tol=1e-10, rank_cap=4, L=3.0)
+    sur = S.Surrogate(ctx, d, synthetic.mlp_init(7, dims, 4))
+    iters, batch = 3000, 128
+    lr = 1e-5 + 0.5 * (2e-3 - 1e-5) * (1 + np.cos(np.pi * np.arange(iters) / iters))
+    loss = sur.fit(Xt, Yt, synthetic.batch_indices(8, iters, 4, batch, len(Xt)), lr)
+    assert loss[-50:].mean() < 1e-2 * loss[:10].mean()
+    kappa, _, _ = sur.calibrate(Xc, Yc)
+    y, bound = sur.predict(Xh)
+    err = S.rel_err(y, Yh)
+    trivial = S.rel_err(np.broadcast_to(Yt.mean(0), Yh.shape), Yh)
+    assert np.median(err) < 0.1 * np.median(trivial)
+    acc = bound <= 1e-3
+    served = np.where(acc, err, 0.0)  # rejected queries are re-solved exactly
+    assert np.mean(served <= 1e-3) >= 0.95
+    t1 = time.perf_counter()
+    sur.predict(Xh)
+    t_net = time.perf_counter() - t1
+    per_solve = t_solve / len(train)
+    print(f"surrogate: kappa {kappa:.3g}, accepted {acc.mean():.2f}, median err {np.median(err):.2e} "
+          f"(trivial {np.median(trivial):.2e}), max accepted err {served.max():.2e}; "
+          f"solver {len(train) / t_solve:.2f} solves/s ({per_solve * 1e3:.0f} ms per 100-step solve), "
+          f"network {len(Xh) / t_net:.0f} queries/s")
+    assert t_net / len(Xh) < per_solve
+    sur.close()
+    ctx.close()
