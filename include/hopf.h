@@ -319,12 +319,19 @@ hopf_status hopf_mlp_train(hopf_mlp* m, int iters, int batch, const int* idx,
  * grad: host [members][P] (FP32). */
 hopf_status hopf_mlp_loss_grad(hopf_mlp* m, int batch, const int* idx,
                                float* loss, float* grad);
-/* Ensemble prediction for nq queries x (host [nq][n_in]): y host
- * [nq][n_out] (the member mean, physical units), bound host [nq],
- * members_y (may be NULL) host [members][nq][n_out].  Errors: HOPF_EINVAL
- * (no statistics yet, nq < 0). */
-hopf_status hopf_mlp_predict(hopf_mlp* m, int nq, const double* x, double kappa,
-                             double* y, double* bound, double* members_y);
+/* Ensemble prediction for nq queries x (host [nq][n_in]).  Member m
+ * answers y_m = base + scale * (mu_y + sd_y * net_m(x_hat)), with base
+ * (host [nq][n_out], may be NULL: 0) and scale (host [nq], may be NULL: 1)
+ * per query, so that a network trained on a rate or an increment answers in
+ * the units of the full quantity.  y: host [nq][n_out], the member mean;
+ * bound: host [nq], kappa ||s||_2 / ||y||_2 with s the per-output standard
+ * deviation of y_m over the members; members_y (may be NULL): host
+ * [members][nq][n_out].  Errors: HOPF_EINVAL (no statistics yet, nq < 0,
+ * kappa < 0). */
+hopf_status hopf_mlp_predict(hopf_mlp* m, int nq, const double* x,
+                             const double* base, const double* scale,
+                             double kappa, double* y, double* bound,
+                             double* members_y);
 void hopf_mlp_free(hopf_mlp* m);
 
 /* ---- instrumentation ----------------------------------------------------- */

@@ -118,14 +118,18 @@ def column_stats(A):
     return mu, np.where(sd > 0, sd, 1.0)
 
 
-def predict(ensemble, X, xstats, ystats, kappa, n_in, width, depth, n_out):
+def predict(ensemble, X, xstats, ystats, kappa, n_in, width, depth, n_out, base=None, scale=None):
     """Ensemble prediction in physical units and its error bound.
 
-    y_m = mu_y + s_y * net_m((x - mu_x) / s_x); the answer is the member mean
-    ybar and the bound is kappa * ||spread||_2 / ||ybar||_2 with spread the
-    per-output standard deviation over members."""
+    Member m answers y_m = base + scale (mu_y + s_y net_m((x - mu_x) / s_x))
+    (base 0 and scale 1 when absent); the answer is the member mean ybar and
+    the bound is kappa ||spread||_2 / ||ybar||_2 with spread the per-output
+    standard deviation over members."""
     Xn = (np.asarray(X, dtype=float) - xstats[0]) / xstats[1]
-    Ys = np.stack([ystats[0] + ystats[1] * forward(p, Xn, n_in, width, depth, n_out)[0] for p in ensemble])
+    b0 = 0.0 if base is None else np.asarray(base, dtype=float)
+    sc = 1.0 if scale is None else np.asarray(scale, dtype=float)[:, None]
+    Ys = np.stack([b0 + sc * (ystats[0] + ystats[1] * forward(p, Xn, n_in, width, depth, n_out)[0])
+                   for p in ensemble])
     ybar = Ys.mean(axis=0)
     spread = np.sqrt(((Ys - ybar) ** 2).mean(axis=0))
     bound = kappa * np.linalg.norm(spread, axis=1) / np.linalg.norm(ybar, axis=1)

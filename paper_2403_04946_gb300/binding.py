@@ -63,7 +63,7 @@ SIGNATURES = {
     "hopf_mlp_set_data": (_i, [_vp, _i, _pd, _pd, _pd]),
     "hopf_mlp_train": (_i, [_vp, _i, _i, _pi, _vp, _vp]),
     "hopf_mlp_loss_grad": (_i, [_vp, _i, _pi, _vp, _vp]),
-    "hopf_mlp_predict": (_i, [_vp, _i, _pd, _d, _pd, _pd, _pd]),
+    "hopf_mlp_predict": (_i, [_vp, _i, _pd, _pd, _pd, _d, _pd, _pd, _pd]),
     "hopf_mlp_free": (None, [_vp]),
 }
 
@@ -415,12 +415,15 @@ class Mlp:
         self.ctx._check(self.lib.hopf_mlp_loss_grad(self.h, idx.shape[1], _iptr(idx), _fptr(loss), _fptr(grad)))
         return loss, grad
 
-    def predict(self, x, kappa, members=False):
+    def predict(self, x, kappa, base=None, scale=None, members=False):
         x = np.ascontiguousarray(x, dtype=np.float64)
         nq = x.shape[0]
+        bs = None if base is None else np.ascontiguousarray(base, dtype=np.float64).reshape(nq, self.p.n_out)
+        sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64).reshape(nq)
         y = np.zeros((nq, self.p.n_out))
         bound = np.zeros(nq)
         ym = np.zeros((self.p.members, nq, self.p.n_out)) if members else None
-        self.ctx._check(self.lib.hopf_mlp_predict(self.h, nq, _dptr(x), float(kappa), _dptr(y), _dptr(bound),
-                                                  _dptr(ym) if members else None))
+        self.ctx._check(self.lib.hopf_mlp_predict(
+            self.h, nq, _dptr(x), None if bs is None else _dptr(bs), None if sc is None else _dptr(sc),
+            float(kappa), _dptr(y), _dptr(bound), _dptr(ym) if members else None))
         return (y, bound, ym) if members else (y, bound)

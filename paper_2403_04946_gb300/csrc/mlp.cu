@@ -268,25 +268,30 @@ __global__ void normalize_kernel(const double* x, int nq, int n_in, const double
   }
 }
 
-// Member mean in physical units and the ensemble error bound per query.
+// Per query b: each member's answer in physical units,
+// y_m = base + scale (mu + sd net_m) (base 0 and scale 1 when absent), the
+// member mean ybar and the error bound kappa ||s||_2 / ||ybar||_2, s the
+// per-output standard deviation of y_m over the members.
 __global__ void ensemble_kernel(const float* Y, long long yme, int members, int nq, int n_out,
-                                const double* ystats, double kappa, double* yout, double* bound,
-                                double* ymem) {
+                                const double* ystats, const double* base, const double* scale, double kappa,
+                                double* yout, double* bound, double* ymem) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nq) return;
   const double *mu = ystats, *sd = ystats + n_out;
+  const double sc = scale ? scale[b] : 1.0;
   double yy = 0.0, ss = 0.0;
   for (int o = 0; o < n_out; ++o) {
+    const double b0 = base ? base[(long long)b * n_out + o] : 0.0;
     double s1 = 0.0;
     for (int e = 0; e < members; ++e) {
-      const double v = mu[o] + sd[o] * (double)Y[e * yme + (long long)b * n_out + o];
+      const double v = b0 + sc * (mu[o] + sd[o] * (double)Y[e * yme + (long long)b * n_out + o]);
       s1 += v;
       if (ymem) ymem[((long long)e * nq + b) * n_out + o] = v;
     }
     const double ybar = s1 / members;
     double s2 = 0.0;
     for (int e = 0; e < members; ++e) {
-      const double r = mu[o] + sd[o] * (double)Y[e * yme + (long long)b * n_out + o] - ybar;
+      const double r = b0 + sc * (mu[o] + sd[o] * (double)Y[e * yme + (long long)b * n_out + o]) - ybar;
       s2 += r * r;
     }
     yout[(long long)b * n_out + o] = ybar;
@@ -325,7 +330,7 @@ struct hopf_mlp {
   long long idx_cap = 0;
   float *lr = nullptr, *loss = nullptr;
   long long it_cap = 0;
-  double *qx = nullptr, *qy = nullptr, *qb = nullptr, *qm = nullptr;
+  double *qx = nullptr, *qy = nullptr, *qb = nullptr, *qm = nullptr, *qbase = nullptr, *qscale = nullptr;
   std::vector<void*> allocs;
 };
 
@@ -596,6 +601,8 @@ hopf_status hopf_mlp_create(hopf_ctx* ctx, const hopf_mlp_params* p, const float
     if (e == cudaSuccess) e = malloc_track(mm, &mm->qy, (size_t)mb * p->n_out);
     if (e == cudaSuccess) e = malloc_track(mm, &mm->qb, (size_t)mb);
     if (e == cudaSuccess) e = malloc_track(mm, &mm->qm, (size_t)M * mb * p->n_out);
+    if (e == cudaSuccess) e = malloc_track(mm, &mm->qbase, (size_t)mb * p->n_out);
+    if (e == cudaSuccess) e = malloc_track(mm, &mm->qscale, (size_t)mb);
     if (e == cudaSuccess) e = join_ctx(mm);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mm->w, init, tot * sizeof(float), cudaMemcpyHostToDevice, mm->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mm->m, 0, tot * sizeof(float), mm->s);
@@ -766,8 +773,8 @@ hopf_status hopf_mlp_loss_grad(hopf_mlp* mm, int batch, const int* idx, float* l
   return HOPF_OK;
 }
 
-hopf_status hopf_mlp_predict(hopf_mlp* mm, int nq, const double* x, double kappa, double* y, double* bound,
-                             double* members_y) {
+hopf_status hopf_mlp_predict(hopf_mlp* mm, int nq, const double* x, const double* base, const double* scale,
+                             double kappa, double* y, double* bound, double* members_y) {
   if (!mm) return HOPF_EINVAL;
   if (!mm->have_stats) return mfail(mm, HOPF_EINVAL, "hopf_mlp_predict: no normalisation statistics");
   if (nq < 0 || (nq > 0 && (!x || !y || !bound)) || !(kappa >= 0.0))
@@ -780,13 +787,18 @@ hopf_status hopf_mlp_predict(hopf_mlp* mm, int nq, const double* x, double kappa
     const int c = std::min(mb, nq - q0);
     MCK(cudaMemcpyAsync(mm->qx, x + (size_t)q0 * n_in, (size_t)c * n_in * sizeof(double), cudaMemcpyHostToDevice,
                         mm->s));
+    if (base)
+      MCK(cudaMemcpyAsync(mm->qbase, base + (size_t)q0 * n_out, (size_t)c * n_out * sizeof(double),
+                          cudaMemcpyHostToDevice, mm->s));
+    if (scale)
+      MCK(cudaMemcpyAsync(mm->qscale, scale + q0, (size_t)c * sizeof(double), cudaMemcpyHostToDevice, mm->s));
     normalize_kernel<<<blocks_for((long long)c * n_in, 256), 256, 0, mm->s>>>(mm->qx, c, n_in, mm->stats,
                                                                                mm->X[0]);
     MCK(cudaGetLastError());
     MCK(forward(mm, c, true));
     ensemble_kernel<<<blocks_for(c, 128, 1 << 20), 128, 0, mm->s>>>(
-        mm->Z[mm->L - 1], (long long)mb * n_out, M, c, n_out, mm->stats + 2 * n_in, kappa, mm->qy, mm->qb,
-        members_y ? mm->qm : nullptr);
+        mm->Z[mm->L - 1], (long long)mb * n_out, M, c, n_out, mm->stats + 2 * n_in, base ? mm->qbase : nullptr,
+        scale ? mm->qscale : nullptr, kappa, mm->qy, mm->qb, members_y ? mm->qm : nullptr);
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(y + (size_t)q0 * n_out, mm->qy, (size_t)c * n_out * sizeof(double), cudaMemcpyDeviceToHost,
                         mm->s));

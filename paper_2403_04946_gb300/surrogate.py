@@ -5,10 +5,17 @@ Orchestration only: the solves run through the library's hopf_* calls, the
 network's training and inference through its hopf_mlp_* calls (every
 arithmetic step a CUDA kernel); this module moves arrays between them.
 
-Inputs (12): nu, sigma, ell, the cos/sin amplitudes of Fourier modes 1..4
-of the initial mean, and T.  Outputs (d + d(d+1)/2): the d means and the
-upper triangle (row by row, j <= k) of the covariance, as the solver's
+Parameters (12): nu, sigma, ell, the cos/sin amplitudes of Fourier modes
+1..4 of the initial mean, and T.  Moments y (d + d(d+1)/2): the d means and
+the upper triangle (row by row, j <= k) of the covariance, as the solver's
 hopf_eval_moments returns them after T / dt RK4 steps.
+
+Residual form.  The solver's own moments at T = 0, y0 (hopf_init_gaussian
+then hopf_eval_moments, no time step), are cheap and exact; the network
+gets the 12 parameters and y0 as inputs and learns the mean rate
+(y(T) - y0) / T, so that y = y0 + T net(params, y0).  The increment over the
+horizon is a few percent of y, so a network that gets the rate to a few
+percent answers y to about 1e-3.
 
 The solver is the fallback and the judge: a query is answered by the
 network only when the ensemble's error bound is at most `tol`; every other
@@ -23,14 +30,18 @@ import numpy as np
 
 from . import binding as B
 
-N_IN = 12
+N_PARAMS = 12
 
 
-def features(w, T):
-    """The 12 network inputs of workload `w` at horizon T."""
+def params(w, T):
+    """The 12 parameters of workload `w` at horizon T."""
     a = list(w.alpha) + [0.0] * (4 - len(w.alpha))
     b = list(w.beta) + [0.0] * (4 - len(w.beta))
     return np.array([w.nu, w.sigma, w.ell, *a[:4], *b[:4], T], dtype=np.float64)
+
+
+def n_in(d):
+    return N_PARAMS + n_out(d)
 
 
 def n_out(d):
@@ -91,11 +102,25 @@ def solve(members, snapshots, concurrency=16):
     return out
 
 
-def dataset(members, snapshots, dt, **kw):
-    """(X, Y) pairs for every (member, snapshot) of a solve batch."""
-    Y = solve(members, snapshots, **kw)
-    X = np.array([features(w, s * dt) for w in members for s in snapshots])
-    return X, Y.reshape(len(members) * len(snapshots), -1)
+def dataset(members, snapshots, **kw):
+    """Training pairs from one batch of solves: inputs [params(T), y0] and
+    targets (y(T) - y0) / T for every member and every snapshot > 0, plus
+    the moments themselves (y0 per pair and y(T)) for evaluation."""
+    steps = sorted(set([0] + [int(s) for s in snapshots]))
+    Y = solve(members, steps, **kw)
+    X, R, Y0, YT, T = [], [], [], [], []
+    for i, w in enumerate(members):
+        y0 = Y[i, 0]
+        for j, s in enumerate(steps):
+            if s == 0:
+                continue
+            t = s * w.dt
+            X.append(np.concatenate([params(w, t), y0]))
+            R.append((Y[i, j] - y0) / t)
+            Y0.append(y0)
+            YT.append(Y[i, j])
+            T.append(t)
+    return np.array(X), np.array(R), np.array(Y0), np.array(YT), np.array(T)
 
 
 def rel_err(pred, ref):
@@ -103,45 +128,50 @@ def rel_err(pred, ref):
 
 
 class Surrogate:
-    """An ensemble of `members` networks N_IN -> width x depth -> n_out."""
+    """An ensemble of `members` networks (12 + n_out) -> width x depth ->
+    n_out on the rate (y(T) - y0) / T."""
 
     def __init__(self, ctx, d, init, width=256, depth=4, members=4, max_batch=4096):
         self.d = d
-        self.net = B.Mlp(ctx, N_IN, width, depth, n_out(d), members, max_batch, init)
+        self.net = B.Mlp(ctx, n_in(d), width, depth, n_out(d), members, max_batch, init)
         self.kappa = None
 
-    def fit(self, X, Y, idx, lr):
-        self.net.set_data(X, Y)
+    def fit(self, X, R, idx, lr):
+        self.net.set_data(X, R)
         return self.net.train(idx, lr)
 
-    def calibrate(self, X, Y):
+    def predict(self, X, Y0, T, kappa=None):
+        """y = y0 + T net(x) and its error bound."""
+        k = self.kappa if kappa is None else kappa
+        return self.net.predict(X, k, base=Y0, scale=T)
+
+    def calibrate(self, X, Y0, T, YT):
         """kappa = the smallest scale for which the bound covers every
         calibration error: max_i err_i / raw_bound_i."""
-        y, raw = self.net.predict(X, 1.0)
-        err = rel_err(y, Y)
+        y, raw = self.predict(X, Y0, T, kappa=1.0)
+        err = rel_err(y, YT)
         self.kappa = float(np.max(err / np.maximum(raw, 1e-300)))
         return self.kappa, err, raw
 
-    def predict(self, X):
-        return self.net.predict(X, self.kappa)
-
-    def answer(self, members, T_steps, tol, solver_kw=None):
-        """Answers the queries (member i at T_steps[i] steps): the network
-        where its bound <= tol, the solver elsewhere.  Returns (Y, accepted,
-        seconds in the network, seconds in the solver)."""
-        dt = members[0].dt
-        X = np.array([features(w, s * dt) for w, s in zip(members, T_steps)])
+    def answer(self, members, steps, tol, concurrency=8):
+        """Answers the queries (member i after steps[i] RK4 steps): the
+        network where its bound <= tol, the solver elsewhere.  Returns
+        (y, accepted, seconds for y0, seconds in the network, seconds in
+        the fallback solves)."""
         t0 = time.perf_counter()
-        Y, bound = self.predict(X)
+        y0 = solve(members, [0], concurrency=concurrency)[:, 0]
         t1 = time.perf_counter()
+        T = np.array([s * w.dt for w, s in zip(members, steps)])
+        X = np.array([np.concatenate([params(w, t), y]) for w, t, y in zip(members, T, y0)])
+        y, bound = self.predict(X, y0, T)
+        t2 = time.perf_counter()
         acc = bound <= tol
         rej = np.flatnonzero(~acc)
-        if rej.size:
-            for s in sorted(set(int(T_steps[i]) for i in rej)):
-                sel = [i for i in rej if int(T_steps[i]) == s]
-                Y[sel] = solve([members[i] for i in sel], [s], **(solver_kw or {}))[:, 0]
-        t2 = time.perf_counter()
-        return Y, acc, t1 - t0, t2 - t1
+        for s in sorted(set(int(steps[i]) for i in rej)):
+            sel = [i for i in rej if int(steps[i]) == s]
+            y[sel] = solve([members[i] for i in sel], [s], concurrency=concurrency)[:, 0]
+        t3 = time.perf_counter()
+        return y, acc, t1 - t0, t2 - t1, t3 - t2
 
     def close(self):
         self.net.close()

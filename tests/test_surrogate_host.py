@@ -11,8 +11,8 @@ from oracle import mlp as O
 def test_features_and_packing():
     from paper_2403_04946_gb300 import surrogate as S
     w = synthetic.surrogate_member(3)
-    x = S.features(w, 0.05)
-    assert x.shape == (S.N_IN,)
+    x = S.params(w, 0.05)
+    assert x.shape == (S.N_PARAMS,)
     np.testing.assert_array_equal(x[:3], [w.nu, w.sigma, w.ell])
     np.testing.assert_array_equal(x[3:7], w.alpha)
     np.testing.assert_array_equal(x[7:11], w.beta)
