@@ -302,6 +302,66 @@ def ensemble_rate(stream_int, nsteps=1):
             "speedup": out["concurrent"] / out["sequential"]}
 
 
+def surrogate_rate(ntrain=64, ncalib=12, nheld=24, iters=3000, batch=128):
+    """The learned surrogate on the C4 parameter distribution at the C1 grid
+    (d=4, n=24, dt=1e-2, T = 0.01..0.1): solver-made training data, GPU
+    training of the 4-member ensemble, calibration of its bound on separate
+    solves, then held-out queries answered with the solver as fallback
+    (bound <= 1e-3), timed against the solver alone on the same queries."""
+    import numpy as np
+    from paper_2403_04946_gb300 import binding as B, surrogate as S
+    import synthetic
+    d, width, depth, members, tol = 4, 256, 4, 4, 1e-3
+    snaps = list(range(1, 11))
+    train = [synthetic.surrogate_member(s) for s in range(1, 1 + ntrain)]
+    calib = [synthetic.surrogate_member(s) for s in range(10001, 10001 + ncalib)]
+    held = [synthetic.surrogate_member(s) for s in range(20001, 20001 + nheld)]
+    t0 = time.perf_counter()
+    Xt, Rt, _, _, _ = S.dataset(train, snaps, concurrency=8)
+    t_data = time.perf_counter() - t0
+    Xc, _, Y0c, YTc, Tc = S.dataset(calib, snaps, concurrency=8)
+    dims = [S.n_in(d)] + [width] * depth + [S.n_out(d)]
+    ctx = B.Context(d=4, n=8, nu=0.05, tol=1e-10, rank_cap=4, L=3.0)
+    sur = S.Surrogate(ctx, d, synthetic.mlp_init(7, dims, members), width=width, depth=depth, members=members)
+    lr = 1e-5 + 0.5 * (1e-3 - 1e-5) * (1 + np.cos(np.pi * np.arange(iters) / iters))
+    t0 = time.perf_counter()
+    loss = sur.fit(Xt, Rt, synthetic.batch_indices(8, iters, members, batch, len(Xt)), lr)
+    t_train = time.perf_counter() - t0
+    kappa, _, _ = sur.calibrate(Xc, Y0c, Tc, YTc)
+    steps = [snaps[i % len(snaps)] for i in range(nheld)]
+    t0 = time.perf_counter()
+    ref = np.concatenate([S.solve([held[i] for i in range(nheld) if steps[i] == s], [s], concurrency=8)[:, 0]
+                          for s in sorted(set(steps))])
+    t_solver = time.perf_counter() - t0
+    order = np.concatenate([[i for i in range(nheld) if steps[i] == s] for s in sorted(set(steps))]).astype(int)
+    y_ref = np.empty_like(ref)
+    y_ref[order] = ref
+    ans = sur.answer(held, steps, tol)
+    err_served = S.rel_err(ans["y"], y_ref)
+    err_net = S.rel_err(ans["y_net"], y_ref)
+    # network throughput alone on a large query batch (inputs on the host)
+    reps = -(-4096 // len(Xc))
+    Xq, Y0q, Tq = (np.repeat(a, reps, axis=0)[:4096] for a in (Xc, Y0c, Tc))
+    sur.predict(Xq, Y0q, Tq)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        sur.predict(Xq, Y0q, Tq)
+    t_q = (time.perf_counter() - t0) / 5
+    sur.close()
+    ctx.close()
+    t_answer = ans["t_y0"] + ans["t_net"] + ans["t_fallback"]
+    return {"config": "d=4, n=24, rank cap 16, tol 1e-10, dt 1e-2, T in 0.01..0.1; C4 parameter draws; "
+                      f"MLP {dims[0]}->{width}x{depth}->{dims[-1]} GELU, {members} members, bf16 weights",
+            "train_solves": ntrain, "train_pairs": int(len(Xt)), "data_s": round(t_data, 2),
+            "train_steps": iters, "train_s": round(t_train, 2),
+            "loss_first_last": [float(loss[:10].mean()), float(loss[-50:].mean())],
+            "kappa": kappa, "held_out_queries": nheld, "accepted": float(ans["accepted"].mean()),
+            "median_err_network": float(np.median(err_net)), "max_err_served": float(err_served.max()),
+            "solver_queries_per_s": nheld / t_solver, "answer_queries_per_s": nheld / t_answer,
+            "gain_vs_solver": t_solver / t_answer,
+            "network_queries_per_s": 4096 / t_q}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -379,6 +439,7 @@ def run_ours(args, rank, world, local_rank):
 
     err = natural_state_error(w, stream.cuda_stream) if not args.no_error_check else None
     ens = ensemble_rate(stream.cuda_stream) if not args.no_error_check else None
+    sur = surrogate_rate() if (world == 1 and not args.no_surrogate) else None
 
     result = None
     if rank == 0:
@@ -408,6 +469,7 @@ def run_ours(args, rank, world, local_rank):
                      "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},
             "mixed_vs_fp64_error": err,
             "ensemble": ens,
+            "surrogate": sur,
             "apply_gbs": apply_gbs,
             "jacobi_sweeps_per_svd": prof["svd"].get("sweeps", 0) / max(1, prof["svd"].get("count", 0)),
             "cpu_baseline": cpu,
@@ -427,6 +489,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -155,23 +155,26 @@ class Surrogate:
 
     def answer(self, members, steps, tol, concurrency=8):
         """Answers the queries (member i after steps[i] RK4 steps): the
-        network where its bound <= tol, the solver elsewhere.  Returns
-        (y, accepted, seconds for y0, seconds in the network, seconds in
-        the fallback solves)."""
+        network where its bound <= tol, the solver elsewhere.  Returns a
+        dict: y (the answers), accepted, y_net and bound (the network's own
+        answers and bounds), and the seconds spent on y0, in the network and
+        in the fallback solves."""
         t0 = time.perf_counter()
         y0 = solve(members, [0], concurrency=concurrency)[:, 0]
         t1 = time.perf_counter()
         T = np.array([s * w.dt for w, s in zip(members, steps)])
         X = np.array([np.concatenate([params(w, t), y]) for w, t, y in zip(members, T, y0)])
-        y, bound = self.predict(X, y0, T)
+        y_net, bound = self.predict(X, y0, T)
         t2 = time.perf_counter()
+        y = y_net.copy()
         acc = bound <= tol
         rej = np.flatnonzero(~acc)
         for s in sorted(set(int(steps[i]) for i in rej)):
             sel = [i for i in rej if int(steps[i]) == s]
             y[sel] = solve([members[i] for i in sel], [s], concurrency=concurrency)[:, 0]
         t3 = time.perf_counter()
-        return y, acc, t1 - t0, t2 - t1, t3 - t2
+        return {"y": y, "accepted": acc, "y_net": y_net, "bound": bound,
+                "t_y0": t1 - t0, "t_net": t2 - t1, "t_fallback": t3 - t2}
 
     def close(self):
         self.net.close()
