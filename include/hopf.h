@@ -86,9 +86,13 @@ hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out);
 void hopf_destroy(hopf_ctx* ctx);
 /* Message of the last failed call on ctx ("" if none).  Owned by ctx. */
 const char* hopf_last_error(const hopf_ctx* ctx);
-/* Sets / reads the a-box half-width L (must be > 0). */
+/* Sets / reads the a-box half-width L (> 0; 0 leaves it unset, so that the
+ * next hopf_init_gaussian picks it from its covariance). */
 hopf_status hopf_set_L(hopf_ctx* ctx, double L);
 hopf_status hopf_get_L(const hopf_ctx* ctx, double* L);
+/* Changes the viscosity nu (>= 0) of the generator, so that one context
+ * (and its workspaces) serves a sequence of solves with different nu. */
+hopf_status hopf_set_nu(hopf_ctx* ctx, double nu);
 /* Method of the small SVDs of the truncation (App. A, Alg. 4: the SVD of
  * the triangular factor R of each bond).  HOPF_SVD_AUTO (the default):
  * square factors through Householder bidiagonalisation, Sturm bisection

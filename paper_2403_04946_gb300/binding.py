@@ -34,6 +34,7 @@ SIGNATURES = {
     "hopf_last_error": (C.c_char_p, [_vp]),
     "hopf_set_L": (_i, [_vp, _d]),
     "hopf_get_L": (_i, [_vp, _pd]),
+    "hopf_set_nu": (_i, [_vp, _d]),
     "hopf_set_svd_method": (_i, [_vp, _i]),
     "hopf_set_max_ctas": (_i, [_vp, _i]),
     "hopf_step_ensemble": (_i, [_i, _vp, _vp, _vp, _i, _vp]),
@@ -181,6 +182,10 @@ class Context:
     # -- calls ----------------------------------------------------------------
     def hopf_set_L(self, L):
         self._check(self.lib.hopf_set_L(self.h, float(L)))
+
+    def hopf_set_nu(self, nu):
+        self._check(self.lib.hopf_set_nu(self.h, float(nu)))
+        self.nu = float(nu)
 
     def hopf_set_max_ctas(self, max_ctas):
         self._check(self.lib.hopf_set_max_ctas(self.h, int(max_ctas)))

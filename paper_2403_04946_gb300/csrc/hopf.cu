@@ -1024,9 +1024,16 @@ const char* hopf_last_error(const hopf_ctx* ctx) { return ctx ? ctx->err.c_str()
 
 hopf_status hopf_set_L(hopf_ctx* ctx, double L) {
   if (!ctx) return HOPF_EINVAL;
-  if (!(L > 0.0) || !std::isfinite(L)) return fail(ctx, HOPF_EINVAL, "L must be positive");
+  if (!(L >= 0.0) || !std::isfinite(L)) return fail(ctx, HOPF_EINVAL, "L must be positive (or 0: unset)");
   ctx->L = L;
-  return build_ops(ctx);
+  return L > 0.0 ? build_ops(ctx) : HOPF_OK;
+}
+
+hopf_status hopf_set_nu(hopf_ctx* ctx, double nu) {
+  if (!ctx) return HOPF_EINVAL;
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(ctx, HOPF_EINVAL, "nu must be >= 0");
+  ctx->p.nu = nu;
+  return ctx->L > 0.0 ? build_ops(ctx) : HOPF_OK;
 }
 
 hopf_status hopf_set_max_ctas(hopf_ctx* ctx, int max_ctas) {

@@ -55,50 +55,54 @@ def pack_moments(mean, cov):
 
 
 def solve(members, snapshots, concurrency=16):
-    """Solves every workload in `members` (same d, n, dt) and returns the
-    packed moments at each snapshot step count: array
+    """Solves every workload in `members` (same d, n, tol, rank cap) and
+    returns the packed moments at each snapshot step count: array
     [len(members)][len(snapshots)][n_out].  Up to `concurrency` solves run
     at once (hopf_step_ensemble), each on its own stream and on an equal
-    share of the SMs."""
+    share of the SMs; one context per slot is reused from solve to solve
+    (nu and L are reset per solve, the workspaces stay)."""
     import torch  # device streams
 
     if not members:
         return np.zeros((0, len(snapshots), 0))
-    d, n = members[0].d, members[0].n
+    w0_ = members[0]
+    d, n = w0_.d, w0_.n
     out = np.zeros((len(members), len(snapshots), n_out(d)))
     concurrency = max(1, min(concurrency, len(members)))
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     share = max(1, sms // concurrency)
     streams = [torch.cuda.Stream() for _ in range(concurrency)]
-    helper = B.Context(d=d, n=n, nu=0.05, tol=1e-10, rank_cap=4, L=1.0, stream=streams[0].cuda_stream)
+    ctxs = []
     try:
+        for st in streams:
+            ctxs.append(B.Context(d=d, n=n, nu=w0_.nu, tol=w0_.tol, rank_cap=w0_.cap, L=0.0,
+                                  stream=st.cuda_stream))
+            if concurrency > 1:
+                ctxs[-1].hopf_set_max_ctas(share)
         for w0 in range(0, len(members), concurrency):
             wave = members[w0:w0 + concurrency]
-            ctxs, tts = [], []
+            tts = []
             try:
-                for i, w in enumerate(wave):
-                    m0, C0 = helper.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
-                    ctx = B.Context(d=d, n=n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=0.0,
-                                    stream=streams[i].cuda_stream)
-                    if len(wave) > 1:
-                        ctx.hopf_set_max_ctas(share)
-                    ctxs.append(ctx)
+                for ctx, w in zip(ctxs, wave):
+                    m0, C0 = ctx.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
+                    ctx.hopf_set_L(0.0)
+                    ctx.hopf_set_nu(w.nu)
                     tts.append(ctx.hopf_init_gaussian(m0, C0))
+                live = list(zip(ctxs, tts))
                 done = 0
                 for j, s in enumerate(snapshots):
                     if s > done:
-                        B.hopf_step_ensemble(list(zip(ctxs, tts)), [w.dt for w in wave], s - done)
+                        B.hopf_step_ensemble(live, [w.dt for w in wave], s - done)
                         done = s
-                    for i, (ctx, t) in enumerate(zip(ctxs, tts)):
+                    for i, (ctx, t) in enumerate(live):
                         mean, cov, _ = ctx.hopf_eval_moments(t)
                         out[w0 + i, j] = pack_moments(mean, cov)
             finally:
                 for ctx, t in zip(ctxs, tts):
                     ctx.tt_free(t)
-                for ctx in ctxs:
-                    ctx.close()
     finally:
-        helper.close()
+        for ctx in ctxs:
+            ctx.close()
     return out
 
 

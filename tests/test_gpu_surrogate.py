@@ -142,6 +142,16 @@ def test_adam_steps_match_oracle(B):
     ctx.close()
 
 
+def test_context_reuse_matches_fresh_contexts():
+    """solve() reuses one context per slot (hopf_set_nu, hopf_set_L(0)):
+    the moments equal those of a fresh context per solve."""
+    from paper_2403_04946_gb300 import surrogate as S
+    members = [synthetic.surrogate_member(s) for s in (31, 32, 33)]
+    reused = S.solve(members, [0, 3], concurrency=1)
+    fresh = np.stack([S.solve([w], [0, 3], concurrency=1)[0] for w in members])
+    np.testing.assert_allclose(reused, fresh, rtol=1e-12, atol=1e-14)
+
+
 def test_surrogate_answers_held_out_queries():
     """Train the ensemble on solver outputs (C4 parameter draws on the C1
     grid), calibrate its bound on separate solves, then answer held-out
