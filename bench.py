@@ -302,7 +302,7 @@ def ensemble_rate(stream_int, nsteps=1):
             "speedup": out["concurrent"] / out["sequential"]}
 
 
-def surrogate_rate(ntrain=64, ncalib=12, nheld=24, iters=3000, batch=128):
+def surrogate_rate(ntrain=128, ncalib=16, nheld=24, iters=3000, batch=128):
     """The learned surrogate on the C4 parameter distribution at the C1 grid
     (d=4, n=24, dt=1e-2, T = 0.01..0.1): solver-made training data, GPU
     training of the 4-member ensemble, calibration of its bound on separate

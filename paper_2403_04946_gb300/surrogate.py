@@ -25,6 +25,7 @@ so that it covers every calibration error.
 from __future__ import annotations
 
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -73,6 +74,7 @@ def solve(members, snapshots, concurrency=16):
     share = max(1, sms // concurrency)
     streams = [torch.cuda.Stream() for _ in range(concurrency)]
     ctxs = []
+    pool = ThreadPoolExecutor(max_workers=concurrency)
     try:
         for st in streams:
             ctxs.append(B.Context(d=d, n=n, nu=w0_.nu, tol=w0_.tol, rank_cap=w0_.cap, L=0.0,
@@ -81,13 +83,18 @@ def solve(members, snapshots, concurrency=16):
                 ctxs[-1].hopf_set_max_ctas(share)
         for w0 in range(0, len(members), concurrency):
             wave = members[w0:w0 + concurrency]
-            tts = []
+            tts = [None] * len(wave)
             try:
-                for ctx, w in zip(ctxs, wave):
+                # Initial states of the wave, one host thread per context
+                # (the foreign calls release the interpreter lock).
+                def init(i):
+                    ctx, w = ctxs[i], wave[i]
                     m0, C0 = ctx.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
                     ctx.hopf_set_L(0.0)
                     ctx.hopf_set_nu(w.nu)
-                    tts.append(ctx.hopf_init_gaussian(m0, C0))
+                    tts[i] = ctx.hopf_init_gaussian(m0, C0)
+
+                list(pool.map(init, range(len(wave))))
                 live = list(zip(ctxs, tts))
                 done = 0
                 for j, s in enumerate(snapshots):
@@ -99,8 +106,10 @@ def solve(members, snapshots, concurrency=16):
                         out[w0 + i, j] = pack_moments(mean, cov)
             finally:
                 for ctx, t in zip(ctxs, tts):
-                    ctx.tt_free(t)
+                    if t is not None:
+                        ctx.tt_free(t)
     finally:
+        pool.shutdown()
         for ctx in ctxs:
             ctx.close()
     return out
