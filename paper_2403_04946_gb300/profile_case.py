@@ -6,6 +6,12 @@ one fused hopf_step when --step is given.  Sized by --d/--n/--r so a capture
 stays small (d=4, n=128, r=64 holds about 2.5 GB on the device).
 
   python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64 [--mixed]
+
+With --surrogate it instead runs the surrogate network alone on seeded
+synthetic data (26 -> 256 x 4 -> 14, 4 members): 20 training steps of batch
+128 (one captured CUDA graph, replayed) and one 4096-query prediction.
+
+  python -m paper_2403_04946_gb300.profile_case --surrogate
 """
 from __future__ import annotations
 
@@ -27,9 +33,13 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--step", action="store_true")
     ap.add_argument("--mixed", action="store_true", help="HOPF_MIXED precision")
+    ap.add_argument("--surrogate", action="store_true", help="the surrogate network only")
     args = ap.parse_args()
     from paper_2403_04946_gb300 import binding
     import synthetic
+
+    if args.surrogate:
+        return surrogate_case(binding, synthetic)
 
     cores, _ = synthetic.saturated_tt_cores(args.d, args.n, args.r, seed=0)
     ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r, L=12.4,
@@ -47,6 +57,27 @@ def main():
         print(f"hopf_step: {time.time() - t0:.3f} s")
     ctx.tt_free(big)
     ctx.tt_free(t)
+    ctx.close()
+
+
+def surrogate_case(binding, synthetic):
+    import numpy as np
+
+    dims, members, iters, batch, ns = [26, 256, 256, 256, 256, 14], 4, 20, 128, 1280
+    ctx = binding.Context(d=4, n=8, nu=0.05, tol=1e-10, rank_cap=4, L=3.0)
+    net = binding.Mlp(ctx, dims[0], dims[1], len(dims) - 2, dims[-1], members, 4096,
+                      synthetic.mlp_init(0, dims, members))
+    rng = np.random.default_rng(1)
+    X, Y = rng.normal(size=(ns, dims[0])), rng.normal(size=(ns, dims[-1]))
+    net.set_data(X, Y)
+    t0 = time.time()
+    loss = net.train(synthetic.batch_indices(2, iters, members, batch, ns), np.full(iters, 1e-3))
+    t1 = time.time()
+    net.predict(np.repeat(X, 4, axis=0)[:4096], 1.0)
+    t2 = time.time()
+    print(f"surrogate: {iters} training steps {t1 - t0:.3f} s (loss {loss[0].mean():.3f} -> "
+          f"{loss[-1].mean():.3f}), 4096-query prediction {t2 - t1:.4f} s")
+    net.close()
     ctx.close()
 
 
