@@ -95,8 +95,9 @@ hopf_status hopf_get_L(const hopf_ctx* ctx, double* L);
 hopf_status hopf_set_nu(hopf_ctx* ctx, double nu);
 /* Method of the small SVDs of the truncation (App. A, Alg. 4: the SVD of
  * the triangular factor R of each bond).  HOPF_SVD_AUTO (the default):
- * square factors through Householder bidiagonalisation, Sturm bisection
- * and inverse iteration; wide factors by one-sided Jacobi.
+ * Householder bidiagonalisation, Sturm bisection and inverse iteration
+ * (a wide factor through its LQ, whose square triangle has the same
+ * singular values and left singular vectors).
  * HOPF_SVD_JACOBI: one-sided Jacobi for every factor.  Both give the same
  * truncation up to rounding.  Errors: HOPF_EINVAL (unknown method). */
 enum { HOPF_SVD_AUTO = 0, HOPF_SVD_JACOBI = 1 };

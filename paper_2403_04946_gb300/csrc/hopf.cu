@@ -474,9 +474,22 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     if (forced && (forced_c < 1 || forced_c > nsv))
       return fail(ctx, HOPF_EINVAL, "forced rank %d at bond %d outside [1, %d]", forced_c, c + 1, nsv);
     // Square factors: bidiagonalisation, bisection and inverse iteration.
-    const bool use_bd = case1 && ctx->svd_method != HOPF_SVD_JACOBI && hk::gebrd_fits(pp, ctx->coop);
+    // A wide factor (pp < cols) goes the same way through its LQ:
+    // R = L Q' with L = R_f^H, R^H = Q_h R_f, so R and the square L share
+    // their singular values and left singular vectors, which is all the
+    // truncation uses (the projection below is S = U^H R).  The LQ is FP64
+    // like the SVD, on the reflector slot c that this step no longer needs.
+    const bool use_bd = ctx->svd_method != HOPF_SVD_JACOBI && hk::gebrd_fits(pp, ctx->coop);
     if (use_bd) {
-      CK(cudaMemcpyAsync(w.Mb, w.Rb, (size_t)pp * cols * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
+      if (case1) {
+        CK(cudaMemcpyAsync(w.Mb, w.Rb, (size_t)pp * cols * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
+      } else {
+        int nbl = 32;
+        LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::conj_transpose(w.Rb, pp, pp, cols, w.Mb, cols, ctx->stream));
+        LAUNCH(HOPF_K_SVD, qr_flops(cols, pp), 0, 1, hk::geqrf(w.Mb, cols, cols, pp, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbl, ctx->coop, ctx->stream, 0));
+        LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::extract_r(w.Mb, cols, pp, pp, w.Jb, pp, ctx->stream));
+        LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::conj_transpose(w.Jb, pp, pp, pp, w.Mb, pp, ctx->stream));
+      }
       LAUNCH(HOPF_K_SVD, gebrd_flops(pp), 0, 1, hk::gebrd(w.Mb, pp, pp, w.bd_d, w.bd_e, w.bd_tauq, w.bd_taup, ctx->coop, ctx->stream));
       LAUNCH(HOPF_K_SVD, 0, 0, 2, hk::bd_sigma(w.bd_d, w.bd_e, pp, w.bd_a2, w.bd_info, w.sig, ctx->stream));
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::bd_rank(w.sig, pp, ctx->d_dbl + 1, cap, forced_c, ctx->d_int, ctx->d_dbl + 2, w.sig + pp, ctx->stream));
