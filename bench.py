@@ -143,6 +143,23 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """Largest value of x over the ranks of the default process group
+    (world 1: x itself): the slowest replica sets the job's time."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, slowest_seconds, world):
+    """Whole-job throughput of `world` independent replicas that each
+    processed `units_per_rank` units: all units over the slowest time."""
+    return world * units_per_rank / slowest_seconds
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -392,10 +409,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     def maxover(x):
-        tm = torch.tensor([x], device=dev, dtype=torch.float64)
-        if world > 1:
-            torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
-        return float(tm.item())
+        return max_over_ranks(x, world, dev)
 
     gpu_id = "0"
     try:
@@ -451,7 +465,7 @@ def run_ours(args, rank, world, local_rank):
     result = None
     if rank == 0:
         peaks = read_peaks()
-        value = world * args.steps / elapsed
+        value = replica_rate(args.steps, elapsed, world)
         total_ms = sum(v["ms"] for v in prof.values() if isinstance(v, dict))
         shares = {k: round(v["ms"] / total_ms, 4) for k, v in prof.items() if isinstance(v, dict) and v["ms"] > 0}
         total64 = sum(v["ms"] for v in prof64.values() if isinstance(v, dict))
@@ -472,7 +486,7 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic", "config": config_dict(w),
             "roofline": roofline(prof, True, peaks),
             "kernel_shares": shares,
-            "fp64": {"value": world * args.steps / el64, "unit": "steps/s", "ms_per_step": el64 / args.steps * 1e3,
+            "fp64": {"value": replica_rate(args.steps, el64, world), "unit": "steps/s", "ms_per_step": el64 / args.steps * 1e3,
                      "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},
             "mixed_vs_fp64_error": err,
             "ensemble": ens,
@@ -480,7 +494,7 @@ def run_ours(args, rank, world, local_rank):
             "apply_gbs": apply_gbs,
             "jacobi_sweeps_per_svd": prof["svd"].get("sweeps", 0) / max(1, prof["svd"].get("count", 0)),
             "cpu_baseline": cpu,
-            "e2e": {"value": world * k_e2e / e2e_s, "unit": "steps/s",
+            "e2e": {"value": replica_rate(k_e2e, e2e_s, world), "unit": "steps/s",
                     "h2d_bytes_per_step": int(nd * 8), "d2h_bytes_per_step": int(out_bytes)},
             "gpu_launches": int(sum(v["launches"] for v in prof.values() if isinstance(v, dict))),
             "clocks": clocks.summary(),
