@@ -43,3 +43,56 @@ def test_param_count_matches_layout(lib):
     bad = B.HopfMlpParams(0, 8, 1, 2, 1, 16)
     P = C.c_longlong()
     assert lib.hopf_mlp_param_count(C.byref(bad), C.byref(P)) == B.HOPF_EINVAL
+
+
+def test_dataset_pairs_rates_with_initial_moments(monkeypatch):
+    """dataset(): one pair per (solve, snapshot > 0), input [params(T), y0],
+    target (y(T) - y0) / T; the solver is replaced by a known table."""
+    from paper_2403_04946_gb300 import surrogate as S
+    members = [synthetic.surrogate_member(s) for s in (1, 2)]
+    table = np.arange(2 * 3 * 14, dtype=float).reshape(2, 3, 14) ** 1.5
+
+    def fake_solve(ms, steps, **kw):
+        assert steps == [0, 2, 5]
+        return table[: len(ms)]
+
+    monkeypatch.setattr(S, "solve", fake_solve)
+    X, R, Y0, YT, T = S.dataset(members, [5, 2])
+    assert X.shape == (4, S.n_in(4)) and R.shape == (4, 14)
+    dt = members[0].dt
+    np.testing.assert_allclose(T, [2 * dt, 5 * dt, 2 * dt, 5 * dt])
+    np.testing.assert_array_equal(X[1, :S.N_PARAMS], S.params(members[0], 5 * dt))
+    np.testing.assert_array_equal(X[3, S.N_PARAMS:], table[1, 0])
+    np.testing.assert_allclose(R[2], (table[1, 1] - table[1, 0]) / (2 * dt))
+    np.testing.assert_array_equal(YT[3], table[1, 2])
+    np.testing.assert_array_equal(Y0[0], table[0, 0])
+
+
+def test_answer_routes_rejected_queries_to_the_solver(monkeypatch):
+    """answer(): the network's answer where its bound <= tol, the solver's
+    elsewhere, with the solves grouped by step count."""
+    from paper_2403_04946_gb300 import surrogate as S
+    members = [synthetic.surrogate_member(s) for s in (3, 4, 5, 6)]
+    steps = [4, 7, 4, 7]
+    calls = []
+
+    def fake_solve(ms, st, **kw):
+        calls.append((len(ms), tuple(st)))
+        if st == [0]:
+            return np.zeros((len(ms), 1, 14))
+        return np.full((len(ms), 1, 14), 100.0 + st[0])
+
+    class FakeNet:
+        def predict(self, X, kappa, base=None, scale=None):
+            return np.ones((len(X), 14)), np.array([1e-4, 5e-3, 2e-3, 1e-5])
+
+    monkeypatch.setattr(S, "solve", fake_solve)
+    sur = S.Surrogate.__new__(S.Surrogate)
+    sur.net, sur.kappa, sur.d = FakeNet(), 1.0, 4
+    out = sur.answer(members, steps, 1e-3)
+    np.testing.assert_array_equal(out["accepted"], [True, False, False, True])
+    np.testing.assert_array_equal(out["y"][0], np.ones(14))
+    np.testing.assert_array_equal(out["y"][1], np.full(14, 107.0))
+    np.testing.assert_array_equal(out["y"][2], np.full(14, 104.0))
+    np.testing.assert_array_equal(out["y_net"][1], np.ones(14))
+    assert calls == [(4, (0,)), (1, (4,)), (1, (7,))]
