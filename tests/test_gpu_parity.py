@@ -9,6 +9,9 @@ are compared core by core.  Rank decisions are replayed from the oracle
 Tolerances (relative L2 unless stated): 1e-13 for gauge-free kernels
 (a few roundings of 16-byte complex products); 1e-12 for one rounding;
 1e-10 for time stepping (the acceptance bound for the FP64 path)."""
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -329,6 +332,26 @@ def test_step_parity_c1_full_horizon(B):
     ctx, t, ocores = _step_parity(B, w, n, w.steps, cores, L)
     err = rel(tt.full(ctx.tt_to_host(t)), tt.full(ocores))
     print(f"C1 {w.steps} steps: rel L2 err {err:.3e}")
+    assert err < 1e-10
+
+
+def test_step_matches_stored_oracle_values(B):
+    """C1, 20 RK4 steps on the GPU with the TT oracle's stored rank log
+    replayed (tests/golden, written from the oracle alone): Phi at the stored
+    points within 1e-10 of the oracle's, relative to the largest value."""
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_golden
+    Ls, idx, _, _, _, ranks, tvals = make_golden.read_c1()
+    w, n, m0, C0, L = _c1_state()
+    assert abs(L - Ls) <= 1e-13 * Ls  # quadrature rounding differs across hosts
+    cores = tt.tt_svd(fullgrid.phi0_grid(m0, C0, n, Ls), w.tol, w.cap)
+    ctx = B.Context(d=w.d, n=n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=Ls)
+    t = ctx.tt_from_host(cores, max_rank=w.cap)
+    out = ctx.hopf_step(t, w.dt, make_golden.NSTEPS, record=True, replay=ranks)
+    assert np.array_equal(out["ranks"], ranks)
+    got = ctx.hopf_eval_points(t, idx)
+    err = np.abs(got - tvals).max() / np.abs(tvals).max()
+    print(f"stored oracle values: max err {err:.2e}")
     assert err < 1e-10
 
 
