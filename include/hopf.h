@@ -194,6 +194,10 @@ hopf_status tt_sum(hopf_ctx* ctx, int nterms, const hopf_tt* const* terms,
  * rank_log (may be NULL): host [8 * nsteps * (d+1)] ints receiving the ranks
  * after every rounding (for ranks replay).  forced_log (may be NULL): host
  * ranks to replay, same layout.  Returns HOPF_ERANKCAP if the cap bound. */
+hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* inout, double dt, int nsteps,
+                      double* discarded_norm_sum, int* rank_log,
+                      const int* forced_log);
+
 /* Advances an ensemble of independent states (Sec. 5: the Gaussian random
  * initial states are solved one at a time in the paper; here several are in
  * flight at once): hopf_step(ctxs[a], tts[a], dt[a], nsteps) for every a,
@@ -204,9 +208,6 @@ hopf_status tt_sum(hopf_ctx* ctx, int nterms, const hopf_tt* const* terms,
  * first failure, else HOPF_ERANKCAP if any cap bound, else HOPF_OK. */
 hopf_status hopf_step_ensemble(int count, hopf_ctx* const* ctxs, hopf_tt* const* tts,
                                const double* dt, int nsteps, hopf_status* statuses);
-hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* inout, double dt, int nsteps,
-                      double* discarded_norm_sum, int* rank_log,
-                      const int* forced_log);
 
 /* Mean and covariance of u from central differences of Phi at a = 0
  * (Sec. 1: moments are functional derivatives of Phi at theta = 0):
@@ -239,8 +240,10 @@ hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts,
  *
  * Arguments and results are those of hopf_eval_points (the tensor's context
  * and stream are used).  npts > HOPF_NOALLOC_MAX_POINTS or d >
- * HOPF_NOALLOC_MAX_D returns HOPF_EINVAL.  The first call on a device looks
- * up the arrays' device addresses (with that device current); make that
+ * HOPF_NOALLOC_MAX_D returns HOPF_EINVAL.  The work runs on the device of
+ * the tensor's context: the call makes that device current for its duration
+ * and restores the caller's current device before it returns.  The first
+ * call on a device looks up the arrays' device addresses there; make that
  * first call before any stream capture.  All calls share the two arrays:
  * calls whose GPU work overlaps (on different streams or contexts) race on
  * them and must be serialised by the caller. */

@@ -18,7 +18,11 @@ Pinned by (tests/test_oracle_mlp.py): GELU at points where the normal CDF is
 known, its odd part GELU(x) - GELU(-x) = x and its slope 1/2 at 0; the
 backward pass against central finite differences of the forward pass; a
 network without hidden layers against the closed-form least-squares gradient;
-the first Adam step against its closed form -lr g / (|g| + eps).
+the first Adam step against its closed form -lr g / (|g| + eps) and the
+second and third steps against the recursions written out by hand with their
+bias corrections; the ensemble bound of a two-member ensemble against the
+spread |y_1 - y_2| / 2 worked by hand; the column statistics on constant,
+two-valued and affine columns.
 """
 from __future__ import annotations
 

@@ -12,7 +12,7 @@ FDE becomes the linear PDE of the form of Eq. (hyper1)
 Each a_j is discretised on a uniform grid (Eq. tt / Eq. ode); the tensor
 product structure lets the generator act mode by mode.
 
-Readings where the paper is silent (listed in the design doc): the a-grid is
+Readings where the paper is silent: the a-grid is
 a_i = (i - n/2) da, da = 2L/n, i = 0..n-1, with slot 0 (a = -L) held at zero
 and a = +L an implicit zero ghost; the covariance kernel is the periodic
 squared exponential sigma^2 exp(-2 sin^2((x-y)/2)/ell^2).

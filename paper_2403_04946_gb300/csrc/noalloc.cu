@@ -37,16 +37,15 @@ constexpr int kMaxDevices = 64;
 Addrs g_addrs[kMaxDevices];
 std::mutex g_addrs_mu;
 
-cudaError_t device_addrs(Addrs* out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Looks up (once) the arrays' addresses on device `dev`, which must be the
+// current device.
+cudaError_t device_addrs(int dev, Addrs* out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_addrs_mu);
   Addrs& a = g_addrs[dev];
   if (!a.ready) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_idx);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_idx);
     if (e != cudaSuccess) return e;
     a.idx = static_cast<int*>(p);
     e = cudaGetSymbolAddress(&p, g_noalloc_vals);
@@ -58,11 +57,27 @@ cudaError_t device_addrs(Addrs* out) {
   return cudaSuccess;
 }
 
+// Makes `dev` current for the lifetime of the guard and restores the
+// caller's device afterwards (on every return path).
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    else if (err == cudaSuccess) prev = -1;  // nothing to restore
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace
 
 // Internal accessors defined in hopf.cu (the tensor layout is private there).
 hopf_ctx* hopf_internal_tt_ctx(const hopf_tt* t);
 cudaStream_t hopf_internal_stream(const hopf_ctx* ctx);
+int hopf_internal_device(const hopf_ctx* ctx);
 hopf_status hopf_internal_tt_view(const hopf_tt* t, const double2* const** d_ptrs, const int** d_ranks,
                                   int* d, int* n, int* maxr);
 void hopf_internal_set_error(hopf_ctx* ctx, const char* msg);
@@ -90,8 +105,13 @@ extern "C" hopf_status hopf_eval_points_noalloc(const hopf_tt* t, int npts, cons
       return HOPF_EINVAL;
     }
   if (npts == 0) return HOPF_OK;
+  // The tensor's data, its context's stream and the arrays used here all
+  // belong to the context's device, whatever device the caller has current.
+  const int dev = hopf_internal_device(ctx);
+  DeviceGuard guard(dev);
+  cudaError_t e = guard.err;
   Addrs a;
-  cudaError_t e = device_addrs(&a);
+  if (e == cudaSuccess) e = device_addrs(dev, &a);
   const cudaStream_t s = hopf_internal_stream(ctx);
   // Every value read below is written first in this call: the index list is
   // copied in, and the kernel writes one result per point.

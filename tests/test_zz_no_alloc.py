@@ -57,3 +57,25 @@ def test_noalloc_rejects_sizes_beyond_its_arrays(B):
     assert rel(ctx.hopf_eval_points_noalloc(t, idx), ctx.hopf_eval_points(t, idx)) < 1e-14
     ctx.tt_free(t)
     ctx.close()
+
+
+def test_noalloc_leaves_device_memory_unchanged(B):
+    """The property the entry point exists for: a burst of calls takes no
+    device memory.  The first call is made before the measurement (the
+    library's module, which holds the two arrays, may be loaded lazily on
+    first use); after it the device's free memory must not move."""
+    torch = pytest.importorskip("torch")
+    d, n = 6, 16
+    x = synthetic.random_tt_cores(d, n, [1, 4, 8, 8, 8, 4, 1], seed=23)
+    ctx = B.Context(d=d, n=n, nu=0.05, tol=1e-10, rank_cap=8, L=3.0)
+    t = ctx.tt_from_host(x)
+    idx = synthetic.random_probe_indices(d, n, 2048, 5)
+    first = ctx.hopf_eval_points_noalloc(t, idx)
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(25):
+        got = ctx.hopf_eval_points_noalloc(t, idx)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    np.testing.assert_array_equal(got, first)
+    ctx.tt_free(t)
+    ctx.close()
