@@ -342,6 +342,22 @@ hopf_status hopf_mlp_predict(hopf_mlp* m, int nq, const double* x,
                              double* members_y);
 void hopf_mlp_free(hopf_mlp* m);
 
+/* ---- tensor-core products (diagnostic) ------------------------------------ */
+
+/* C = op(A) op(B) for complex matrices through the library's tensor-core
+ * path: the digit-split (Ozaki-style) BF16 products with exact FP32
+ * accumulation that the mixed-precision rounding uses for its dense
+ * contractions (App. A, Alg. 4's products), with three real products per
+ * complex one.  op(X) = X (op 0) or X^H (op 1).  A: host, column-major,
+ * op(A) is M x K (A itself is M x K with lda >= M, or K x M with lda >= K);
+ * B likewise with op(B) K x N; C: host M x N, ldc >= M.  digits: 1..5
+ * (each 8 bits of every operand row, relative to the row's largest
+ * entry; 5 digits give about 5e-12 of |op(A)| |op(B)|).  Exposed so that the
+ * products can be checked directly; the solver calls the same kernels.
+ * Errors: HOPF_EINVAL (sizes, digits), HOPF_ENOMEM, HOPF_ETIMEOUT, HOPF_ECUDA. */
+hopf_status hopf_tc_zgemm(hopf_ctx* ctx, int M, int N, int K, const double* A, int lda, int opA,
+                          const double* B, int ldb, int opB, int digits, double* C, int ldc);
+
 /* ---- instrumentation ----------------------------------------------------- */
 
 /* Kernel classes of the profile record. */

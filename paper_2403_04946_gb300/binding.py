@@ -58,6 +58,7 @@ SIGNATURES = {
     "hopf_profile_enable": (_i, [_vp, _i]),
     "hopf_profile_read": (_i, [_vp, _vp, _i]),
     "hopf_eval_points_noalloc": (_i, [_vp, _i, _pi, _pd]),
+    "hopf_tc_zgemm": (_i, [_vp, _i, _i, _i, _pd, _i, _i, _pd, _i, _i, _i, _pd, _i]),
     "hopf_mlp_create": (_i, [_vp, _vp, _vp, C.POINTER(_vp)]),
     "hopf_mlp_param_count": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "hopf_mlp_get_params": (_i, [_vp, _vp]),
@@ -326,6 +327,21 @@ class Context:
         vals = np.zeros(2 * idx.shape[0])
         self._check(self.lib.hopf_eval_points_noalloc(t, idx.shape[0], _iptr(idx), _dptr(vals)))
         return vals.view(np.complex128)
+
+    def hopf_tc_zgemm(self, A, B, opA=0, opB=0, digits=5):
+        """op(A) op(B) through the tensor-core digit products (op 1 = conj
+        transpose); A, B complex numpy matrices."""
+        A = np.asfortranarray(A, dtype=np.complex128)
+        B = np.asfortranarray(B, dtype=np.complex128)
+        M, K = (A.shape[1], A.shape[0]) if opA else A.shape
+        K2, N = (B.shape[1], B.shape[0]) if opB else B.shape
+        if K != K2:
+            raise ValueError("inner dimensions differ")
+        Cm = np.zeros((M, N), dtype=np.complex128, order="F")
+        flat = lambda X: X.reshape(-1, order="F").view(np.float64)  # views of the F-ordered data
+        self._check(self.lib.hopf_tc_zgemm(self.h, M, N, K, _dptr(flat(A)), A.shape[0], int(opA), _dptr(flat(B)),
+                                           B.shape[0], int(opB), int(digits), _dptr(flat(Cm)), M))
+        return Cm
 
     def tt_norm(self, t):
         v = C.c_double()

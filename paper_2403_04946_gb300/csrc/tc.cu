@@ -1,0 +1,559 @@
+// Complex products on the tensor cores (tcgen05) with FP64-class accuracy.
+//
+// The mixed-precision rounding (App. A, Alg. 2 / Alg. 4: the QR trailing
+// updates, the Q applications and the merges of the orthogonalisation sweep)
+// needs products accurate to about 1e-12 of |A||B|, far beyond one BF16 or
+// TF32 product.  Each operand is therefore cut into S digit planes
+// (Ozaki-style splitting): per row r and per K-chunk, a power-of-two scale
+// 2^e[r] brings the row below 1 in magnitude, and
+//     x 2^-e = sum_j q_j 2^(-7-8j),   q_j integers with |q_j| <= 128,
+// each q_j exactly representable in BF16.  A product of two digits is an
+// integer below 2^14 in magnitude, so a K-chunk of at most 192 products per
+// digit pair, summed over the pairs (i, j) of one level L = i + j (L + 1 <= 5
+// pairs), stays below 2^24: the FP32 accumulation in tensor memory is exact.
+// Levels L < S are kept (S (S + 1) / 2 digit products per real product); the
+// dropped pairs weigh about S 2^(-8S) of |A||B| (5 digits: ~5e-12).
+//
+// Complex products use three real products (3M):
+//     T1 = Ar Br,  T2 = Ai Bi,  T3 = (Ar + Ai)(Br + Bi),
+//     C = (T1 - T2) + i (T3 - T1 - T2),
+// each of Ar, Ai, Ar + Ai (and the same for B) split with its own scales.
+//
+// The product kernel: one CTA per 128 x 32 output tile and K-chunk.  Warp 4
+// streams digit slabs (64 K-values, 128 B per row, 128-byte swizzle) into a
+// two-stage shared-memory ring with TMA (cp.async.bulk.tensor); warp 5 issues
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into 15 accumulators
+// (3 products x 5 levels x 32 columns) in tensor memory; warps 0-3 read the
+// accumulators back (tcgen05.ld), combine levels, scales and the 3M terms in
+// FP64, and write the complex result (overwritten, added, or as a per-chunk
+// partial that a reduction kernel sums in a fixed order).
+//
+// Every wait is bounded (2 s of wall time): on expiry the kernel records
+// the error in the grid-barrier record the host checks (HOPF_ETIMEOUT),
+// stops issuing work, waits (bounded) for what it issued, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "kernels.h"
+
+namespace hk {
+
+namespace {
+
+constexpr int kTcM = 128;        // rows of an output tile (one TMEM lane each)
+constexpr int kTcN = 32;         // columns of an output tile
+constexpr int kSlab = 64;        // K-values per digit slab (128 bytes of BF16)
+constexpr int kMaxDigits = 5;    // 3 products x 5 levels x 32 columns = 480 TMEM columns
+constexpr int kTmemCols = 512;
+constexpr int kStages = 2;
+constexpr int kTcThreads = 192;  // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+__host__ __device__ constexpr int a_plane_bytes() { return kTcM * kSlab * 2; }  // 16 KB
+__host__ __device__ constexpr int b_plane_bytes() { return kTcN * kSlab * 2; }  // 4 KB
+__host__ __device__ int stage_bytes(int S) { return S * (a_plane_bytes() + b_plane_bytes()); }
+size_t tc_smem_bytes(int S) { return (size_t)kStages * stage_bytes(S) + 1024; }
+
+DV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+DV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+DV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+DV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase of `bar` with the given parity.  Returns false if the
+// kernel is aborting (flag set by another role) or the wait expired (then
+// the flag is set here and the expiry recorded in *err).
+DV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u) {
+      if (*abort_flag) return false;
+      const uint64_t now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        *abort_flag = 1;
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+DV void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major BF16 tile written by TMA with
+// the 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart.
+DV uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address / 16
+  d |= (uint64_t)1 << 16;                   // leading-dimension offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride between 8-row atoms / 16
+  d |= (uint64_t)1 << 46;                   // descriptor version of tcgen05
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: dense BF16 x BF16 -> FP32, both operands K-major,
+// M = 128, N = kTcN.
+constexpr uint32_t kIdesc = (1u << 4)                      // D in FP32
+                            | (1u << 7)                    // A in BF16
+                            | (1u << 10)                   // B in BF16
+                            | ((uint32_t)(kTcN >> 3) << 17)  // N / 8
+                            | ((uint32_t)(kTcM >> 4) << 24);  // M / 16
+
+DV void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+DV void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+DV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+DV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+DV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+struct TcArgs {
+  int M, N, K, S, Kc, nchunks;
+  const int* eA;  // [3][nchunks][M] scale exponents of the A digits
+  const int* eB;  // [3][nchunks][N]
+  cplx* out;      // out[z * zstride + m + ldo * n]
+  long long ldo, zstride;
+  double alpha;   // out = alpha * result (+ out if accumulate)
+  int accumulate;
+  int* err;       // expiry record (the context's grid-barrier err field)
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_zgemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], acc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  // 1024-byte aligned stage ring (the swizzle atoms need it)
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int S = a.S;
+  const int sbytes = stage_bytes(S);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * kTcN, z = blockIdx.z;
+  const int k_begin = z * a.Kc;
+  const int k_len = min(a.Kc, a.K - k_begin);
+  const int nslab = (k_len + kSlab - 1) / kSlab;
+  const int nstage = 3 * nslab;  // (slab, product) pairs
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* vabort = &abort_flag;
+
+  if (warp == 4) {
+    // ---- producer: one (slab, product) stage at a time ------------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int st = 0; st < nstage; ++st) {
+        const int slot = st % kStages;
+        if (st >= kStages && !mbar_wait(&empty_bar[slot], ((st / kStages) - 1) & 1, vabort, a.err)) break;
+        const int c = st % 3, slab = st / 3;
+        const int k0 = k_begin + slab * kSlab;
+        unsigned char* base = smem + (size_t)slot * sbytes;
+        mbar_expect_tx(&full_bar[slot], (uint32_t)sbytes);
+        for (int j = 0; j < S; ++j) {
+          tma_load_3d(base + (size_t)j * a_plane_bytes(), &mapA, &full_bar[slot], k0, m0, c * S + j);
+          tma_load_3d(base + (size_t)S * a_plane_bytes() + (size_t)j * b_plane_bytes(), &mapB, &full_bar[slot], k0, n0,
+                      c * S + j);
+        }
+        issued = st + 1;
+      }
+      // before leaving, every issued copy has landed (bounded): the stage
+      // ring must not be written after the CTA exits
+      for (int st = max(0, issued - kStages); st < issued; ++st) {
+        uint64_t t0 = global_ns();
+        while (!mbar_try_wait(&full_bar[st % kStages], (st / kStages) & 1))
+          if (global_ns() - t0 > kWaitNs) break;
+      }
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer -------------------------------------------------------
+    if (lane == 0) {
+      for (int st = 0; st < nstage; ++st) {
+        const int slot = st % kStages;
+        if (!mbar_wait(&full_bar[slot], (st / kStages) & 1, vabort, a.err)) break;
+        tc_fence_after();
+        const int c = st % 3, slab = st / 3;
+        const uint32_t abase = smem_u32(smem + (size_t)slot * sbytes);
+        const uint32_t bbase = abase + (uint32_t)(S * a_plane_bytes());
+        for (int L = 0; L < S; ++L) {
+          const uint32_t acc = tmem + (uint32_t)((c * S + L) * kTcN);
+          for (int i = 0; i <= L; ++i) {
+            const int j = L - i;
+#pragma unroll
+            for (int kk = 0; kk < kSlab / 16; ++kk) {
+              const uint64_t ad = sw128_desc(abase + (uint32_t)(i * a_plane_bytes() + kk * 32));
+              const uint64_t bd = sw128_desc(bbase + (uint32_t)(j * b_plane_bytes() + kk * 32));
+              umma(acc, ad, bd, (slab > 0 || i > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+        }
+        umma_commit(&empty_bar[slot]);  // the stage is free once these MMAs have read it
+      }
+      umma_commit(&acc_bar);  // all accumulators final (also after an abort)
+    }
+  } else {
+    // ---- epilogue: warps 0-3, thread = output row ------------------------
+    const bool ok = mbar_wait(&acc_bar, 0, vabort, a.err);
+    tc_fence_after();
+    const int m = m0 + 32 * warp + lane;
+    if (ok && !*vabort) {
+      const int* eA = a.eA + (size_t)z * a.M;
+      const int* eB = a.eB + (size_t)z * a.N;
+      const size_t eAs = (size_t)a.nchunks * a.M, eBs = (size_t)a.nchunks * a.N;
+      int ea[3] = {0, 0, 0};
+      if (m < a.M)
+        for (int c = 0; c < 3; ++c) ea[c] = eA[c * eAs + m];
+      cplx* out = a.out + (size_t)z * a.zstride;
+#pragma unroll 1
+      for (int h = 0; h < kTcN / 16; ++h) {
+        double cre[16], cim[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) cre[q] = cim[q] = 0.0;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+          double t[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) t[q] = 0.0;
+#pragma unroll 1
+          for (int L = 0; L < S; ++L) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((c * S + L) * kTcN + 16 * h), v);
+            const double w = ldexp(1.0, -14 - 8 * L);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) t[q] = fma(w, (double)v[q], t[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int n = n0 + 16 * h + q;
+            const int eb = (n < a.N) ? eB[c * eBs + n] : 0;
+            const double tv = ldexp(t[q], ea[c] + eb);
+            if (c == 0) {
+              cre[q] += tv;
+              cim[q] -= tv;
+            } else if (c == 1) {
+              cre[q] -= tv;
+              cim[q] -= tv;
+            } else {
+              cim[q] += tv;
+            }
+          }
+        }
+        if (m < a.M) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int n = n0 + 16 * h + q;
+            if (n < a.N) {
+              cplx* p = out + m + (size_t)a.ldo * n;
+              cplx r = mk(a.alpha * cre[q], a.alpha * cim[q]);
+              if (a.accumulate) r = cadd(*p, r);
+              *p = r;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ---- digit splitting ----------------------------------------------------------
+// The operand view of TcOperandView (kernels.h), passed by value.
+struct SplitView {
+  const cplx* X;
+  long long rs, ks;
+  int R, K, conj;
+  int tri_mode, tri;
+};
+
+DV cplx view_at(const SplitView& v, int r, int k) {
+  if (v.tri_mode == 1 && r > k + v.tri) return mk(0, 0);
+  if (v.tri_mode == 2) {
+    // reflector s = r (rows of the view are reflector indices), entry i = k:
+    // zero above the unit diagonal k < r + tri, one on it
+    if (k < r + v.tri) return mk(0, 0);
+    if (k == r + v.tri) return mk(1, 0);
+  }
+  if (v.tri_mode == 3) {
+    // same reflector block, view with rows = entry index i, columns = s
+    if (r < k + v.tri) return mk(0, 0);
+    if (r == k + v.tri) return mk(1, 0);
+  }
+  cplx x = v.X[(long long)r * v.rs + (long long)k * v.ks];
+  if (v.conj) x.y = -x.y;
+  return x;
+}
+
+DV void comps(cplx x, double (&c)[3]) {
+  c[0] = x.x;
+  c[1] = x.y;
+  c[2] = x.x + x.y;
+}
+
+// Per (row, chunk, product component): exponent e with max |x| 2^-e < 1.
+// One warp per (row, chunk): lanes stride over the chunk.
+__global__ void split_exp_kernel(SplitView v, int Kc, int nchunks, int* e) {
+  const int warps = blockDim.x >> 5;
+  const long long task = (long long)blockIdx.x * warps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (task >= (long long)v.R * nchunks) return;
+  const int r = (int)(task % v.R), z = (int)(task / v.R);
+  const int k0 = z * Kc, k1 = min(v.K, k0 + Kc);
+  double mx[3] = {0.0, 0.0, 0.0};
+  for (int k = k0 + lane; k < k1; k += 32) {
+    double c[3];
+    comps(view_at(v, r, k), c);
+    for (int q = 0; q < 3; ++q) mx[q] = fmax(mx[q], fabs(c[q]));
+  }
+  for (int q = 0; q < 3; ++q)
+    for (int o = 16; o >= 1; o >>= 1) mx[q] = fmax(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+  if (lane == 0)
+    for (int q = 0; q < 3; ++q)
+      e[((size_t)q * nchunks + z) * v.R + r] = (mx[q] > 0.0) ? ilogb(mx[q]) + 1 : 0;
+}
+
+// Digit planes: plane (q * S + j) holds digit j of component q, row-major
+// [R][ldk] BF16 (K contiguous).  One thread per (r, k).
+__global__ void split_digit_kernel(SplitView v, int Kc, int nchunks, const int* e, int S, __nv_bfloat16* planes,
+                                   long long ldk) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)v.R * v.K) return;
+  // k fastest when the operand is K-contiguous, r fastest otherwise (coalesced reads)
+  int r, k;
+  if (v.ks == 1) {
+    k = (int)(idx % v.K);
+    r = (int)(idx / v.K);
+  } else {
+    r = (int)(idx % v.R);
+    k = (int)(idx / v.R);
+  }
+  const int z = k / Kc;
+  double c[3];
+  comps(view_at(v, r, k), c);
+  const size_t plane = (size_t)v.R * ldk;
+  for (int q = 0; q < 3; ++q) {
+    double x = ldexp(c[q], -e[((size_t)q * nchunks + z) * v.R + r]);  // |x| < 1
+    for (int j = 0; j < S; ++j) {
+      const double d = rint(ldexp(x, 7 + 8 * j));  // |d| <= 128, exact in BF16
+      x -= ldexp(d, -7 - 8 * j);                    // exact
+      planes[(size_t)(q * S + j) * plane + (size_t)r * ldk + k] = __float2bfloat16_rn((float)d);
+    }
+  }
+}
+
+// out[m + ldo n] = alpha * sum_z part[z * zstride + m + M n] (+ out)
+__global__ void reduce_parts_kernel(const cplx* part, int M, int N, int nz, long long zstride, double alpha, int accumulate,
+                                    cplx* out, long long ldo) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * N) return;
+  const int m = (int)(idx % M), n = (int)(idx / M);
+  cplx s = mk(0, 0);
+  for (int z = 0; z < nz; ++z) s = cadd(s, part[(size_t)z * zstride + idx]);
+  cplx* p = out + m + (size_t)ldo * n;
+  cplx r = mk(alpha * s.x, alpha * s.y);
+  if (accumulate) r = cadd(*p, r);
+  *p = r;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on libcuda).
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+// 3-D map over digit planes [planes][rows][ldk] BF16 with a box of
+// kSlab x box_rows x 1 and the 128-byte swizzle; rows beyond `rows` and K
+// beyond `K` read as zero.
+cudaError_t plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int K, long long ldk, int rows, int nplanes,
+                      int box_rows) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)ldk * 2 * (cuuint64_t)rows};
+  const cuuint32_t box[3] = {(cuuint32_t)kSlab, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(planes), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// ---- host entry points ------------------------------------------------------------
+
+size_t tc_operand_bytes(int R, int K, int S, int Kc) {
+  const long long ldk = ((long long)K + kSlab - 1) / kSlab * kSlab;
+  const int nchunks = (K + Kc - 1) / Kc;
+  const size_t planes = (size_t)3 * S * R * ldk * sizeof(__nv_bfloat16);
+  const size_t exps = (size_t)3 * nchunks * R * sizeof(int);
+  return ((planes + 255) & ~(size_t)255) + exps + 256;
+}
+
+int tc_chunk() { return 3 * kSlab; }
+int tc_max_digits() { return kMaxDigits; }
+
+cudaError_t tc_split(const TcOperandView& ov, int S, TcOperand* out, void* buf, cudaStream_t s) {
+  if (S < 1 || S > kMaxDigits || ov.R <= 0 || ov.K <= 0) return cudaErrorInvalidValue;
+  const int Kc = tc_chunk();
+  const long long ldk = ((long long)ov.K + kSlab - 1) / kSlab * kSlab;
+  const int nchunks = (ov.K + Kc - 1) / Kc;
+  const size_t planes = (size_t)3 * S * ov.R * ldk * sizeof(__nv_bfloat16);
+  out->planes = buf;
+  out->e = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(buf) + ((planes + 255) & ~(size_t)255));
+  out->R = ov.R;
+  out->K = ov.K;
+  out->S = S;
+  out->ldk = ldk;
+  out->nchunks = nchunks;
+  SplitView v{ov.X, ov.rs, ov.ks, ov.R, ov.K, ov.conj, ov.tri_mode, ov.tri};
+  {
+    const long long tasks = (long long)ov.R * nchunks;
+    const int threads = 256, per = threads / 32;
+    split_exp_kernel<<<(unsigned)((tasks + per - 1) / per), threads, 0, s>>>(v, Kc, nchunks, out->e);
+  }
+  {
+    const long long n = (long long)ov.R * ov.K;
+    split_digit_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, Kc, nchunks, out->e, S,
+                                                                    reinterpret_cast<__nv_bfloat16*>(buf), ldk);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t tc_zgemm(const TcOperand& A, const TcOperand& B, cplx* out, long long ldo, double alpha, int accumulate,
+                     cplx* part, size_t part_elems, int* err, cudaStream_t s) {
+  if (A.K != B.K || A.S != B.S || A.nchunks != B.nchunks) return cudaErrorInvalidValue;
+  const int M = A.R, N = B.R, K = A.K, S = A.S, nz = A.nchunks;
+  CUtensorMap ma, mb;
+  cudaError_t e = plane_map(&ma, static_cast<const __nv_bfloat16*>(A.planes), K, A.ldk, M, 3 * S, kTcM);
+  if (e == cudaSuccess) e = plane_map(&mb, static_cast<const __nv_bfloat16*>(B.planes), K, B.ldk, N, 3 * S, kTcN);
+  if (e != cudaSuccess) return e;
+  const size_t smem = tc_smem_bytes(S);
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, []() {
+    attr = cudaFuncSetAttribute(tc_zgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem_bytes(kMaxDigits));
+  });
+  if (attr != cudaSuccess) return attr;
+  TcArgs a{};
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.S = S;
+  a.Kc = tc_chunk();
+  a.nchunks = nz;
+  a.eA = A.e;
+  a.eB = B.e;
+  a.err = err;
+  const dim3 grid((M + kTcM - 1) / kTcM, (N + kTcN - 1) / kTcN, nz);
+  if (nz == 1) {
+    a.out = out;
+    a.ldo = ldo;
+    a.zstride = 0;
+    a.alpha = alpha;
+    a.accumulate = accumulate;
+    tc_zgemm_kernel<<<grid, kTcThreads, smem, s>>>(ma, mb, a);
+    return cudaGetLastError();
+  }
+  if (!part || part_elems < (size_t)nz * M * N) return cudaErrorInvalidValue;
+  a.out = part;
+  a.ldo = M;
+  a.zstride = (long long)M * N;
+  a.alpha = 1.0;
+  a.accumulate = 0;
+  tc_zgemm_kernel<<<grid, kTcThreads, smem, s>>>(ma, mb, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)M * N;
+  reduce_parts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, M, N, nz, (long long)M * N, alpha, accumulate,
+                                                                   out, ldo);
+  return cudaGetLastError();
+}
+
+size_t tc_part_elems(int M, int N, int K) {
+  const int nz = (K + tc_chunk() - 1) / tc_chunk();
+  return nz > 1 ? (size_t)nz * M * N : 0;
+}
+
+}  // namespace hk
