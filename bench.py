@@ -8,7 +8,9 @@ truncated SVD) and 4 TT sums, on the d=32, n=128, rank<=64 workload, in the
 orthonormal cores), complex values in FP64 storage.  ``value`` is the mixed-
 precision solver (FP64 Householder scalars and SVD, double-float QR arithmetic); the FP64 solver
 is timed on the same state under the ``fp64`` key, and the mixed-vs-FP64
-error is measured on a physical state.
+error is measured on a physical state.  In the mixed solver the products of
+the tall QR factorisations and Q applications run on the tensor cores
+(tcgen05) as digit-split BF16 products with exact FP32 accumulation.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -215,11 +217,41 @@ def timed_steps(ctx, t, w, steps, warmup, stream, barrier):
     return e0.elapsed_time(e1) / 1e3, prof
 
 
+# Tensor-core products of the mixed path: every complex multiply-add (8
+# FP64-equivalent FLOPs) costs 3 real products (3M) x 15 digit pairs (5
+# digits per operand) of BF16 multiply-adds, i.e. 45 real multiply-adds
+# where the FP64-equivalent count assigns 4.
+TC_DIGIT_PAIRS = 15
+TC_BF16_PER_FP64EQ = 3 * TC_DIGIT_PAIRS / 4.0
+
+
+def tc_roofline(prof, peaks):
+    """The tensor-core class (digit splitting included) against the measured
+    sustained BF16 peak (the products run inside a seconds-long step),
+    expressed in FP64-equivalent complex FLOP/s."""
+    pd = prof.get("tc", {})
+    if not pd or pd.get("ms", 0) <= 0 or pd.get("flops", 0) <= 0:
+        return None
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    src = "of measured (bf16_tflops_sustained, MEASURED_PEAKS.json)"
+    if not bf16:
+        bf16, src = 1700.0, "of fallback (1.7 PFLOP/s sustained bf16)"
+    achieved = pd["flops"] / (pd["ms"] / 1e3) / 1e12
+    peak = bf16 / TC_BF16_PER_FP64EQ
+    return {"bound": "tensor", "kernel": "tc (tc_zgemm_kernel + digit splitting)", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": f"{bf16:.1f} TFLOP/s bf16 {src} / {TC_BF16_PER_FP64EQ:.2f} bf16 multiply-adds "
+                           "per FP64-equivalent one (3M x 15 digit pairs / 4)",
+            "bf16_tflops_achieved": achieved * TC_BF16_PER_FP64EQ, "traffic": None}
+
+
 def roofline(prof, mixed, peaks):
     """Dominant contraction kernel class (largest device time among classes
     with an algorithmic FLOP count) against the peak of its own arithmetic."""
     cls = [k for k in prof if isinstance(prof[k], dict) and prof[k].get("flops", 0) > 0 and prof[k]["ms"] > 0]
     dom = max(cls, key=lambda k: prof[k]["ms"])
+    if dom == "tc":
+        return tc_roofline(prof, peaks)
     pd = prof[dom]
     launch_s = pd["ms"] / 1e3 / max(pd["timed_launches"], 1)
     achieved = pd["flops"] / max(pd["timed_launches"], 1) / launch_s / 1e12
@@ -482,9 +514,12 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 storage; QR/apply-Q/merges in double-float (2 x f32) arithmetic; f64 Householder scalars and SVD",
+            "dtype": ("f64 storage; QR trailing products and Q applications of tall factors on tensor cores "
+                      "(bf16 digit products, 5 digits, exact f32 accumulation, 3M complex); QR panels and merges "
+                      "in double-float (2 x f32); f64 Householder scalars and SVD"),
             "data": "synthetic", "config": config_dict(w),
             "roofline": roofline(prof, True, peaks),
+            "tensor_core_roofline": tc_roofline(prof, peaks),
             "kernel_shares": shares,
             "fp64": {"value": replica_rate(args.steps, el64, world), "unit": "steps/s", "ms_per_step": el64 / args.steps * 1e3,
                      "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},

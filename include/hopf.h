@@ -102,6 +102,17 @@ hopf_status hopf_set_nu(hopf_ctx* ctx, double nu);
  * truncation up to rounding.  Errors: HOPF_EINVAL (unknown method). */
 enum { HOPF_SVD_AUTO = 0, HOPF_SVD_JACOBI = 1 };
 hopf_status hopf_set_svd_method(hopf_ctx* ctx, int method);
+/* How the mixed-precision rounding factors its tall flattenings (QR of
+ * n p x K matrices, App. A Alg. 1/2; in HOPF_FP64 every QR is FP64).
+ * HOPF_QR_DOUBLEFLOAT (the default): one cooperative Householder kernel in
+ * double-float arithmetic (about 1e-13 relative per step).
+ * HOPF_QR_TENSOR: for factors of at least 4096 rows, blocked Householder in
+ * outer panels whose Gram, trailing products and Q applications run on the
+ * tensor cores (digit-split BF16 products with exact FP32 accumulation, see
+ * hopf_tc_zgemm; about 1e-9 relative per step); panels and scalars as in
+ * the default.  Errors: HOPF_EINVAL (unknown method). */
+enum { HOPF_QR_DOUBLEFLOAT = 0, HOPF_QR_TENSOR = 1 };
+hopf_status hopf_set_qr_method(hopf_ctx* ctx, int method);
 /* Limits every cooperative kernel launched by this context to max_ctas
  * CTAs, one per SM (0, the default: all SMs).  Several contexts whose
  * limits add up to at most the SM count run their solves concurrently on
@@ -110,6 +121,31 @@ hopf_status hopf_set_svd_method(hopf_ctx* ctx, int method);
  * parallel.  The paper solves one state at a time; this is a scheduling
  * option only, results are unchanged.  Errors: HOPF_EINVAL (negative). */
 hopf_status hopf_set_max_ctas(hopf_ctx* ctx, int max_ctas);
+
+/* Selects the equation the context's generator stands for.
+ * HOPF_EQ_PHI (the default): the characteristic-function PDE above, box
+ * half-width L (box = L; 0 leaves it unset).
+ * HOPF_EQ_CDF: the paper's CDF equation of the same Burgers dynamics
+ * (Sec. 5, Eq. cdf-burgers, reaction alpha = 0) for the joint CDF
+ * F(u_1..u_d) of the d grid values, on u_k = -box + k du, du = 2 box/(n-1),
+ * k = 0..n-1 (both box edges on the grid; the paper's box is 1.3): centred
+ * differences with dF/du = 0 on the box boundary (outflow), trapezoidal
+ * integrals from the lower edge, viscosity gamma = the context's nu.  Its
+ * operator has the same bond structure as the PDE's (each neighbour pair
+ * (m, m+1) contributes P+_m K_{m+1} + K_m P-_{m+1}, K = u - integral), so
+ * hopf_apply_op, tt_round and the step schemes serve it unchanged.
+ * The paper's numerical-diffusion stabiliser is not part of it (its
+ * coefficient is not given).  hopf_eval_moments and hopf_init_gaussian
+ * refuse a CDF context.  Errors: HOPF_EINVAL (unknown equation, box <= 0
+ * for the CDF). */
+enum { HOPF_EQ_PHI = 0, HOPF_EQ_CDF = 1 };
+hopf_status hopf_set_equation(hopf_ctx* ctx, int equation, double box);
+/* Initial state of the CDF equation (Sec. 5): F(u, 0) = prod_k g(u_k - mu_k),
+ * g(u) = (1 + erf(u / (sigma sqrt 2))) / 2, a rank-1 TT with zero imaginary
+ * parts (the paper: sigma = 0.25, mu = 0).  mu: host [d] or NULL (zero).
+ * *out has capacity rank_cap.  Errors: HOPF_EINVAL (not a CDF context,
+ * sigma <= 0). */
+hopf_status hopf_init_cdf(hopf_ctx* ctx, double sigma, const double* mu, hopf_tt** out);
 
 /* ---- model set-up -------------------------------------------------------- */
 
@@ -197,6 +233,21 @@ hopf_status tt_sum(hopf_ctx* ctx, int nterms, const hopf_tt* const* terms,
 hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* inout, double dt, int nsteps,
                       double* discarded_norm_sum, int* rank_log,
                       const int* forced_log);
+
+/* Step-truncation schemes (Sec. 4, "Step-truncation tensor methods"):
+ *  HOPF_RK4       classical RK4 increment, 8 roundings per step (hopf_step);
+ *  HOPF_EULER     truncated explicit Euler, Eq. (adaptive-euler-method):
+ *                 f <- T[f + dt T[G f]], 2 roundings per step;
+ *  HOPF_MIDPOINT  truncated explicit midpoint, Eq. (adaptive-midpoint-method):
+ *                 f <- T[f + dt T[G(f + dt/2 T[G f])]], 3 roundings per step,
+ *                 the inner sum untruncated as printed (the operator then acts
+ *                 on ranks up to 2 rank_cap).
+ * Every T at the context's tol and rank_cap.  Arguments as hopf_step, with
+ * rank_log / forced_log holding (roundings per step) x nsteps x (d+1) ints.
+ * Errors as hopf_step, HOPF_EINVAL for an unknown scheme. */
+enum { HOPF_RK4 = 0, HOPF_EULER = 1, HOPF_MIDPOINT = 2 };
+hopf_status hopf_step_scheme(hopf_ctx* ctx, hopf_tt* inout, int scheme, double dt, int nsteps,
+                             double* discarded_norm_sum, int* rank_log, const int* forced_log);
 
 /* Advances an ensemble of independent states (Sec. 5: the Gaussian random
  * initial states are solved one at a time in the paper; here several are in
@@ -369,6 +420,9 @@ enum {
   HOPF_K_GEMM = 4,    /* small dense products (merges, projections)         */
   HOPF_K_SUM = 5,     /* TT sums, copies, transposes                        */
   HOPF_K_SMALL = 6,   /* rank selection, gathers, norms, set-up             */
+  HOPF_K_TC = 7,      /* tensor-core products of the mixed precision (digit */
+                      /* splitting included); flops counted as FP64-       */
+                      /* equivalent complex products, 8 per multiply-add   */
   HOPF_K_NCLASS = 8
 };
 typedef struct {

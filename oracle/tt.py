@@ -278,3 +278,44 @@ def moments(cores, n, L, da):
                       - at([(j, -1), (k, 1)]) + at([(j, -1), (k, -1)])) / (4 * da ** 2)
             second[j, k] = v.real
     return mean, second - np.outer(mean, mean)
+
+
+def euler_step(cores, dt, G, tol, cap, replay=None, record=None):
+    """Truncated explicit Euler (Eq. adaptive-euler-method):
+    f_{k+1} = T_r[f_k + dt T_s[G(f_k)]], both truncations ``round_tt`` at
+    (tol, cap).  ``G`` applies the operator to a TT (e.g. apply_mpo with the
+    operator's blocks); replay/record as in rk4_step.  Returns (cores,
+    discarded norms of the 2 roundings)."""
+    discs = []
+
+    def T(x):
+        forced = next(replay) if replay is not None else None
+        y, r, disc = round_tt(x, tol, cap, forced)
+        if record is not None:
+            record.append(r)
+        discs.append(disc)
+        return y
+
+    K = T(G(cores))
+    return T(tt_sum([(1.0, cores), (dt, K)])), discs
+
+
+def midpoint_step(cores, dt, G, tol, cap, replay=None, record=None):
+    """Truncated explicit midpoint (Eq. adaptive-midpoint-method):
+    f_{k+1} = T_a[f_k + dt T_b[G(f_k + dt/2 T_c(G(f_k)))]]; the inner sum
+    f_k + dt/2 T_c(G f_k) is not truncated, as printed.  Returns (cores,
+    discarded norms of the 3 roundings)."""
+    discs = []
+
+    def T(x):
+        forced = next(replay) if replay is not None else None
+        y, r, disc = round_tt(x, tol, cap, forced)
+        if record is not None:
+            record.append(r)
+        discs.append(disc)
+        return y
+
+    K1 = T(G(cores))
+    Y = tt_sum([(1.0, cores), (0.5 * dt, K1)])
+    K2 = T(G(Y))
+    return T(tt_sum([(1.0, cores), (dt, K2)])), discs

@@ -24,6 +24,10 @@ STATUS_NAMES = ["HOPF_OK", "HOPF_EINVAL", "HOPF_ENOMEM", "HOPF_ECUDA", "HOPF_ENU
                 "HOPF_ETIMEOUT", "HOPF_ERANKCAP"]
 HOPF_FP64, HOPF_MIXED = 0, 1
 HOPF_SVD_AUTO, HOPF_SVD_JACOBI = 0, 1
+HOPF_RK4, HOPF_EULER, HOPF_MIDPOINT = 0, 1, 2
+HOPF_EQ_PHI, HOPF_EQ_CDF = 0, 1
+HOPF_QR_DOUBLEFLOAT, HOPF_QR_TENSOR = 0, 1
+SCHEME_ROUNDINGS = {HOPF_RK4: 8, HOPF_EULER: 2, HOPF_MIDPOINT: 3}
 
 # Every symbol include/hopf.h declares, with (restype, argtypes).
 _vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
@@ -36,6 +40,7 @@ SIGNATURES = {
     "hopf_get_L": (_i, [_vp, _pd]),
     "hopf_set_nu": (_i, [_vp, _d]),
     "hopf_set_svd_method": (_i, [_vp, _i]),
+    "hopf_set_qr_method": (_i, [_vp, _i]),
     "hopf_set_max_ctas": (_i, [_vp, _i]),
     "hopf_step_ensemble": (_i, [_i, _vp, _vp, _vp, _i, _vp]),
     "hopf_cell_moments": (_i, [_vp, _i, _pd, _pd, _d, _d, _pd, _pd]),
@@ -51,6 +56,9 @@ SIGNATURES = {
     "tt_round": (_i, [_vp, _vp, _d, _i, _pi, _pd]),
     "tt_sum": (_i, [_vp, _i, C.POINTER(_vp), _pd, _vp]),
     "hopf_step": (_i, [_vp, _vp, _d, _i, _pd, _pi, _pi]),
+    "hopf_step_scheme": (_i, [_vp, _vp, _i, _d, _i, _pd, _pi, _pi]),
+    "hopf_set_equation": (_i, [_vp, _i, _d]),
+    "hopf_init_cdf": (_i, [_vp, _d, _pd, C.POINTER(_vp)]),
     "hopf_eval_moments": (_i, [_vp, _vp, _pd, _pd, _pd]),
     "hopf_eval_points": (_i, [_vp, _vp, _i, _pi, _pd]),
     "tt_norm": (_i, [_vp, _vp, _pd]),
@@ -69,7 +77,7 @@ SIGNATURES = {
     "hopf_mlp_free": (None, [_vp]),
 }
 
-KERNEL_CLASSES = ["qr", "apply_q", "svd", "apply", "gemm", "sum", "small", "unused"]
+KERNEL_CLASSES = ["qr", "apply_q", "svd", "apply", "gemm", "sum", "small", "tc"]
 
 
 class HopfProfile(C.Structure):
@@ -191,6 +199,9 @@ class Context:
     def hopf_set_max_ctas(self, max_ctas):
         self._check(self.lib.hopf_set_max_ctas(self.h, int(max_ctas)))
 
+    def hopf_set_qr_method(self, method):
+        self._check(self.lib.hopf_set_qr_method(self.h, int(method)))
+
     def hopf_set_svd_method(self, method):
         self._check(self.lib.hopf_set_svd_method(self.h, int(method)))
 
@@ -275,6 +286,31 @@ class Context:
         if record:
             out["ranks"] = log.reshape(8 * nsteps, self.d + 1)
         return out
+
+    def hopf_step_scheme(self, t, scheme, dt, nsteps, record=False, replay=None):
+        """nsteps of HOPF_RK4 / HOPF_EULER / HOPF_MIDPOINT (rank logs of
+        SCHEME_ROUNDINGS[scheme] roundings per step)."""
+        per = SCHEME_ROUNDINGS[scheme]
+        disc = C.c_double()
+        log = np.zeros(per * nsteps * (self.d + 1), dtype=np.int32) if record else None
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.int32).reshape(-1)
+        st = self._check(self.lib.hopf_step_scheme(self.h, t, int(scheme), float(dt), int(nsteps), C.byref(disc),
+                                                   None if log is None else _iptr(log),
+                                                   None if rep is None else _iptr(rep)),
+                         allow=(HOPF_OK, HOPF_ERANKCAP))
+        out = {"discarded": disc.value, "status": st}
+        if record:
+            out["ranks"] = log.reshape(per * nsteps, self.d + 1)
+        return out
+
+    def hopf_set_equation(self, equation, box):
+        self._check(self.lib.hopf_set_equation(self.h, int(equation), float(box)))
+
+    def hopf_init_cdf(self, sigma=0.25, mu=None):
+        h = C.c_void_p()
+        m = None if mu is None else np.ascontiguousarray(mu, dtype=np.float64)
+        self._check(self.lib.hopf_init_cdf(self.h, float(sigma), None if m is None else _dptr(m), C.byref(h)))
+        return h
 
     def hopf_eval_moments(self, t):
         mean = np.zeros(self.d)

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhopf.so")
-SOURCES = ["hopf.cu", "qr.cu", "svd.cu", "bdsvd.cu", "cross.cu", "tt.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["hopf.cu", "qr.cu", "svd.cu", "bdsvd.cu", "cross.cu", "tt.cu", "tc.cu", "qrtc.cu", "noalloc.cu", "mlp.cu"]
 HEADERS = ["common.cuh", "kernels.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

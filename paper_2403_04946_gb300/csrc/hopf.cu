@@ -56,15 +56,21 @@ struct RoundWs {
   double* bd_info = nullptr;  // 4
   double* bd_X = nullptr;     // kcap * kcap
   double* bd_Zs = nullptr;    // kcap * 2 kcap
+  // mixed precision, tensor-core QR: per core the Gram blocks of the
+  // phase-1 reflectors (gstride elements each), and those of phase 2's QR
+  cplx* G = nullptr;
+  size_t gstride = 0;
+  cplx* G2 = nullptr;
 };
 
 struct hopf_ctx {
   hopf_params p{};
   cudaStream_t stream = nullptr;
   std::string err;
-  double L = 0.0;
+  double L = 0.0;      // a-box half-width (Phi), or the u-box half-width U (CDF)
+  int equation = HOPF_EQ_PHI;
   // operator tables
-  cplx* d_coef = nullptr;             // 5 ops x 3 x n
+  cplx* d_coef = nullptr;             // kNumOps ops x 3 x n
   unsigned char* d_blocks = nullptr;  // 3 site kinds x 36
   double* d_agrid = nullptr;          // n
   std::vector<double> agrid;
@@ -73,16 +79,21 @@ struct hopf_ctx {
   int coop_kcap = 0;
   int device = 0;
   int svd_method = HOPF_SVD_AUTO;
+  int qr_method = HOPF_QR_DOUBLEFLOAT;
   // small device scalars and pinned mirrors
   double* d_dbl = nullptr;  // [16]
   int* d_int = nullptr;     // [16]
   double* h_dbl = nullptr;  // pinned [16]
   int* h_int = nullptr;     // pinned [16]
   RoundWs rw;
+  // scratch of the tensor-core QR / Q application (grown on demand)
+  void* tcbuf = nullptr;
+  size_t tcbytes = 0;
   // hopf_step workspace
   hopf_tt* big = nullptr;
   hopf_tt* kst[4] = {nullptr, nullptr, nullptr, nullptr};
   hopf_tt* ytmp = nullptr;
+  int step_scheme = -1;            // scheme the step workspace was sized for
   hk::SumTerm* d_terms = nullptr;  // [16]
   std::vector<void*> extra;        // other device allocations to free
   // launch instrumentation
@@ -200,14 +211,17 @@ cudaError_t dalloc(T** p, size_t count) {
 // ---- per-mode operator coefficients ------------------------------------------
 // (op x)[i] = lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1] on a_i = (i - n/2) da,
 // slot 0 with zero row and column for A, D, S (and so for P, Q, Z).
+hopf_status build_ops_cdf(hopf_ctx* ctx);
+
 hopf_status build_ops(hopf_ctx* ctx) {
+  if (ctx->equation == HOPF_EQ_CDF) return build_ops_cdf(ctx);
   const int n = ctx->p.n, d = ctx->p.d;
   const double L = ctx->L;
   const double da = 2.0 * L / n;
   const double h = 2.0 * M_PI / d;
   ctx->agrid.assign(n, 0.0);
   for (int i = 0; i < n; ++i) ctx->agrid[i] = (i - n / 2) * da;
-  std::vector<cplx> coef((size_t)5 * 3 * n, cplx{0.0, 0.0});
+  std::vector<cplx> coef((size_t)hk::kNumOps * 3 * n, cplx{0.0, 0.0});
   auto set = [&](int op, int which, int i, cplx v) { coef[(size_t)op * 3 * n + (size_t)which * n + i] = v; };
   const cplx cS = ctx->p.nonlinear ? cplx{0.0, 1.0 / (4.0 * h)} : cplx{0.0, 0.0};
   const double e = ctx->p.nu / (h * h);
@@ -241,8 +255,49 @@ hopf_status build_ops(hopf_ctx* ctx) {
   return HOPF_OK;
 }
 
+// Per-variable operators of the CDF equation (Sec. 5, Eq. cdf-burgers with
+// alpha = 0) on u_k = -U + k du, du = 2U/(n-1), k = 0..n-1:
+// D centred differences with dF/du = 0 on the two boundary rows (outflow),
+// A = diag(u), and in the table's slots
+//   A <- P+ = (A D)/(2h) - (gamma/h^2) D,   Q <- P- = -(A D)/(2h) - (gamma/h^2) D,
+//   Z <- (2 gamma/h^2) A D,                 K <- A - J (J the trapezoidal
+// integral from the lower edge, op_apply), gamma = nu.  Each cyclic pair
+// (m, m+1) of the x grid contributes P+_m K_{m+1} + K_m P-_{m+1}.
+hopf_status build_ops_cdf(hopf_ctx* ctx) {
+  const int n = ctx->p.n, d = ctx->p.d;
+  const double U = ctx->L;
+  const double du = 2.0 * U / (n - 1);
+  const double h = 2.0 * M_PI / d;
+  ctx->agrid.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) ctx->agrid[k] = -U + k * du;
+  std::vector<cplx> coef((size_t)hk::kNumOps * 3 * n, cplx{0.0, 0.0});
+  auto set = [&](int op, int which, int i, double v) { coef[(size_t)op * 3 * n + (size_t)which * n + i] = cplx{v, 0.0}; };
+  const double c = ctx->p.nonlinear ? 1.0 / (2.0 * h) : 0.0;
+  const double e = ctx->p.nu / (h * h);
+  for (int k = 0; k < n; ++k) {
+    set(hk::OP_I, 1, k, 1.0);
+    set(hk::OP_K, 1, k, ctx->agrid[k]);
+    if (k == 0 || k == n - 1) continue;  // outflow rows
+    const double u = ctx->agrid[k];
+    const double dlo = -1.0 / (2 * du), dup = 1.0 / (2 * du);
+    set(hk::OP_A, 0, k, c * u * dlo - e * dlo);
+    set(hk::OP_A, 2, k, c * u * dup - e * dup);
+    set(hk::OP_Q, 0, k, -c * u * dlo - e * dlo);
+    set(hk::OP_Q, 2, k, -c * u * dup - e * dup);
+    set(hk::OP_Z, 0, k, 2.0 * e * u * dlo);
+    set(hk::OP_Z, 2, k, 2.0 * e * u * dup);
+  }
+  set(hk::OP_K, 0, 0, du);  // weight of the cumulative integral (op_apply)
+  CK(cudaMemcpyAsync(ctx->d_coef, coef.data(), coef.size() * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_agrid, ctx->agrid.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HOPF_OK;
+}
+
 // MPO block tables: kind 0 first site (row), 1 interior, 2 last site (column).
-void mpo_tables(unsigned char out[3][36]) {
+void mpo_tables_cdf(unsigned char out[3][36]);
+void mpo_tables(unsigned char out[3][36], int equation) {
+  if (equation == HOPF_EQ_CDF) return mpo_tables_cdf(out);
   for (int k = 0; k < 3; ++k)
     for (int e = 0; e < 36; ++e) out[k][e] = hk::OP_NONE;
   using namespace hk;
@@ -255,6 +310,22 @@ void mpo_tables(unsigned char out[3][36]) {
   I6(1, 3, OP_P); I6(2, 3, OP_A); I6(3, 3, OP_I); I6(4, 4, OP_I); I6(5, 5, OP_I);
   const unsigned char last[6] = {OP_Z, OP_P, OP_A, OP_I, OP_A, OP_Q};
   for (int a = 0; a < 6; ++a) out[2][a] = last[a];  // Al = 6, Ar = 1
+}
+
+// The same bond states for the CDF equation: the first operator of the pair
+// type "A then P" is P+ (slot A) and its second K; the pair type "Q then A"
+// becomes K then P- (slot Q).
+void mpo_tables_cdf(unsigned char out[3][36]) {
+  for (int k = 0; k < 3; ++k)
+    for (int e = 0; e < 36; ++e) out[k][e] = hk::OP_NONE;
+  using namespace hk;
+  const unsigned char first[6] = {OP_I, OP_A, OP_K, OP_Z, OP_K, OP_Q};
+  for (int b = 0; b < 6; ++b) out[0][b] = first[b];
+  auto I6 = [&](int a, int b, unsigned char op) { out[1][a * 6 + b] = op; };
+  I6(0, 0, OP_I); I6(0, 1, OP_A); I6(0, 2, OP_K); I6(0, 3, OP_Z);
+  I6(1, 3, OP_K); I6(2, 3, OP_Q); I6(3, 3, OP_I); I6(4, 4, OP_I); I6(5, 5, OP_I);
+  const unsigned char last[6] = {OP_Z, OP_K, OP_Q, OP_I, OP_A, OP_K};
+  for (int a = 0; a < 6; ++a) out[2][a] = last[a];
 }
 
 hopf_status coop_reserve(hopf_ctx* ctx, int kcap) {
@@ -296,6 +367,7 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   cudaFree(w.sig); cudaFree(w.perm);
   cudaFree(w.bd_d); cudaFree(w.bd_e); cudaFree(w.bd_tauq); cudaFree(w.bd_taup); cudaFree(w.bd_a2);
   cudaFree(w.bd_info); cudaFree(w.bd_X); cudaFree(w.bd_Zs);
+  cudaFree(w.G); cudaFree(w.G2);
   w = RoundWs{};
   const size_t elems = std::max(need, w.elems);
   const int d = t->d;
@@ -323,6 +395,9 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   CK(dalloc(&w.bd_info, 4));
   CK(dalloc(&w.bd_X, (size_t)K * K));
   CK(dalloc(&w.bd_Zs, (size_t)2 * K * K));
+  w.gstride = hk::qr_tc_gram_elems(K);
+  CK(dalloc(&w.G, (size_t)d * w.gstride));
+  CK(dalloc(&w.G2, w.gstride));
   w.elems = elems;
   w.d = d;
   w.kcap = K;
@@ -404,6 +479,70 @@ hopf_status check_barrier(hopf_ctx* ctx) {
   return HOPF_OK;
 }
 
+// Digits of the tensor-core products in mixed precision (about 5e-12 of
+// |A||B| per product).
+constexpr int kTcDigits = 5;
+
+bool use_tc(const hopf_ctx* ctx, int m, int p) {
+  return ctx->p.precision == HOPF_MIXED && ctx->qr_method == HOPF_QR_TENSOR && hk::qr_tc_applies(m, p);
+}
+
+hopf_status tc_reserve(hopf_ctx* ctx, int m, int k) {
+  const size_t need = hk::qr_tc_scratch_bytes(m, k, kTcDigits);
+  if (need <= ctx->tcbytes) return HOPF_OK;
+  cudaFree(ctx->tcbuf);
+  ctx->tcbuf = nullptr;
+  ctx->tcbytes = 0;
+  CK(cudaMalloc(&ctx->tcbuf, need));
+  ctx->tcbytes = need;
+  return HOPF_OK;
+}
+
+// Profile hooks for the phases of the tensor-core QR (PhaseTimer).
+int pt_begin(void* user) { return prof_begin(static_cast<hopf_ctx*>(user)); }
+void pt_end(void* user, int slot, int cls, double flops, int nl) {
+  prof_end(static_cast<hopf_ctx*>(user), slot, cls, flops, 0.0, nl);
+}
+hk::PhaseTimer phase_timer(hopf_ctx* ctx, int cls_panel) {
+  hk::PhaseTimer pt;
+  pt.user = ctx;
+  pt.begin = pt_begin;
+  pt.end = pt_end;
+  pt.cls_panel = cls_panel;
+  pt.cls_tc = HOPF_K_TC;
+  pt.cls_small = HOPF_K_SMALL;
+  return pt;
+}
+
+// Householder QR of the m x k matrix A (lda) in place: in mixed precision
+// and for tall factors the blocked form with tensor-core products (G
+// receives its panel Grams), otherwise the cooperative kernel alone.
+hopf_status qr_factor(hopf_ctx* ctx, cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb, cplx* G) {
+  if (use_tc(ctx, m, std::min(m, k))) {
+    TRY(tc_reserve(ctx, m, k));
+    *nb = 32;
+    CK(hk::geqrf_tc(A, lda, m, k, tau, T, G, ctx->tcbuf, ctx->tcbytes, ctx->coop, kTcDigits, ctx->stream,
+                    phase_timer(ctx, HOPF_K_QR)));
+    return HOPF_OK;
+  }
+  LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1, hk::geqrf(A, lda, m, k, tau, T, nb, ctx->coop, ctx->stream, MIXED_FLAG));
+  return HOPF_OK;
+}
+
+// C <- Q C with the Q of qr_factor (same m and p = min(m, k)).
+hopf_status qr_apply(hopf_ctx* ctx, const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* T, int nb,
+                     const cplx* G, cplx* C, int ldc, int q) {
+  if (use_tc(ctx, m, p)) {
+    TRY(tc_reserve(ctx, m, q));
+    CK(hk::ormqr_tc(A, lda, m, p, tau, G, C, ldc, q, ctx->tcbuf, ctx->tcbytes, &ctx->coop.bar->err, kTcDigits,
+                    ctx->stream, phase_timer(ctx, HOPF_K_APPLYQ)));
+    return HOPF_OK;
+  }
+  LAUNCH(HOPF_K_APPLYQ, applyq_flops(m, q, p), 0, 1,
+         hk::ormqr(A, lda, m, p, tau, T, nb, C, ldc, q, ctx->coop, ctx->stream, MIXED_FLAG));
+  return HOPF_OK;
+}
+
 // Phase 1 of the rounding: right-to-left Householder LQ sweep (App. A,
 // Alg. 1 mirrored).  Reads the cores of t (unchanged), leaves B_c = the
 // factored H(Y_c)^H with its reflectors for c >= 1 and B_0 = V(Y_0 L_1)
@@ -419,7 +558,8 @@ hopf_status orth_sweep(hopf_ctx* ctx, const hopf_tt* t, std::vector<int>& p, std
   LAUNCH(HOPF_K_SUM, 0, 32.0 * r[d - 1] * n, 1, hk::conj_transpose(t->cores[d - 1], r[d - 1], r[d - 1], n, w.B[d - 1], n, ctx->stream));
   for (int c = d - 1; c >= 1; --c) {
     const int m = n * p[c + 1], k = r[c];
-    LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1, hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream, MIXED_FLAG));
+    TRY(qr_factor(ctx, w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c],
+                  w.G + (size_t)c * w.gstride));
     p[c] = std::min(m, k);
     // merge L_c = R_c^H into core c-1
     const int rl = r[c - 1];
@@ -459,13 +599,13 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     } else {
       const int mc = n * p[c + 1];
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::init_sh_pad(w.Sb, rho[c], rho[c], p[c], t->cores[c], mc, mc, ctx->stream));
-      LAUNCH(HOPF_K_APPLYQ, applyq_flops(mc, rho[c], p[c]), 0, 1, hk::ormqr(w.B[c], mc, mc, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c],
-                   t->cores[c], mc, rho[c], ctx->coop, ctx->stream, MIXED_FLAG));
+      TRY(qr_apply(ctx, w.B[c], mc, mc, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c],
+                   w.G + (size_t)c * w.gstride, t->cores[c], mc, rho[c]));
       LAUNCH(HOPF_K_SUM, 0, 32.0 * mc * rho[c], 1, hk::conj_transpose(t->cores[c], mc, mc, rho[c], w.W1, rho[c], ctx->stream));
       Z = w.W1;
     }
     int nb2 = 32;
-    LAUNCH(HOPF_K_QR, qr_flops(Mrows, cols), 0, 1, hk::geqrf(Z, Mrows, Mrows, cols, w.tau2, w.T2, &nb2, ctx->coop, ctx->stream, MIXED_FLAG));
+    TRY(qr_factor(ctx, Z, Mrows, Mrows, cols, w.tau2, w.T2, &nb2, w.G2));
     const int pp = std::min(Mrows, cols);
     LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::extract_r(Z, Mrows, pp, cols, w.Rb, pp, ctx->stream));
     const int forced_c = forced ? forced[c + 1] : 0;
@@ -543,7 +683,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     } else {
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::gather_u(w.Jb, pp, pp, w.perm, w.sig, 0, rnew, t->cores[c], Mrows, Mrows, w.Ub, pp, ctx->stream));
     }
-    LAUNCH(HOPF_K_APPLYQ, applyq_flops(Mrows, rnew, pp), 0, 1, hk::ormqr(Z, Mrows, Mrows, pp, w.tau2, w.T2, nb2, t->cores[c], Mrows, rnew, ctx->coop, ctx->stream, MIXED_FLAG));
+    TRY(qr_apply(ctx, Z, Mrows, Mrows, pp, w.tau2, w.T2, nb2, w.G2, t->cores[c], Mrows, rnew));
     // S = U_rho^H R (rho x cols)
     LAUNCH(HOPF_K_GEMM, 8.0 * rnew * pp * cols, 0, 1, hk::gemm_uh_r(w.Ub, pp, rnew, pp, w.Rb, pp, cols, w.Sb, rnew, ctx->stream));
   }
@@ -551,8 +691,8 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
   {
     const int c = d - 1;
     LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::init_sh_pad(w.Sb, rho[c], rho[c], p[c], w.W1, n, n, ctx->stream));
-    LAUNCH(HOPF_K_APPLYQ, applyq_flops(n, rho[c], p[c]), 0, 1, hk::ormqr(w.B[c], n, n, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c], w.W1, n, rho[c],
-                 ctx->coop, ctx->stream, MIXED_FLAG));
+    TRY(qr_apply(ctx, w.B[c], n, n, p[c], w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, nbv[c],
+                 w.G + (size_t)c * w.gstride, w.W1, n, rho[c]));
     LAUNCH(HOPF_K_SUM, 0, 32.0 * n * rho[c], 1, hk::conj_transpose(w.W1, n, n, rho[c], t->cores[c], rho[c], ctx->stream));
   }
   rho[d] = 1;
@@ -600,8 +740,8 @@ hopf_status orth_sweep_apply(hopf_ctx* ctx, const hopf_tt* X, std::vector<int>& 
   }
   for (int c = d - 1; c >= 1; --c) {
     const int m = n * p[c + 1], k = 6 * r[c];
-    LAUNCH(HOPF_K_QR, qr_flops(m, k), 0, 1,
-           hk::geqrf(w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c], ctx->coop, ctx->stream, MIXED_FLAG));
+    TRY(qr_factor(ctx, w.B[c], m, m, k, w.tau + (size_t)c * w.kcap, w.T + (size_t)c * w.tstride, &nbv[c],
+                  w.G + (size_t)c * w.gstride));
     p[c] = std::min(m, k);
     const int rl = r[c - 1];
     const size_t blk = (size_t)rl * n * p[c];
@@ -697,17 +837,23 @@ hopf_status copy_impl(hopf_ctx* ctx, const hopf_tt* src, hopf_tt* dst) {
   return sync_meta(ctx, dst);
 }
 
-hopf_status ensure_step_ws(hopf_ctx* ctx, int cap) {
-  if (ctx->big && ctx->big->cap_rank >= 6 * cap && ctx->kst[0]->cap_rank >= cap) return HOPF_OK;
+// Step workspace: `big` takes an operator output (6 x the input rank; the
+// midpoint scheme applies the operator to an untruncated sum of rank 2 cap),
+// `ytmp` the stage inputs (rank 2 cap for the midpoint's sum).
+hopf_status ensure_step_ws(hopf_ctx* ctx, int cap, int scheme) {
+  const int mult = (scheme == HOPF_MIDPOINT) ? 2 : 1;
+  if (ctx->big && ctx->big->cap_rank >= 6 * mult * cap && ctx->kst[0]->cap_rank >= cap &&
+      ctx->ytmp->cap_rank >= mult * cap)
+    return HOPF_OK;
   if (ctx->big) tt_free(ctx->big);
   for (auto& k : ctx->kst)
     if (k) tt_free(k);
   if (ctx->ytmp) tt_free(ctx->ytmp);
   ctx->big = ctx->ytmp = nullptr;
   for (auto& k : ctx->kst) k = nullptr;
-  TRY(tt_alloc(ctx, 6 * cap, &ctx->big));
+  TRY(tt_alloc(ctx, 6 * mult * cap, &ctx->big));
   for (auto& k : ctx->kst) TRY(tt_alloc(ctx, cap, &k));
-  TRY(tt_alloc(ctx, cap, &ctx->ytmp));
+  TRY(tt_alloc(ctx, mult * cap, &ctx->ytmp));
   return HOPF_OK;
 }
 
@@ -981,7 +1127,7 @@ hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out) {
     hopf_destroy(ctx);
     return st;
   };
-  if (dalloc(&ctx->d_coef, (size_t)15 * p->n) != cudaSuccess || dalloc(&ctx->d_blocks, 3 * 36) != cudaSuccess ||
+  if (dalloc(&ctx->d_coef, (size_t)3 * hk::kNumOps * p->n) != cudaSuccess || dalloc(&ctx->d_blocks, 3 * 36) != cudaSuccess ||
       dalloc(&ctx->d_agrid, p->n) != cudaSuccess || dalloc(&ctx->d_dbl, 16) != cudaSuccess ||
       dalloc(&ctx->d_int, 16) != cudaSuccess || dalloc(&ctx->coop.bar, 1) != cudaSuccess ||
       dalloc(&ctx->coop.pr, 1024) != cudaSuccess || dalloc(&ctx->coop.scal, 8) != cudaSuccess ||
@@ -992,7 +1138,7 @@ hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out) {
     return bad(HOPF_ENOMEM);
   if (cudaMemsetAsync(ctx->coop.bar, 0, sizeof(GridBar), ctx->stream) != cudaSuccess) return bad(HOPF_ECUDA);
   unsigned char tab[3][36];
-  mpo_tables(tab);
+  mpo_tables(tab, HOPF_EQ_PHI);
   if (cudaMemcpyAsync(ctx->d_blocks, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
     return bad(HOPF_ECUDA);
   if (ctx->L > 0.0 && build_ops(ctx) != HOPF_OK) return bad(HOPF_ECUDA);
@@ -1022,6 +1168,10 @@ void hopf_destroy(hopf_ctx* ctx) {
   cudaFree(w.W1); cudaFree(w.tau); cudaFree(w.T); cudaFree(w.tau2); cudaFree(w.T2);
   cudaFree(w.Rb); cudaFree(w.Mb); cudaFree(w.Jb); cudaFree(w.Ub); cudaFree(w.Sb);
   cudaFree(w.sig); cudaFree(w.perm);
+  cudaFree(w.bd_d); cudaFree(w.bd_e); cudaFree(w.bd_tauq); cudaFree(w.bd_taup); cudaFree(w.bd_a2);
+  cudaFree(w.bd_info); cudaFree(w.bd_X); cudaFree(w.bd_Zs);
+  cudaFree(w.G); cudaFree(w.G2);
+  cudaFree(ctx->tcbuf);
   cudaFree(ctx->coop.bar); cudaFree(ctx->coop.pr); cudaFree(ctx->coop.pc);
   cudaFree(ctx->coop.wfin); cudaFree(ctx->coop.scal); cudaFree(ctx->coop.counters);
   cudaFree(ctx->coop.colnorm); cudaFree(ctx->coop.colver); cudaFree(ctx->coop.pairchk);
@@ -1054,6 +1204,13 @@ hopf_status hopf_set_max_ctas(hopf_ctx* ctx, int max_ctas) {
   if (!ctx) return HOPF_EINVAL;
   if (max_ctas < 0) return fail(ctx, HOPF_EINVAL, "max_ctas must be >= 0");
   ctx->coop.max_ctas = max_ctas;
+  return HOPF_OK;
+}
+
+hopf_status hopf_set_qr_method(hopf_ctx* ctx, int method) {
+  if (!ctx) return HOPF_EINVAL;
+  if (method != HOPF_QR_DOUBLEFLOAT && method != HOPF_QR_TENSOR) return fail(ctx, HOPF_EINVAL, "unknown QR method %d", method);
+  ctx->qr_method = method;
   return HOPF_OK;
 }
 
@@ -1245,17 +1402,22 @@ hopf_status tt_norm(hopf_ctx* ctx, const hopf_tt* t, double* norm) {
   return HOPF_OK;
 }
 
-hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* f, double dt, int nsteps, double* disc_sum, int* rank_log,
-                      const int* forced_log) {
+// Roundings per step of each scheme (the layout of rank logs).
+int scheme_roundings(int scheme) { return scheme == HOPF_EULER ? 2 : scheme == HOPF_MIDPOINT ? 3 : 8; }
+
+hopf_status hopf_step_scheme(hopf_ctx* ctx, hopf_tt* f, int scheme, double dt, int nsteps, double* disc_sum,
+                             int* rank_log, const int* forced_log) {
   if (!ctx || !f) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_step: null argument") : HOPF_EINVAL;
   if (nsteps < 0 || !std::isfinite(dt)) return fail(ctx, HOPF_EINVAL, "hopf_step: bad dt or nsteps");
+  if (scheme != HOPF_RK4 && scheme != HOPF_EULER && scheme != HOPF_MIDPOINT)
+    return fail(ctx, HOPF_EINVAL, "hopf_step: unknown scheme %d", scheme);
   if (!(ctx->L > 0.0)) return fail(ctx, HOPF_EINVAL, "L is not set (hopf_set_L or hopf_init_gaussian)");
   const int cap = ctx->p.rank_cap;
   const double tol = ctx->p.tol;
   if (f->cap_rank < cap) return fail(ctx, HOPF_EINVAL, "hopf_step: the state needs capacity >= rank_cap");
   for (int k = 0; k <= f->d; ++k)
     if (f->ranks[k] > cap) return fail(ctx, HOPF_EINVAL, "hopf_step: input rank %d exceeds rank_cap", f->ranks[k]);
-  TRY(ensure_step_ws(ctx, cap));
+  TRY(ensure_step_ws(ctx, cap, scheme));
   hopf_tt* big = ctx->big;
   hopf_tt** K = ctx->kst;
   hopf_tt* Y = ctx->ytmp;
@@ -1289,6 +1451,26 @@ hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* f, double dt, int nsteps, double* 
   for (int s = 0; s < nsteps; ++s) {
     const hopf_tt* tm[5];
     double cf[10] = {0};
+    if (scheme == HOPF_EULER) {
+      // f <- T_r[f + dt T_s[G f]]  (Eq. adaptive-euler-method)
+      TRY(TG(f, K[0]));
+      tm[0] = f; tm[1] = K[0]; cf[0] = 1.0; cf[2] = dt;
+      TRY(sum_impl(ctx, 2, tm, cf, big));
+      TRY(T(big, f));
+      continue;
+    }
+    if (scheme == HOPF_MIDPOINT) {
+      // f <- T_a[f + dt T_b[G(f + dt/2 T_c[G f])]]  (Eq. adaptive-midpoint-method;
+      // the inner sum is not truncated)
+      TRY(TG(f, K[0]));
+      tm[0] = f; tm[1] = K[0]; cf[0] = 1.0; cf[2] = 0.5 * dt;
+      TRY(sum_impl(ctx, 2, tm, cf, Y));
+      TRY(TG(Y, K[1]));
+      tm[1] = K[1]; cf[2] = dt;
+      TRY(sum_impl(ctx, 2, tm, cf, big));
+      TRY(T(big, f));
+      continue;
+    }
     // K1 = T[G f]
     TRY(TG(f, K[0]));
     // Y2 = T[f + dt/2 K1]; K2 = T[G Y2]
@@ -1317,6 +1499,62 @@ hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* f, double dt, int nsteps, double* 
   return capped ? HOPF_ERANKCAP : HOPF_OK;
 }
 
+hopf_status hopf_step(hopf_ctx* ctx, hopf_tt* f, double dt, int nsteps, double* disc_sum, int* rank_log,
+                      const int* forced_log) {
+  return hopf_step_scheme(ctx, f, HOPF_RK4, dt, nsteps, disc_sum, rank_log, forced_log);
+}
+
+hopf_status hopf_set_equation(hopf_ctx* ctx, int equation, double box) {
+  if (!ctx) return HOPF_EINVAL;
+  if (equation != HOPF_EQ_PHI && equation != HOPF_EQ_CDF) return fail(ctx, HOPF_EINVAL, "unknown equation %d", equation);
+  if (!(box >= 0.0) || !std::isfinite(box)) return fail(ctx, HOPF_EINVAL, "box half-width must be >= 0");
+  if (equation == HOPF_EQ_CDF && !(box > 0.0)) return fail(ctx, HOPF_EINVAL, "the CDF equation needs a box half-width > 0");
+  ctx->equation = equation;
+  ctx->L = box;
+  unsigned char tab[3][36];
+  mpo_tables(tab, equation);
+  CK(cudaMemcpyAsync(ctx->d_blocks, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream));
+  if (box > 0.0) TRY(build_ops(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HOPF_OK;
+}
+
+hopf_status hopf_init_cdf(hopf_ctx* ctx, double sigma, const double* mu, hopf_tt** out) {
+  if (!ctx || !out) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_init_cdf: null argument") : HOPF_EINVAL;
+  if (ctx->equation != HOPF_EQ_CDF) return fail(ctx, HOPF_EINVAL, "hopf_init_cdf: the context is not set to the CDF equation");
+  if (!(sigma > 0.0)) return fail(ctx, HOPF_EINVAL, "hopf_init_cdf: sigma must be > 0");
+  const int d = ctx->p.d, n = ctx->p.n;
+  std::vector<double> host((size_t)2 * n * d);
+  for (int k = 0; k < d; ++k)
+    for (int i = 0; i < n; ++i) {
+      const double m = mu ? mu[k] : 0.0;
+      host[2 * ((size_t)k * n + i)] = 0.5 * (1.0 + std::erf((ctx->agrid[i] - m) / (sigma * std::sqrt(2.0))));
+      host[2 * ((size_t)k * n + i) + 1] = 0.0;
+    }
+  std::vector<int> ranks(d + 1, 1);
+  hopf_tt* t = nullptr;
+  TRY(tt_alloc(ctx, ctx->p.rank_cap, &t));
+  size_t off = 0;
+  for (int k = 0; k < d; ++k) {
+    cudaError_t e = cudaMemcpyAsync(t->cores[k], host.data() + 2 * off, (size_t)n * sizeof(cplx), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e != cudaSuccess) {
+      tt_free(t);
+      return fail(ctx, HOPF_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    off += n;
+  }
+  t->ranks = ranks;
+  hopf_status st = sync_meta(ctx, t);
+  if (st == HOPF_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, HOPF_ECUDA, "upload failed");
+  if (st != HOPF_OK) {
+    tt_free(t);
+    return st;
+  }
+  *out = t;
+  return HOPF_OK;
+}
+
 hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts, const int* idx, double* vals) {
   if (!ctx || !t || (npts > 0 && (!idx || !vals)) || npts < 0)
     return ctx ? fail(ctx, HOPF_EINVAL, "hopf_eval_points: bad arguments") : HOPF_EINVAL;
@@ -1343,6 +1581,7 @@ hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts, const in
 hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean, double* cov, double* imag_resid) {
   if (!ctx || !t || !mean || !cov) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_eval_moments: null argument") : HOPF_EINVAL;
   if (!(ctx->L > 0.0)) return fail(ctx, HOPF_EINVAL, "L is not set");
+  if (ctx->equation != HOPF_EQ_PHI) return fail(ctx, HOPF_EINVAL, "hopf_eval_moments: moments come from Phi, not a CDF");
   const int d = t->d, n = t->n, c = n / 2;
   const int npts = 1 + 2 * d + 2 * d * (d - 1);
   std::vector<int> idx((size_t)npts * d, c);
@@ -1386,6 +1625,7 @@ hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean, dou
 
 hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0, const double* C0, hopf_tt** out) {
   if (!ctx || !m0 || !C0 || !out) return ctx ? fail(ctx, HOPF_EINVAL, "hopf_init_gaussian: null argument") : HOPF_EINVAL;
+  if (ctx->equation != HOPF_EQ_PHI) return fail(ctx, HOPF_EINVAL, "hopf_init_gaussian: the context is set to the CDF equation");
   const int d = ctx->p.d, n = ctx->p.n;
   bool diag = true;
   double minc = 1e300;
@@ -1479,6 +1719,45 @@ hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0, const double* C0
   }
   *out = t;
   return capped ? HOPF_ERANKCAP : HOPF_OK;
+}
+
+hopf_status hopf_tc_zgemm(hopf_ctx* ctx, int M, int N, int K, const double* A, int lda, int opA, const double* B,
+                          int ldb, int opB, int digits, double* C, int ldc) {
+  if (!ctx) return HOPF_EINVAL;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (opA != 0 && opA != 1) || (opB != 0 && opB != 1) ||
+      digits < 1 || digits > hk::tc_max_digits() || ldc < M || lda < (opA ? K : M) || ldb < (opB ? N : K))
+    return fail(ctx, HOPF_EINVAL, "hopf_tc_zgemm: bad arguments");
+  const size_t na = (size_t)lda * (opA ? M : K), nb = (size_t)ldb * (opB ? K : N), nc = (size_t)ldc * N;
+  const int Kc = hk::tc_chunk();
+  const size_t oa = hk::tc_operand_bytes(M, K, digits, Kc), ob = hk::tc_operand_bytes(N, K, digits, Kc);
+  const size_t np = hk::tc_part_elems(M, N, K);
+  cplx *dA = nullptr, *dB = nullptr, *dC = nullptr, *dP = nullptr;
+  unsigned char *bufA = nullptr, *bufB = nullptr;
+  auto release = [&]() {
+    cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(dP); cudaFree(bufA); cudaFree(bufB);
+  };
+  if (dalloc(&dA, na) != cudaSuccess || dalloc(&dB, nb) != cudaSuccess || dalloc(&dC, nc) != cudaSuccess ||
+      dalloc(&dP, np) != cudaSuccess || dalloc(&bufA, oa) != cudaSuccess || dalloc(&bufB, ob) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(ctx, HOPF_ENOMEM, "hopf_tc_zgemm: allocation failed");
+  }
+  // op(A)(m, k): A[m + lda k] or conj(A[k + lda m]); B operand rows are the
+  // columns n of op(B): op(B)(k, n) = B[k + ldb n] or conj(B[n + ldb k])
+  hk::TcOperandView va{dA, opA ? (long long)lda : 1, opA ? 1 : (long long)lda, M, K, opA, 0, 0};
+  hk::TcOperandView vb{dB, opB ? 1 : (long long)ldb, opB ? (long long)ldb : 1, N, K, opB, 0, 0};
+  hk::TcOperand oA, oB;
+  cudaError_t e = cudaMemcpyAsync(dA, A, na * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dB, B, nb * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = hk::tc_split(va, digits, &oA, bufA, ctx->stream);
+  if (e == cudaSuccess) e = hk::tc_split(vb, digits, &oB, bufB, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dC, 0, nc * sizeof(cplx), ctx->stream);
+  if (e == cudaSuccess) e = hk::tc_zgemm(oA, oB, dC, ldc, 1.0, 0, dP, np, &ctx->coop.bar->err, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, nc * sizeof(cplx), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  release();
+  if (e != cudaSuccess) return fail(ctx, HOPF_ECUDA, "hopf_tc_zgemm: %s", cudaGetErrorString(e));
+  return check_barrier(ctx);
 }
 
 hopf_status hopf_step_ensemble(int count, hopf_ctx* const* ctxs, hopf_tt* const* tts, const double* dt,

@@ -148,12 +148,30 @@ cudaError_t gemm_uh_r(const cplx* U, int ldu, int M, int K, const cplx* R, int l
 
 // ---- TT-level kernels -------------------------------------------------------------
 struct OpTable {
-  // Tridiagonal coefficients (lo, di, up) of the per-mode operators
-  // I, A, P, Q, Z (index op*3*n + {0,n,2n} + i), complex.
+  // Coefficients (lo, di, up) of the per-mode operators in slots
+  // I, A, P, Q, Z, K (index op*3*n + {0,n,2n} + i), complex (op_apply).
   cplx* coef;
   int n;
 };
-enum { OP_I = 0, OP_A = 1, OP_P = 2, OP_Q = 3, OP_Z = 4, OP_NONE = 7 };
+enum { OP_I = 0, OP_A = 1, OP_P = 2, OP_Q = 3, OP_Z = 4, OP_K = 5, OP_NONE = 7 };
+constexpr int kNumOps = 6;  // slots of the coefficient table
+// (op x)[m] for the fiber x (stride s): a tridiagonal operator from its
+// coefficients (lo, di, up) at coef + op * 3n; OP_K, the CDF equation's
+// u - (trapezoidal integral from the lower edge), is di[m] x_m minus
+// du (x_0 / 2 + x_1 + ... + x_{m-1} + x_m / 2), du stored in lo[0].
+DV cplx op_apply(const cplx* coef, int op, int n, const cplx* x, size_t s, int m) {
+  const cplx* cf = coef + (size_t)op * 3 * n;
+  cplx v = cmul(cf[n + m], x[s * m]);
+  if (op == OP_K) {
+    cplx acc = mk(0, 0);
+    for (int q = 0; q <= m; ++q) acc = cadd(acc, x[s * q]);
+    acc = csub(acc, cscale(cadd(x[0], x[s * m]), 0.5));
+    return csub(v, cscale(acc, cf[0].x));
+  }
+  if (m > 0) v = cfma(cf[m], x[s * (m - 1)], v);
+  if (m + 1 < n) v = cfma(cf[2 * n + m], x[s * (m + 1)], v);
+  return v;
+}
 // Operator blocks applied along the middle index and summed over beta:
 // out(alpha, i, m, q) = sum_{beta < Bn} W[alpha*Ar + beta](T_beta[i, :, q])[m].
 // mode 0: V layout, mode 1: conj-transposed H^H layout with leading dim ldo.
@@ -203,5 +221,70 @@ cudaError_t moments_combine(const cplx* vals, int d, double da, double* mean, do
                             double* imag_resid, cudaStream_t s);
 // Any non-finite value in x[count]? sets *flag = 1.
 cudaError_t check_finite(const cplx* x, size_t count, int* flag, cudaStream_t s);
+
+
+// ---- complex products on the tensor cores (tc.cu) ---------------------------
+// Logical R x K operand: element (r, k) = X[r * rs + k * ks] (conjugated if
+// conj).  tri_mode 1: zero where r > k + tri (upper trapezoid); 2: rows are
+// Householder reflectors s and columns their entries i, zero where
+// k < r + tri, one where k == r + tri; 3: the same reflectors with rows i and
+// columns s (zero where r < k + tri, one where r == k + tri).
+struct TcOperandView {
+  const cplx* X;
+  long long rs, ks;
+  int R, K, conj;
+  int tri_mode, tri;
+};
+// Digit planes of an operand split for the tensor cores: 3 components
+// (re, im, re + im) x S digits, each R x ldk BF16 (K contiguous), and the
+// per-(component, K-chunk, row) power-of-two exponents.
+struct TcOperand {
+  void* planes;
+  int* e;
+  int R, K, S;
+  long long ldk;
+  int nchunks;
+};
+// Bytes of device memory an operand's digits take (planes + exponents).
+size_t tc_operand_bytes(int R, int K, int S, int Kc);
+int tc_chunk();       // K-chunk with exact FP32 accumulation (192)
+int tc_max_digits();  // 5
+// Splits the operand into S digit planes in `buf` (tc_operand_bytes).
+cudaError_t tc_split(const TcOperandView& v, int S, TcOperand* out, void* buf, cudaStream_t s);
+// out (M x N, column-major, ldo) = alpha * A B^T (+ out if accumulate), with
+// A (M x K) and B (N x K) split operands, i.e. out[m, n] =
+// alpha sum_k A(m, k) B(n, k).  K beyond one chunk: per-chunk partials in
+// part (tc_part_elems), summed in a fixed order.  err: expiry record.
+cudaError_t tc_zgemm(const TcOperand& A, const TcOperand& B, cplx* out, long long ldo, double alpha, int accumulate,
+                     cplx* part, size_t part_elems, int* err, cudaStream_t s);
+size_t tc_part_elems(int M, int N, int K);
+
+// ---- blocked QR / Q application with tensor-core products (qrtc.cu) -------
+// Optional per-phase timing: begin() before a phase's launches returns a
+// slot, end() after them records the phase under a profile class (the
+// caller's class numbering) with its algorithmic FLOPs.
+struct PhaseTimer {
+  void* user = nullptr;
+  int (*begin)(void* user) = nullptr;
+  void (*end)(void* user, int slot, int cls, double flops, int nlaunch) = nullptr;
+  int cls_panel = 0, cls_tc = 0, cls_small = 0;
+  int b() const { return begin ? begin(user) : -1; }
+  void e(int slot, int cls, double flops, int nl) const {
+    if (end) end(user, slot, cls, flops, nl);
+  }
+};
+// Used by the mixed-precision rounding for tall factors (qr_tc_applies).
+int tc_outer_panel();                                   // 128
+bool qr_tc_applies(int m, int p);                       // m rows, p = min(m, k) reflectors
+size_t qr_tc_scratch_bytes(int m, int k, int S);        // scratch of one call
+size_t qr_tc_gram_elems(int k);                         // complex elements of Gout
+// As geqrf (mixed), plus Gout: per outer panel j the Gram v_s^H v_u of its
+// reflectors (128 x 128 block at Gout + j 128^2, leading dimension 128),
+// which ormqr_tc needs.  T receives the inner panels' records as geqrf.
+cudaError_t geqrf_tc(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, cplx* Gout, void* scratch,
+                     size_t scratch_bytes, const CoopWs& cws, int S, cudaStream_t s, const PhaseTimer& pt);
+// C <- Q C for the Q of geqrf_tc (p reflectors).
+cudaError_t ormqr_tc(const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* Gin, cplx* C, int ldc, int q,
+                     void* scratch, size_t scratch_bytes, int* err, int S, cudaStream_t s, const PhaseTimer& pt);
 
 }  // namespace hk

@@ -48,7 +48,8 @@ static inline int nblk(size_t n, int t) { return (int)((n + t - 1) / t); }
 
 // ---- operator apply ------------------------------------------------------------
 // Y[(alpha, i), m, (beta, j)] = sum_m' W[alpha, beta][m, m'] X[i, m', j] with
-// every W block tridiagonal in (m, m'): one of I, A, P, Q, Z.  One thread per
+// every W block one of the per-mode operators (op_apply): tridiagonal in
+// (m, m'), or the CDF equation's cumulative K.  One thread per
 // output element, consecutive threads along the fastest (left-rank) index, so
 // loads of X and stores of Y are both coalesced 16-byte accesses.
 __global__ void apply_core_kernel(const cplx* __restrict__ X, int a, int n, int c,
@@ -67,13 +68,7 @@ __global__ void apply_core_kernel(const cplx* __restrict__ X, int a, int n, int 
     const int be = (int)(q / c), j = (int)(q % c);
     const int op = blocks[al * Ar + be];
     cplx v = mk(0, 0);
-    if (op != OP_NONE) {
-      const cplx* cf = coef + (size_t)op * 3 * n;
-      const cplx* x = X + i + (size_t)a * n * j;  // X[i, :, j] with stride a
-      v = cmul(cf[n + m], x[(size_t)a * m]);
-      if (m > 0) v = cfma(cf[m], x[(size_t)a * (m - 1)], v);
-      if (m + 1 < n) v = cfma(cf[2 * n + m], x[(size_t)a * (m + 1)], v);
-    }
+    if (op != OP_NONE) v = op_apply(coef, op, n, X + i + (size_t)a * n * j, (size_t)a, m);  // X[i, :, j], stride a
     Y[e] = v;
   }
 }
@@ -672,11 +667,7 @@ __global__ void stencil_combine_kernel(const cplx* __restrict__ T, int r, int n,
     for (int be = 0; be < Bn; ++be) {
       const int op = blocks[al * Ar + be];
       if (op == OP_NONE) continue;
-      const cplx* cf = coef + (size_t)op * 3 * n;
-      const cplx* x = T + blk * be + i + (size_t)r * n * q;  // T_beta[i, :, q], stride r
-      v = cfma(cf[n + m], x[(size_t)r * m], v);
-      if (m > 0) v = cfma(cf[m], x[(size_t)r * (m - 1)], v);
-      if (m + 1 < n) v = cfma(cf[2 * n + m], x[(size_t)r * (m + 1)], v);
+      v = cadd(v, op_apply(coef, op, n, T + blk * be + i + (size_t)r * n * q, (size_t)r, m));  // T_beta[i, :, q]
     }
     if (mode == 0) out[e] = v;
     else out[(size_t)(m + (size_t)n * q) + (size_t)ldo * pr] = cconj(v);

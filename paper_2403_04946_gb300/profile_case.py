@@ -5,7 +5,7 @@ operator apply (hopf_apply_op) and one rounding (tt_round) at rank 6r, plus
 one fused hopf_step when --step is given.  Sized by --d/--n/--r so a capture
 stays small (d=4, n=128, r=64 holds about 2.5 GB on the device).
 
-  python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64 [--mixed]
+  python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64 [--mixed [--tensor]] [--profile]
 
 With --surrogate it instead runs the surrogate network alone on seeded
 synthetic data (26 -> 256 x 4 -> 14, 4 members): 20 training steps of batch
@@ -34,6 +34,8 @@ def main():
     ap.add_argument("--step", action="store_true")
     ap.add_argument("--mixed", action="store_true", help="HOPF_MIXED precision")
     ap.add_argument("--surrogate", action="store_true", help="the surrogate network only")
+    ap.add_argument("--profile", action="store_true", help="print the per-class profile record")
+    ap.add_argument("--tensor", action="store_true", help="mixed precision with the tensor-core QR")
     args = ap.parse_args()
     from paper_2403_04946_gb300 import binding
     import synthetic
@@ -44,20 +46,35 @@ def main():
     cores, _ = synthetic.saturated_tt_cores(args.d, args.n, args.r, seed=0)
     ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r, L=12.4,
                           precision=binding.HOPF_MIXED if args.mixed else binding.HOPF_FP64)
+    if args.tensor:
+        ctx.hopf_set_qr_method(binding.HOPF_QR_TENSOR)
     t = ctx.tt_from_host(cores, max_rank=args.r)
     big = ctx.tt_create(6 * args.r)
+    if args.profile:
+        ctx.hopf_profile_enable(True)
     t0 = time.time()
     ctx.hopf_apply_op(t, big)
     disc, _ = ctx.tt_round(big, args.tol, args.r)
     print(f"apply+round d={args.d} n={args.n} r={args.r}: {time.time() - t0:.3f} s, "
           f"ranks {ctx.tt_get_ranks(big)}, discarded {disc:.3e}")
+    if args.profile:
+        print_profile(ctx.hopf_profile_read(reset=True))
     if args.step:
         t0 = time.time()
         ctx.hopf_step(t, 1.2e-5, 1)
         print(f"hopf_step: {time.time() - t0:.3f} s")
+        if args.profile:
+            print_profile(ctx.hopf_profile_read(reset=True))
     ctx.tt_free(big)
     ctx.tt_free(t)
     ctx.close()
+
+
+def print_profile(prof):
+    for k, v in prof.items():
+        if isinstance(v, dict) and v.get("launches", 0):
+            rate = v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 and v["flops"] > 0 else 0.0
+            print(f"  {k:8s} {v['ms']:10.2f} ms  {v['launches']:6d} launches  {rate:8.3f} TFLOP/s")
 
 
 def surrogate_case(binding, synthetic):

@@ -104,7 +104,7 @@ def test_c3_slice_apply_and_exact_rounding(B, c3_slice):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tensor"])
 def test_c3_slice_truncation_at_planted_gap(B, precision):
     """A rank-64 state of norm 1 plus a perturbation of norm 1e-9 and ranks
     320, so the flattenings are 49152 x 384 as in C3 and the tolerance puts
@@ -119,9 +119,11 @@ def test_c3_slice_truncation_at_planted_gap(B, precision):
     assert tt.ranks(x) == [1, 384, 384, 384, 1]
     want, wranks, wdisc = tt.round_tt(x, TOL3, R)
     assert wranks == [1, 64, 64, 64, 1]
-    mixed = precision == "mixed"
+    mixed = precision.startswith("mixed")
     ctx = B.Context(d=D, n=N, nu=NU3, tol=TOL3, rank_cap=R, L=L3,
                     precision=B.HOPF_MIXED if mixed else B.HOPF_FP64)
+    if precision == "mixed-tensor":
+        ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR)
     t = ctx.tt_from_host(x, max_rank=384)
     disc, _ = ctx.tt_round(t, TOL3, R)
     assert ctx.tt_get_ranks(t) == wranks
@@ -136,7 +138,7 @@ def test_c3_slice_truncation_at_planted_gap(B, precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tensor"])
 def test_c3_slice_rk4_step(B, c3_slice, c3_step_oracle, precision):
     """One fused hopf_step of the saturated C3 slice (dt = 1.2e-5, tol 1e-7,
     cap 64) with the oracle's ranks replayed: four K-roundings of 384-rank
@@ -145,9 +147,11 @@ def test_c3_slice_rk4_step(B, c3_slice, c3_step_oracle, precision):
     covariance."""
     x = c3_slice[0]
     want, log = c3_step_oracle
-    mixed = precision == "mixed"
+    mixed = precision.startswith("mixed")
     ctx = B.Context(d=D, n=N, nu=NU3, tol=TOL3, rank_cap=R, L=L3,
                     precision=B.HOPF_MIXED if mixed else B.HOPF_FP64)
+    if precision == "mixed-tensor":
+        ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR)
     t = ctx.tt_from_host(x, max_rank=R)
     out = ctx.hopf_step(t, DT3, 1, record=True, replay=log)
     assert np.array_equal(out["ranks"], log)
@@ -229,3 +233,31 @@ def test_c2_linear_against_closed_form_ladder(B):
     print(f"\nC2 linear vs closed form: max err n=64 {errs[0]:.2e}, n=128 {errs[1]:.2e}, ratio {errs[0] / errs[1]:.2f}")
     assert errs[0] < 3e-4
     assert 3.0 < errs[0] / errs[1] < 6.0
+
+
+def test_mixed_tensor_core_qr_ragged_panels(B):
+    """Mixed precision takes the blocked QR with tensor-core products for
+    factors of at least 4096 rows.  Ranks [1, 64, 200, 64, 1] at n = 64 give
+    a 4096 x 200 factor (outer panels of 128 and 72 columns), a 12800 x 64
+    one (a single panel) and the matching Q applications; at tol = 0 with
+    the oracle's ranks the rounding reproduces the tensor.  Bar: 5-digit
+    products are exact to about 3e-12 of |A||B|, and the blocked
+    factorisation with its compact-WY Gram amplifies that about a hundred
+    times, as it does the double-float arithmetic's 2^-48 (1.6e-13 on the
+    C3 slice): 1e-8 leaves a factor of ten."""
+    d, n = 4, 64
+    x = synthetic.random_tt_cores(d, n, [1, 64, 200, 64, 1], seed=31)
+    want, wranks, _ = tt.round_tt(x, 0.0, 1000)
+    assert wranks == [1, 64, 200, 64, 1]
+    ctx = B.Context(d=d, n=n, nu=0.02, tol=0.0, rank_cap=200, L=4.0, precision=B.HOPF_MIXED)
+    ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR)
+    t = ctx.tt_from_host(x, max_rank=200)
+    ctx.tt_round(t, 0.0, 200, forced_ranks=wranks)
+    got = ctx.tt_to_host(t)
+    e, e_in = rel_tt(got, want), rel_tt(got, x)
+    print(f"\nmixed tensor-core QR, ragged panels: vs oracle {e:.2e}, vs input {e_in:.2e}")
+    assert e < 1e-8 and e_in < 1e-8
+    for C in got[:-1]:
+        V = tt.V(C)
+        assert np.abs(V.conj().T @ V - np.eye(V.shape[1])).max() < 1e-8
+    ctx.close()
