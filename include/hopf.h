@@ -25,7 +25,8 @@
  *    cudaStream_t, e.g. PyTorch's current stream; NULL = legacy default
  *    stream).  Calls that return host data synchronise that stream.
  *  - The library allocates and owns all device memory it uses (contexts,
- *    tensors, workspaces) and frees it in hopf_destroy / tt_free.  Host
+ *    tensors, workspaces; through the caller's allocator if one is set,
+ *    hopf_set_allocator) and frees it in hopf_destroy / tt_free.  Host
  *    arrays passed in are read during the call only; host output arrays
  *    are caller-owned and written before the call returns.
  *  - Every call returns a hopf_status; nothing aborts.  On an error the
@@ -79,6 +80,24 @@ typedef struct {
 
 /* ---- context ------------------------------------------------------------ */
 
+/* Device memory.  By default the library allocates with cudaMalloc and
+ * releases with cudaFree.  hopf_set_allocator routes every device
+ * allocation of the library (contexts, tensors, workspaces, networks)
+ * through the caller's functions instead, e.g. a framework's caching
+ * allocator, so that the solver's memory is accounted and reused with the
+ * rest of the process's.  alloc(bytes, user) returns a device pointer
+ * aligned to at least 256 bytes, or NULL when it cannot serve the request
+ * (the calling entry point then returns HOPF_ENOMEM and leaves its objects
+ * valid); free(ptr, user) releases a pointer alloc returned.  Both NULL
+ * restores cudaMalloc / cudaFree.  The allocator can change only while no
+ * context, tensor or network exists (so that every pointer is released by
+ * the functions that allocated it): HOPF_EINVAL otherwise, or when exactly
+ * one of the two functions is NULL.  Pinned host staging buffers are not
+ * affected. */
+typedef void* (*hopf_alloc_fn)(size_t bytes, void* user);
+typedef void (*hopf_free_fn)(void* ptr, void* user);
+hopf_status hopf_set_allocator(hopf_alloc_fn alloc, hopf_free_fn free, void* user);
+
 /* Creates a context bound to `stream` (cudaStream_t or NULL) on the current
  * device.  `p` is copied.  Errors: HOPF_EINVAL (d < 3 or > 64, n < 4 or odd,
  * rank_cap < 1, tol < 0, unknown precision), HOPF_ENOMEM, HOPF_ECUDA. */
@@ -102,6 +121,21 @@ hopf_status hopf_set_nu(hopf_ctx* ctx, double nu);
  * truncation up to rounding.  Errors: HOPF_EINVAL (unknown method). */
 enum { HOPF_SVD_AUTO = 0, HOPF_SVD_JACOBI = 1 };
 hopf_status hopf_set_svd_method(hopf_ctx* ctx, int method);
+/* Limit of the bounded device-side waits of this context's cooperative
+ * kernels (the grid barriers of the QR, Q application, SVD and cross
+ * kernels): a wait longer than the limit records an expiry, every CTA of
+ * the launch leaves, and the call returns HOPF_ETIMEOUT (the context stays
+ * usable; the tensors involved have unspecified contents).  seconds in
+ * (0, 60]; 0 restores the default of 4 s.  A short limit also serves to
+ * check a caller's handling of the expiry path without a fault.  Errors:
+ * HOPF_EINVAL (out of range). */
+hopf_status hopf_set_wait_limit(hopf_ctx* ctx, double seconds);
+/* Exercises the expiry path: launches a two-CTA cooperative kernel whose
+ * grid barrier cannot complete (one CTA never arrives), so the other's
+ * bounded wait runs out after the context's wait limit.  Returns
+ * HOPF_ETIMEOUT when the watchdog works (the context stays usable), or a
+ * CUDA error.  Nothing faults; the call blocks for the wait limit. */
+hopf_status hopf_check_watchdog(hopf_ctx* ctx);
 /* How the mixed-precision rounding factors its tall flattenings (QR of
  * n p x K matrices, App. A Alg. 1/2; in HOPF_FP64 every QR is FP64).
  * HOPF_QR_DOUBLEFLOAT (the default): one cooperative Householder kernel in
@@ -271,7 +305,8 @@ hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean,
                               double* cov, double* imag_resid);
 
 /* Phi at npts grid multi-indices idx (host [npts*d], row-major, each in
- * [0, n)).  vals: host [2*npts] complex. */
+ * [0, n)).  vals: host [2*npts] complex.  Device staging is kept by the
+ * context between calls (grown to the largest request). */
 hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts,
                              const int* idx, double* vals);
 
@@ -301,6 +336,18 @@ hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts,
 #define HOPF_NOALLOC_MAX_POINTS 2048
 #define HOPF_NOALLOC_MAX_D 64
 hopf_status hopf_eval_points_noalloc(const hopf_tt* t, int npts, const int* idx, double* vals);
+
+/* Checkpoint and resume.  tt_save writes the TT (d, n, ranks, the cores in
+ * the layout above as FP64) and a time stamp to `path` in this machine's
+ * byte order: 8 bytes "HOPFTT\0\1", int32 d, int32 n, int32 ranks[d+1],
+ * double time, then 2 sum_k r_{k-1} n r_k doubles.  tt_load reads such a
+ * file into a new tensor of ctx (capacity max(max_rank, largest rank)) and
+ * its time stamp into *time (may be NULL).  The kernels reduce in a fixed
+ * order, so stepping a loaded tensor gives bitwise the same result as
+ * stepping the saved one.  Errors: HOPF_EINVAL (cannot open or write, not
+ * such a file, another d or n), HOPF_ENOMEM, HOPF_ECUDA. */
+hopf_status tt_save(const hopf_tt* t, const char* path, double time);
+hopf_status tt_load(hopf_ctx* ctx, const char* path, int max_rank, hopf_tt** out, double* time);
 
 /* ||t||_F (by orthogonalisation, computed on the device). */
 hopf_status tt_norm(hopf_ctx* ctx, const hopf_tt* t, double* norm);

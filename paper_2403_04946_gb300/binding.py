@@ -41,6 +41,11 @@ SIGNATURES = {
     "hopf_set_nu": (_i, [_vp, _d]),
     "hopf_set_svd_method": (_i, [_vp, _i]),
     "hopf_set_qr_method": (_i, [_vp, _i]),
+    "hopf_set_wait_limit": (_i, [_vp, _d]),
+    "hopf_check_watchdog": (_i, [_vp]),
+    "hopf_set_allocator": (_i, [_vp, _vp, _vp]),
+    "tt_save": (_i, [_vp, C.c_char_p, _d]),
+    "tt_load": (_i, [_vp, C.c_char_p, _i, C.POINTER(_vp), _pd]),
     "hopf_set_max_ctas": (_i, [_vp, _i]),
     "hopf_step_ensemble": (_i, [_i, _vp, _vp, _vp, _i, _vp]),
     "hopf_cell_moments": (_i, [_vp, _i, _pd, _pd, _d, _d, _pd, _pd]),
@@ -78,6 +83,29 @@ SIGNATURES = {
 }
 
 KERNEL_CLASSES = ["qr", "apply_q", "svd", "apply", "gemm", "sum", "small", "tc"]
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_allocator_keepalive = []
+
+
+def hopf_set_allocator(alloc=None, free=None):
+    """Route the library's device allocations through alloc(bytes) -> int
+    pointer (0 on failure) and free(ptr); both None restores cudaMalloc.
+    Only while no context, tensor or network exists (else HopfError)."""
+    lib = load()
+    if alloc is None and free is None:
+        st = lib.hopf_set_allocator(None, None, None)
+        if st != HOPF_OK:
+            raise HopfError(st, "hopf_set_allocator: objects are alive")
+        _allocator_keepalive.clear()
+        return
+    fa = ALLOC_FN(lambda nbytes, user: alloc(nbytes) or None)
+    ff = FREE_FN(lambda ptr, user: free(ptr))
+    st = lib.hopf_set_allocator(C.cast(fa, C.c_void_p), C.cast(ff, C.c_void_p), None)
+    if st != HOPF_OK:
+        raise HopfError(st, "hopf_set_allocator: objects are alive or a function is missing")
+    _allocator_keepalive[:] = [fa, ff]
 
 
 class HopfProfile(C.Structure):
@@ -198,6 +226,22 @@ class Context:
 
     def hopf_set_max_ctas(self, max_ctas):
         self._check(self.lib.hopf_set_max_ctas(self.h, int(max_ctas)))
+
+    def hopf_set_wait_limit(self, seconds):
+        self._check(self.lib.hopf_set_wait_limit(self.h, float(seconds)))
+
+    def hopf_check_watchdog(self):
+        """Status of the watchdog check (HOPF_ETIMEOUT when it works)."""
+        return self.lib.hopf_check_watchdog(self.h)
+
+    def tt_save(self, t, path, time=0.0):
+        self._check(self.lib.tt_save(t, str(path).encode(), float(time)))
+
+    def tt_load(self, path, max_rank=0):
+        h = C.c_void_p()
+        tm = C.c_double()
+        self._check(self.lib.tt_load(self.h, str(path).encode(), int(max_rank), C.byref(h), C.byref(tm)))
+        return h, tm.value
 
     def hopf_set_qr_method(self, method):
         self._check(self.lib.hopf_set_qr_method(self.h, int(method)))

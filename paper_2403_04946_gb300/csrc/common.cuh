@@ -154,8 +154,8 @@ DV uint64_t global_ns() {
 // every cooperative launch; `err` records an expired wait.
 struct GridBar {
   unsigned int count;
-  unsigned int unused;
-  int err;  // nonzero after a wait expired
+  unsigned int limit_us;  // wait limit in microseconds (0: kBarrierTimeoutNs)
+  int err;                // nonzero after a wait expired
   int pad;
 };
 
@@ -164,8 +164,9 @@ struct GridBar {
 // k-th barrier every CTA adds one and waits until the counter reaches
 // k * gridDim, so no CTA has to reset anything between barriers (one atomic
 // and one polled load per CTA per barrier).  Every wait is bounded: after
-// kBarrierTimeoutNs of wall time the CTA records the expiry in err and
-// leaves; callers check grid_failed() and return early.
+// kBarrierTimeoutNs of wall time (or the context's limit_us) the CTA records
+// the expiry in err and leaves; callers check grid_failed() and return
+// early.
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // 4 s
 
 struct GridSync {
@@ -182,12 +183,14 @@ DV void grid_sync(GridSync& gs) {
       __threadfence();
       atomicAdd(&gs.bar->count, 1u);
       volatile unsigned int* vc = &gs.bar->count;
+      const unsigned int lim = *((volatile unsigned int*)&gs.bar->limit_us);
+      const uint64_t limit_ns = lim ? (uint64_t)lim * 1000ull : kBarrierTimeoutNs;
       const uint64_t t0 = global_ns();
       unsigned int spins = 0;
       while ((int)(*vc - gs.target) < 0) {
-        if (((++spins) & 255u) == 0u) {
+        if (((++spins) & 31u) == 0u) {
           if (*verr != 0) break;
-          if (global_ns() - t0 > kBarrierTimeoutNs) {
+          if (global_ns() - t0 > limit_ns) {
             atomicExch(&gs.bar->err, 1);
             break;
           }

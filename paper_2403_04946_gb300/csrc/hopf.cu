@@ -12,6 +12,7 @@
 #include <string>
 #include <set>
 #include <thread>
+#include <atomic>
 #include <vector>
 
 #include "../../include/hopf.h"
@@ -80,6 +81,12 @@ struct hopf_ctx {
   int device = 0;
   int svd_method = HOPF_SVD_AUTO;
   int qr_method = HOPF_QR_DOUBLEFLOAT;
+  unsigned int wait_limit_us = 0;  // grid-barrier wait limit (0: the default)
+  // persistent staging of point / moment evaluation (grown on demand)
+  int* ev_idx = nullptr;
+  cplx* ev_vals = nullptr;
+  double* ev_out = nullptr;
+  size_t ev_idx_cap = 0, ev_vals_cap = 0, ev_out_cap = 0;
   // small device scalars and pinned mirrors
   double* d_dbl = nullptr;  // [16]
   int* d_int = nullptr;     // [16]
@@ -108,6 +115,33 @@ struct hopf_ctx {
 };
 
 // ---------------------------------------------------------------------------
+// Library-wide device allocator (hopf_set_allocator) and the count of live
+// contexts and tensors, which must be zero while the allocator changes.
+namespace {
+hopf_alloc_fn g_alloc = nullptr;
+hopf_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+std::atomic<long long> g_live{0};
+}  // namespace
+
+namespace hk {
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 1;
+  if (g_alloc) {
+    *p = g_alloc(bytes, g_alloc_user);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+void dev_free(void* p) {
+  if (!p) return;
+  if (g_free) g_free(p, g_alloc_user);
+  else cudaFree(p);
+}
+void live_add(int delta) { g_live += delta; }
+}  // namespace hk
+
 namespace {
 
 hopf_status fail(hopf_ctx* c, hopf_status st, const char* fmt, ...) {
@@ -205,8 +239,9 @@ template <class T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc((void**)p, count * sizeof(T));
+  return hk::dev_alloc((void**)p, count * sizeof(T));
 }
+inline void dfree(void* p) { hk::dev_free(p); }
 
 // ---- per-mode operator coefficients ------------------------------------------
 // (op x)[i] = lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1] on a_i = (i - n/2) da,
@@ -332,11 +367,11 @@ hopf_status coop_reserve(hopf_ctx* ctx, int kcap) {
   if (kcap <= ctx->coop_kcap) return HOPF_OK;
   kcap = std::max(kcap, 64);
   hk::CoopWs& w = ctx->coop;
-  cudaFree(w.pc);
-  cudaFree(w.wfin);
-  cudaFree(w.colnorm);
-  cudaFree(w.colver);
-  cudaFree(w.pairchk);
+  dfree(w.pc);
+  dfree(w.wfin);
+  dfree(w.colnorm);
+  dfree(w.colver);
+  dfree(w.pairchk);
   w.pc = nullptr;
   w.wfin = nullptr;
   w.colnorm = nullptr;
@@ -361,13 +396,13 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   const int kcap = t->cap_rank;
   RoundWs& w = ctx->rw;
   if (w.elems >= need && w.kcap >= kcap && w.d >= t->d) return HOPF_OK;
-  for (cplx* b : w.B) cudaFree(b);
-  cudaFree(w.W1); cudaFree(w.tau); cudaFree(w.T); cudaFree(w.tau2); cudaFree(w.T2);
-  cudaFree(w.Rb); cudaFree(w.Mb); cudaFree(w.Jb); cudaFree(w.Ub); cudaFree(w.Sb);
-  cudaFree(w.sig); cudaFree(w.perm);
-  cudaFree(w.bd_d); cudaFree(w.bd_e); cudaFree(w.bd_tauq); cudaFree(w.bd_taup); cudaFree(w.bd_a2);
-  cudaFree(w.bd_info); cudaFree(w.bd_X); cudaFree(w.bd_Zs);
-  cudaFree(w.G); cudaFree(w.G2);
+  for (cplx* b : w.B) dfree(b);
+  dfree(w.W1); dfree(w.tau); dfree(w.T); dfree(w.tau2); dfree(w.T2);
+  dfree(w.Rb); dfree(w.Mb); dfree(w.Jb); dfree(w.Ub); dfree(w.Sb);
+  dfree(w.sig); dfree(w.perm);
+  dfree(w.bd_d); dfree(w.bd_e); dfree(w.bd_tauq); dfree(w.bd_taup); dfree(w.bd_a2);
+  dfree(w.bd_info); dfree(w.bd_X); dfree(w.bd_Zs);
+  dfree(w.G); dfree(w.G2);
   w = RoundWs{};
   const size_t elems = std::max(need, w.elems);
   const int d = t->d;
@@ -415,9 +450,9 @@ hopf_status tt_alloc(hopf_ctx* ctx, int cap_rank, hopf_tt** out) {
   t->cores.assign(t->d, nullptr);
   t->ranks.assign(t->d + 1, 1);
   auto cleanup = [&]() {
-    for (cplx* c : t->cores) cudaFree(c);
-    cudaFree(t->d_ptrs);
-    cudaFree(t->d_ranks);
+    for (cplx* c : t->cores) dfree(c);
+    dfree(t->d_ptrs);
+    dfree(t->d_ranks);
     delete t;
   };
   for (int k = 0; k < t->d; ++k) {
@@ -442,6 +477,7 @@ hopf_status tt_alloc(hopf_ctx* ctx, int cap_rank, hopf_tt** out) {
     cleanup();
     return fail(ctx, HOPF_ECUDA, "%s", cudaGetErrorString(e));
   }
+  hk::live_add(1);
   *out = t;
   return HOPF_OK;
 }
@@ -468,12 +504,19 @@ hopf_status read_small(hopf_ctx* ctx, int nint, int ndbl) {
   return HOPF_OK;
 }
 
+// Barrier record back to its initial state (count 0, no expiry) with the
+// context's wait limit.  Pageable host source: staged before the call returns.
+void reset_barrier(hopf_ctx* ctx) {
+  const GridBar hb{0u, ctx->wait_limit_us, 0, 0};
+  cudaMemcpyAsync(ctx->coop.bar, &hb, sizeof hb, cudaMemcpyHostToDevice, ctx->stream);
+}
+
 hopf_status check_barrier(hopf_ctx* ctx) {
   GridBar hb;
   CK(cudaMemcpyAsync(&hb, ctx->coop.bar, sizeof(GridBar), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (hb.err) {
-    cudaMemsetAsync(ctx->coop.bar, 0, sizeof(GridBar), ctx->stream);
+    reset_barrier(ctx);
     return fail(ctx, HOPF_ETIMEOUT, "a grid barrier wait expired");
   }
   return HOPF_OK;
@@ -487,14 +530,37 @@ bool use_tc(const hopf_ctx* ctx, int m, int p) {
   return ctx->p.precision == HOPF_MIXED && ctx->qr_method == HOPF_QR_TENSOR && hk::qr_tc_applies(m, p);
 }
 
-hopf_status tc_reserve(hopf_ctx* ctx, int m, int k) {
-  const size_t need = hk::qr_tc_scratch_bytes(m, k, kTcDigits);
+hopf_status tc_reserve_bytes(hopf_ctx* ctx, size_t need) {
   if (need <= ctx->tcbytes) return HOPF_OK;
-  cudaFree(ctx->tcbuf);
+  dfree(ctx->tcbuf);
+  dfree(ctx->ev_idx); dfree(ctx->ev_vals); dfree(ctx->ev_out);
   ctx->tcbuf = nullptr;
   ctx->tcbytes = 0;
-  CK(cudaMalloc(&ctx->tcbuf, need));
+  CK(hk::dev_alloc(&ctx->tcbuf, need));
   ctx->tcbytes = need;
+  return HOPF_OK;
+}
+
+hopf_status tc_reserve(hopf_ctx* ctx, int m, int k) { return tc_reserve_bytes(ctx, hk::qr_tc_scratch_bytes(m, k, kTcDigits)); }
+
+// out (a.R x b.R, column-major, ldo) = A B^T of two operand views on the
+// tensor cores (digit splits in the context's scratch), profiled as one
+// HOPF_K_TC phase with the given FLOP count.
+hopf_status tc_product(hopf_ctx* ctx, const hk::TcOperandView& a, const hk::TcOperandView& b, cplx* out, long long ldo,
+                       double flops) {
+  const int Kc = hk::tc_chunk();
+  const size_t ba = (hk::tc_operand_bytes(a.R, a.K, kTcDigits, Kc) + 255) & ~(size_t)255;
+  const size_t bb = (hk::tc_operand_bytes(b.R, b.K, kTcDigits, Kc) + 255) & ~(size_t)255;
+  const size_t np = hk::tc_part_elems(a.R, b.R, a.K);
+  TRY(tc_reserve_bytes(ctx, ba + bb + np * sizeof(cplx) + 256));
+  unsigned char* buf = static_cast<unsigned char*>(ctx->tcbuf);
+  hk::TcOperand oa, ob;
+  const int slot = prof_begin(ctx);
+  CK(hk::tc_split(a, kTcDigits, &oa, buf, ctx->stream));
+  CK(hk::tc_split(b, kTcDigits, &ob, buf + ba, ctx->stream));
+  CK(hk::tc_zgemm(oa, ob, out, ldo, 1.0, 0, np ? reinterpret_cast<cplx*>(buf + ba + bb) : nullptr, np,
+                  &ctx->coop.bar->err, ctx->stream));
+  prof_end(ctx, slot, HOPF_K_TC, flops, 0.0, np ? 4 : 3);
   return HOPF_OK;
 }
 
@@ -543,6 +609,33 @@ hopf_status qr_apply(hopf_ctx* ctx, const cplx* A, int lda, int m, int p, const 
   return HOPF_OK;
 }
 
+// Persistent device staging of point / moment evaluation, grown on demand
+// (no per-call allocation once large enough).
+hopf_status ev_reserve(hopf_ctx* ctx, size_t nidx, size_t nvals, size_t nout) {
+  if (nidx > ctx->ev_idx_cap) {
+    dfree(ctx->ev_idx);
+    ctx->ev_idx = nullptr;
+    ctx->ev_idx_cap = 0;
+    CK(dalloc(&ctx->ev_idx, nidx));
+    ctx->ev_idx_cap = nidx;
+  }
+  if (nvals > ctx->ev_vals_cap) {
+    dfree(ctx->ev_vals);
+    ctx->ev_vals = nullptr;
+    ctx->ev_vals_cap = 0;
+    CK(dalloc(&ctx->ev_vals, nvals));
+    ctx->ev_vals_cap = nvals;
+  }
+  if (nout > ctx->ev_out_cap) {
+    dfree(ctx->ev_out);
+    ctx->ev_out = nullptr;
+    ctx->ev_out_cap = 0;
+    CK(dalloc(&ctx->ev_out, nout));
+    ctx->ev_out_cap = nout;
+  }
+  return HOPF_OK;
+}
+
 // Phase 1 of the rounding: right-to-left Householder LQ sweep (App. A,
 // Alg. 1 mirrored).  Reads the cores of t (unchanged), leaves B_c = the
 // factored H(Y_c)^H with its reflectors for c >= 1 and B_0 = V(Y_0 L_1)
@@ -563,7 +656,15 @@ hopf_status orth_sweep(hopf_ctx* ctx, const hopf_tt* t, std::vector<int>& p, std
     p[c] = std::min(m, k);
     // merge L_c = R_c^H into core c-1
     const int rl = r[c - 1];
-    if (c - 1 >= 1) {
+    if (c - 1 >= 1 && use_tc(ctx, rl * n, 64)) {
+      // on the tensor cores: C = X_{c-1} R^H into the scratch W1
+      // (column-major), then H(Y)^H into the next factor's buffer
+      TRY(tc_product(ctx, hk::TcOperandView{t->cores[c - 1], 1, (long long)rl * n, rl * n, k, 0, 0, 0},
+                     hk::TcOperandView{w.B[c], 1, m, p[c], k, 1, 1, 0}, w.W1, (long long)rl * n,
+                     arh_flops((double)rl * n, k, p[c])));
+      LAUNCH(HOPF_K_SUM, 0, 32.0 * rl * n * p[c], 1,
+             hk::conj_transpose(w.W1, rl, rl, n * p[c], w.B[c - 1], n * p[c], ctx->stream));
+    } else if (c - 1 >= 1) {
       LAUNCH(HOPF_K_GEMM, arh_flops((double)rl * n, k, p[c]), 0, 1, hk::gemm_a_rh(t->cores[c - 1], rl * n, rl * n, k, w.B[c], m, p[c], w.B[c - 1], n * p[c], 1, rl, n, ctx->stream, MIXED_FLAG));
     } else {
       LAUNCH(HOPF_K_GEMM, arh_flops(n, k, p[1]), 0, 1, hk::gemm_a_rh(t->cores[0], n, n, k, w.B[1], m, p[1], w.B[0], n, 0, 1, n, ctx->stream, MIXED_FLAG));
@@ -685,7 +786,12 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     }
     TRY(qr_apply(ctx, Z, Mrows, Mrows, pp, w.tau2, w.T2, nb2, w.G2, t->cores[c], Mrows, rnew));
     // S = U_rho^H R (rho x cols)
-    LAUNCH(HOPF_K_GEMM, 8.0 * rnew * pp * cols, 0, 1, hk::gemm_uh_r(w.Ub, pp, rnew, pp, w.Rb, pp, cols, w.Sb, rnew, ctx->stream));
+    if (use_tc(ctx, 4096, pp)) {
+      TRY(tc_product(ctx, hk::TcOperandView{w.Ub, pp, 1, rnew, pp, 1, 0, 0}, hk::TcOperandView{w.Rb, pp, 1, cols, pp, 0, 0, 0},
+                     w.Sb, rnew, 8.0 * rnew * pp * cols));
+    } else {
+      LAUNCH(HOPF_K_GEMM, 8.0 * rnew * pp * cols, 0, 1, hk::gemm_uh_r(w.Ub, pp, rnew, pp, w.Rb, pp, cols, w.Sb, rnew, ctx->stream));
+    }
   }
   // last core: C = Q_{B,d-1} [S^H; 0] (n x rho), core = C^H
   {
@@ -745,10 +851,34 @@ hopf_status orth_sweep_apply(hopf_ctx* ctx, const hopf_tt* X, std::vector<int>& 
     p[c] = std::min(m, k);
     const int rl = r[c - 1];
     const size_t blk = (size_t)rl * n * p[c];
-    for (int be = 0; be < 6; ++be) {
-      LAUNCH(HOPF_K_GEMM, rblk_flops((double)rl * n, r[c], p[c], be * r[c]), 0, 1,
-             hk::gemm_a_rblk_h(X->cores[c - 1], rl * n, rl * n, r[c], w.B[c], m, be * r[c], p[c], w.W1 + be * blk, rl * n,
-                               ctx->stream, MIXED_FLAG));
+    if (use_tc(ctx, rl * n, 64)) {
+      // the six products on the tensor cores: X_{c-1} (rl n x r) split once,
+      // each block of R^H (conjugated, upper trapezoid) split in turn
+      const int Kc = hk::tc_chunk();
+      const size_t ba = (hk::tc_operand_bytes(rl * n, r[c], kTcDigits, Kc) + 255) & ~(size_t)255;
+      const size_t bb = (hk::tc_operand_bytes(p[c], r[c], kTcDigits, Kc) + 255) & ~(size_t)255;
+      const size_t np = hk::tc_part_elems(rl * n, p[c], r[c]);
+      TRY(tc_reserve_bytes(ctx, ba + bb + np * sizeof(cplx) + 256));
+      unsigned char* buf = static_cast<unsigned char*>(ctx->tcbuf);
+      cplx* part = np ? reinterpret_cast<cplx*>(buf + ba + bb) : nullptr;
+      hk::TcOperand oX, oR;
+      int slot = prof_begin(ctx);
+      CK(hk::tc_split(hk::TcOperandView{X->cores[c - 1], 1, (long long)rl * n, rl * n, r[c], 0, 0, 0}, kTcDigits, &oX, buf,
+                      ctx->stream));
+      prof_end(ctx, slot, HOPF_K_TC, 0.0, 0.0, 1);
+      for (int be = 0; be < 6; ++be) {
+        slot = prof_begin(ctx);
+        CK(hk::tc_split(hk::TcOperandView{w.B[c] + (size_t)m * be * r[c], 1, m, p[c], r[c], 1, 1, be * r[c]}, kTcDigits,
+                        &oR, buf + ba, ctx->stream));
+        CK(hk::tc_zgemm(oX, oR, w.W1 + be * blk, rl * n, 1.0, 0, part, np, &ctx->coop.bar->err, ctx->stream));
+        prof_end(ctx, slot, HOPF_K_TC, rblk_flops((double)rl * n, r[c], p[c], be * r[c]), 0.0, np ? 3 : 2);
+      }
+    } else {
+      for (int be = 0; be < 6; ++be) {
+        LAUNCH(HOPF_K_GEMM, rblk_flops((double)rl * n, r[c], p[c], be * r[c]), 0, 1,
+               hk::gemm_a_rblk_h(X->cores[c - 1], rl * n, rl * n, r[c], w.B[c], m, be * r[c], p[c], w.W1 + be * blk,
+                                 rl * n, ctx->stream, MIXED_FLAG));
+      }
     }
     const int Al = (c - 1 == 0) ? 1 : 6;
     const int kind = (c - 1 == 0) ? 0 : 1;
@@ -908,8 +1038,8 @@ struct CrossBufs {
   cplx* tau = nullptr;   // cap
   cplx* T = nullptr;     // panel Grams of the QR
   void release() {
-    cudaFree(A); cudaFree(W); cudaFree(Gw); cudaFree(Gi); cudaFree(il); cudaFree(jr); cudaFree(piv); cudaFree(mc);
-    cudaFree(seq); cudaFree(Q); cudaFree(tau); cudaFree(T);
+    dfree(A); dfree(W); dfree(Gw); dfree(Gi); dfree(il); dfree(jr); dfree(piv); dfree(mc);
+    dfree(seq); dfree(Q); dfree(tau); dfree(T);
   }
 };
 
@@ -1119,6 +1249,7 @@ hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out) {
     return HOPF_EINVAL;
   hopf_ctx* ctx = new (std::nothrow) hopf_ctx();
   if (!ctx) return HOPF_ENOMEM;
+  hk::live_add(1);  // hopf_destroy (also on the failure paths below) takes it back
   ctx->p = *p;
   ctx->stream = (cudaStream_t)stream;
   cudaGetDevice(&ctx->device);
@@ -1148,36 +1279,48 @@ hopf_status hopf_create(const hopf_params* p, void* stream, hopf_ctx** out) {
   return HOPF_OK;
 }
 
+hopf_status hopf_set_allocator(hopf_alloc_fn alloc, hopf_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return HOPF_EINVAL;
+  if (g_live.load() != 0) return HOPF_EINVAL;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return HOPF_OK;
+}
+
 void tt_free(hopf_tt* t) {
   if (!t) return;
-  for (cplx* c : t->cores) cudaFree(c);
-  cudaFree(t->d_ptrs);
-  cudaFree(t->d_ranks);
+  hk::live_add(-1);
+  for (cplx* c : t->cores) dfree(c);
+  dfree(t->d_ptrs);
+  dfree(t->d_ranks);
   delete t;
 }
 
 void hopf_destroy(hopf_ctx* ctx) {
   if (!ctx) return;
+  hk::live_add(-1);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   tt_free(ctx->big);
   for (auto k : ctx->kst) tt_free(k);
   tt_free(ctx->ytmp);
   RoundWs& w = ctx->rw;
-  for (cplx* b : w.B) cudaFree(b);
-  cudaFree(w.W1); cudaFree(w.tau); cudaFree(w.T); cudaFree(w.tau2); cudaFree(w.T2);
-  cudaFree(w.Rb); cudaFree(w.Mb); cudaFree(w.Jb); cudaFree(w.Ub); cudaFree(w.Sb);
-  cudaFree(w.sig); cudaFree(w.perm);
-  cudaFree(w.bd_d); cudaFree(w.bd_e); cudaFree(w.bd_tauq); cudaFree(w.bd_taup); cudaFree(w.bd_a2);
-  cudaFree(w.bd_info); cudaFree(w.bd_X); cudaFree(w.bd_Zs);
-  cudaFree(w.G); cudaFree(w.G2);
-  cudaFree(ctx->tcbuf);
-  cudaFree(ctx->coop.bar); cudaFree(ctx->coop.pr); cudaFree(ctx->coop.pc);
-  cudaFree(ctx->coop.wfin); cudaFree(ctx->coop.scal); cudaFree(ctx->coop.counters);
-  cudaFree(ctx->coop.colnorm); cudaFree(ctx->coop.colver); cudaFree(ctx->coop.pairchk);
-  cudaFree(ctx->d_coef); cudaFree(ctx->d_blocks); cudaFree(ctx->d_agrid);
-  cudaFree(ctx->d_dbl); cudaFree(ctx->d_int); cudaFree(ctx->d_terms);
-  for (void* p : ctx->extra) cudaFree(p);
+  for (cplx* b : w.B) dfree(b);
+  dfree(w.W1); dfree(w.tau); dfree(w.T); dfree(w.tau2); dfree(w.T2);
+  dfree(w.Rb); dfree(w.Mb); dfree(w.Jb); dfree(w.Ub); dfree(w.Sb);
+  dfree(w.sig); dfree(w.perm);
+  dfree(w.bd_d); dfree(w.bd_e); dfree(w.bd_tauq); dfree(w.bd_taup); dfree(w.bd_a2);
+  dfree(w.bd_info); dfree(w.bd_X); dfree(w.bd_Zs);
+  dfree(w.G); dfree(w.G2);
+  dfree(ctx->tcbuf);
+  dfree(ctx->ev_idx); dfree(ctx->ev_vals); dfree(ctx->ev_out);
+  dfree(ctx->coop.bar); dfree(ctx->coop.pr); dfree(ctx->coop.pc);
+  dfree(ctx->coop.wfin); dfree(ctx->coop.scal); dfree(ctx->coop.counters);
+  dfree(ctx->coop.colnorm); dfree(ctx->coop.colver); dfree(ctx->coop.pairchk);
+  dfree(ctx->d_coef); dfree(ctx->d_blocks); dfree(ctx->d_agrid);
+  dfree(ctx->d_dbl); dfree(ctx->d_int); dfree(ctx->d_terms);
+  for (void* p : ctx->extra) dfree(p);
   for (auto e : ctx->prof_ev) cudaEventDestroy(e);
   if (ctx->h_dbl) cudaFreeHost(ctx->h_dbl);
   if (ctx->h_int) cudaFreeHost(ctx->h_int);
@@ -1204,6 +1347,74 @@ hopf_status hopf_set_max_ctas(hopf_ctx* ctx, int max_ctas) {
   if (!ctx) return HOPF_EINVAL;
   if (max_ctas < 0) return fail(ctx, HOPF_EINVAL, "max_ctas must be >= 0");
   ctx->coop.max_ctas = max_ctas;
+  return HOPF_OK;
+}
+
+hopf_status hopf_check_watchdog(hopf_ctx* ctx) {
+  if (!ctx) return HOPF_EINVAL;
+  CK(hk::watchdog_probe(ctx->coop, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_barrier(ctx);
+}
+
+hopf_status hopf_set_wait_limit(hopf_ctx* ctx, double seconds) {
+  if (!ctx) return HOPF_EINVAL;
+  if (!(seconds >= 0.0) || seconds > 60.0) return fail(ctx, HOPF_EINVAL, "wait limit must be in [0, 60] s");
+  ctx->wait_limit_us = seconds == 0.0 ? 0u : (unsigned int)std::max(1.0, std::round(seconds * 1e6));
+  reset_barrier(ctx);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HOPF_OK;
+}
+
+namespace {
+constexpr char kTtMagic[8] = {'H', 'O', 'P', 'F', 'T', 'T', '\0', '\1'};
+}
+
+hopf_status tt_save(const hopf_tt* t, const char* path, double time) {
+  if (!t || !path) return HOPF_EINVAL;
+  hopf_ctx* ctx = t->ctx;
+  size_t nd = 0;
+  tt_size(t, &nd);
+  std::vector<double> buf(nd);
+  TRY(tt_to_host(t, buf.data(), nd));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, HOPF_EINVAL, "tt_save: cannot open %s", path);
+  const int hdr[2] = {t->d, t->n};
+  bool ok = std::fwrite(kTtMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 2, f) == 2 &&
+            std::fwrite(t->ranks.data(), sizeof(int), t->d + 1, f) == (size_t)(t->d + 1) &&
+            std::fwrite(&time, sizeof(double), 1, f) == 1 && std::fwrite(buf.data(), sizeof(double), nd, f) == nd;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(ctx, HOPF_EINVAL, "tt_save: write to %s failed", path);
+  return HOPF_OK;
+}
+
+hopf_status tt_load(hopf_ctx* ctx, const char* path, int max_rank, hopf_tt** out, double* time) {
+  if (!ctx || !path || !out) return ctx ? fail(ctx, HOPF_EINVAL, "tt_load: null argument") : HOPF_EINVAL;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, HOPF_EINVAL, "tt_load: cannot open %s", path);
+  char magic[8];
+  int hdr[2] = {0, 0};
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kTtMagic, 8) == 0 &&
+            std::fread(hdr, sizeof(int), 2, f) == 2 && hdr[0] == ctx->p.d && hdr[1] == ctx->p.n;
+  std::vector<int> ranks(ctx->p.d + 1);
+  double tm = 0.0;
+  ok = ok && std::fread(ranks.data(), sizeof(int), ranks.size(), f) == ranks.size() &&
+       std::fread(&tm, sizeof(double), 1, f) == 1;
+  size_t nd = 0;
+  if (ok) {
+    for (int k = 0; k < ctx->p.d && ok; ++k) {
+      ok = ranks[k] >= 1 && ranks[k + 1] >= 1 && ranks[k] <= (1 << 20) && ranks[k + 1] <= (1 << 20);
+      nd += 2 * (size_t)ranks[k] * ctx->p.n * ranks[k + 1];
+    }
+  }
+  std::vector<double> buf(ok ? nd : 0);
+  ok = ok && std::fread(buf.data(), sizeof(double), nd, f) == nd;
+  std::fclose(f);
+  if (!ok) return fail(ctx, HOPF_EINVAL, "tt_load: %s is not a TT of this context's d and n (or is truncated)", path);
+  const int cap = max_rank > 0 ? max_rank : *std::max_element(ranks.begin(), ranks.end());
+  TRY(tt_from_host(ctx, ranks.data(), buf.data(), cap, out));
+  if (time) *time = tm;
   return HOPF_OK;
 }
 
@@ -1249,7 +1460,7 @@ hopf_status hopf_cell_moments(hopf_ctx* ctx, int nmodes, const double* alpha, co
   if (e == cudaSuccess) e = cudaMemcpyAsync(m0, dm0, d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(C0, dC0, (size_t)d * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  cudaFree(dbuf);
+  dfree(dbuf);
   if (e != cudaSuccess) return fail(ctx, HOPF_ECUDA, "hopf_cell_moments: %s", cudaGetErrorString(e));
   for (int j = 0; j < d; ++j)
     for (int k = j + 1; k < d; ++k) {
@@ -1564,16 +1775,13 @@ hopf_status hopf_eval_points(hopf_ctx* ctx, const hopf_tt* t, int npts, const in
     if (idx[e] < 0 || idx[e] >= n) return fail(ctx, HOPF_EINVAL, "index %d outside [0, %d)", idx[e], n);
   int maxr = 1;
   for (int r : t->ranks) maxr = std::max(maxr, r);
-  int* didx = nullptr;
-  cplx* dv = nullptr;
-  CK(dalloc(&didx, (size_t)npts * d));
-  cudaError_t e = dalloc(&dv, (size_t)npts);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(didx, idx, (size_t)npts * d * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  TRY(ev_reserve(ctx, (size_t)npts * d, (size_t)npts, 0));
+  int* didx = ctx->ev_idx;
+  cplx* dv = ctx->ev_vals;
+  cudaError_t e = cudaMemcpyAsync(didx, idx, (size_t)npts * d * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = hk::eval_points(t->d_ptrs, t->d_ranks, d, n, maxr, npts, didx, dv, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(vals, dv, (size_t)npts * sizeof(cplx), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  cudaFree(didx);
-  cudaFree(dv);
   if (e != cudaSuccess) return fail(ctx, HOPF_ECUDA, "hopf_eval_points: %s", cudaGetErrorString(e));
   return HOPF_OK;
 }
@@ -1600,13 +1808,11 @@ hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean, dou
     }
   int maxr = 1;
   for (int r : t->ranks) maxr = std::max(maxr, r);
-  int* didx = nullptr;
-  cplx* dv = nullptr;
-  double* dout = nullptr;
-  CK(dalloc(&didx, idx.size()));
-  cudaError_t e = dalloc(&dv, (size_t)npts);
-  if (e == cudaSuccess) e = dalloc(&dout, (size_t)d + (size_t)d * d + 1);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  TRY(ev_reserve(ctx, idx.size(), (size_t)npts, (size_t)d + (size_t)d * d + 1));
+  int* didx = ctx->ev_idx;
+  cplx* dv = ctx->ev_vals;
+  double* dout = ctx->ev_out;
+  cudaError_t e = cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = hk::eval_points(t->d_ptrs, t->d_ranks, d, n, maxr, npts, didx, dv, ctx->stream);
   const double da = 2.0 * ctx->L / n;
   if (e == cudaSuccess) e = hk::moments_combine(dv, d, da, dout, dout + d, dout + d + (size_t)d * d, ctx->stream);
@@ -1615,9 +1821,6 @@ hopf_status hopf_eval_moments(hopf_ctx* ctx, const hopf_tt* t, double* mean, dou
   if (e == cudaSuccess) e = cudaMemcpyAsync(cov, dout + d, (size_t)d * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ir, dout + d + (size_t)d * d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  cudaFree(didx);
-  cudaFree(dv);
-  cudaFree(dout);
   if (e != cudaSuccess) return fail(ctx, HOPF_ECUDA, "hopf_eval_moments: %s", cudaGetErrorString(e));
   if (imag_resid) *imag_resid = ir;
   return HOPF_OK;
@@ -1700,7 +1903,7 @@ hopf_status hopf_init_gaussian(hopf_ctx* ctx, const double* m0, const double* C0
     else e = hk::identity_core(n, r[k], r[k + 1], 0, full->cores[k], ctx->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  cudaFree(dmc);
+  dfree(dmc);
   if (e != cudaSuccess) st = fail(ctx, HOPF_ECUDA, "init: %s", cudaGetErrorString(e));
   if (st == HOPF_OK) {
     full->ranks = r;
@@ -1734,7 +1937,7 @@ hopf_status hopf_tc_zgemm(hopf_ctx* ctx, int M, int N, int K, const double* A, i
   cplx *dA = nullptr, *dB = nullptr, *dC = nullptr, *dP = nullptr;
   unsigned char *bufA = nullptr, *bufB = nullptr;
   auto release = [&]() {
-    cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(dP); cudaFree(bufA); cudaFree(bufB);
+    dfree(dA); dfree(dB); dfree(dC); dfree(dP); dfree(bufA); dfree(bufB);
   };
   if (dalloc(&dA, na) != cudaSuccess || dalloc(&dB, nb) != cudaSuccess || dalloc(&dC, nc) != cudaSuccess ||
       dalloc(&dP, np) != cudaSuccess || dalloc(&bufA, oa) != cudaSuccess || dalloc(&bufB, ob) != cudaSuccess) {

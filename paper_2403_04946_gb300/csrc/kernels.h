@@ -252,7 +252,7 @@ int tc_max_digits();  // 5
 // Splits the operand into S digit planes in `buf` (tc_operand_bytes).
 cudaError_t tc_split(const TcOperandView& v, int S, TcOperand* out, void* buf, cudaStream_t s);
 // out (M x N, column-major, ldo) = alpha * A B^T (+ out if accumulate), with
-// A (M x K) and B (N x K) split operands, i.e. out[m, n] =
+// alpha a signed power of two, A (M x K) and B (N x K) split operands, i.e. out[m, n] =
 // alpha sum_k A(m, k) B(n, k).  K beyond one chunk: per-chunk partials in
 // part (tc_part_elems), summed in a fixed order.  err: expiry record.
 cudaError_t tc_zgemm(const TcOperand& A, const TcOperand& B, cplx* out, long long ldo, double alpha, int accumulate,
@@ -286,5 +286,18 @@ cudaError_t geqrf_tc(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, cplx* G
 // C <- Q C for the Q of geqrf_tc (p reflectors).
 cudaError_t ormqr_tc(const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* Gin, cplx* C, int ldc, int q,
                      void* scratch, size_t scratch_bytes, int* err, int S, cudaStream_t s, const PhaseTimer& pt);
+
+// ---- device memory of the library (hopf.cu) -----------------------------------
+// Every device allocation of the solver and the surrogate goes through these:
+// cudaMalloc / cudaFree, or the caller's functions set by hopf_set_allocator.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+// Contexts, tensors and networks alive (the allocator may change only at 0).
+void live_add(int delta);
+
+// Watchdog check: a cooperative launch of two CTAs in which CTA 0 never
+// reaches the grid barrier, so CTA 1's bounded wait must expire (recorded
+// in ws.bar->err after the context's wait limit).  Faults nothing.
+cudaError_t watchdog_probe(const CoopWs& ws, cudaStream_t s);
 
 }  // namespace hk

@@ -20,6 +20,14 @@
 
 #include "../../include/hopf.h"
 
+// The library's device allocator (hopf.cu: cudaMalloc or the caller's
+// functions, hopf_set_allocator) and its count of live objects.
+namespace hk {
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+void live_add(int delta);
+}  // namespace hk
+
 typedef __nv_bfloat16 bf16;
 
 // Internal accessors defined in hopf.cu.
@@ -361,7 +369,7 @@ hopf_status mfail(hopf_mlp* m, hopf_status st, const char* fmt, ...) {
 template <class T>
 cudaError_t malloc_track(hopf_mlp* mm, T** p, size_t count) {
   *p = nullptr;
-  cudaError_t e = cudaMalloc((void**)p, (count ? count : 1) * sizeof(T));
+  cudaError_t e = hk::dev_alloc((void**)p, (count ? count : 1) * sizeof(T));
   if (e == cudaSuccess) mm->allocs.push_back(*p);
   return e;
 }
@@ -539,8 +547,9 @@ hopf_status hopf_mlp_param_count(const hopf_mlp_params* p, long long* P) {
 
 void hopf_mlp_free(hopf_mlp* mm) {
   if (!mm) return;
+  hk::live_add(-1);
   if (mm->s) cudaStreamSynchronize(mm->s);
-  for (void* p : mm->allocs) cudaFree(p);
+  for (void* p : mm->allocs) hk::dev_free(p);
   if (mm->s) cudaStreamDestroy(mm->s);
   delete mm;
 }
@@ -553,6 +562,7 @@ hopf_status hopf_mlp_create(hopf_ctx* ctx, const hopf_mlp_params* p, const float
     return HOPF_EINVAL;
   }
   hopf_mlp* mm = new hopf_mlp;
+  hk::live_add(1);  // hopf_mlp_free takes it back
   mm->ctx = ctx;
   mm->p = *p;
   layer_dims(*p, mm->dims);
@@ -570,6 +580,7 @@ hopf_status hopf_mlp_create(hopf_ctx* ctx, const hopf_mlp_params* p, const float
   const long long mb = p->max_batch, tot = (long long)M * mm->P;
   for (size_t i = 0; i < (size_t)tot; ++i)
     if (!std::isfinite(init[i])) {
+      hk::live_add(-1);
       delete mm;
       hopf_internal_set_error(ctx, "hopf_mlp_create: non-finite initial parameter");
       return HOPF_EINVAL;
@@ -642,7 +653,7 @@ hopf_status hopf_mlp_set_data(hopf_mlp* mm, int nsamples, const double* x, const
     for (double* p : {mm->xd, mm->yd}) {
       for (size_t i = 0; i < mm->allocs.size(); ++i)
         if (mm->allocs[i] == p) {
-          cudaFree(p);
+          hk::dev_free(p);
           mm->allocs.erase(mm->allocs.begin() + i);
           break;
         }
@@ -678,7 +689,7 @@ hopf_status ensure_tables(hopf_mlp* mm, long long idx_count, long long iters) {
   if (idx_count > mm->idx_cap) {
     for (size_t i = 0; i < mm->allocs.size(); ++i)
       if (mm->allocs[i] == mm->idx) {
-        cudaFree(mm->idx);
+        hk::dev_free(mm->idx);
         mm->allocs.erase(mm->allocs.begin() + i);
         break;
       }
@@ -691,7 +702,7 @@ hopf_status ensure_tables(hopf_mlp* mm, long long idx_count, long long iters) {
     for (float* p : {mm->lr, mm->loss})
       for (size_t i = 0; i < mm->allocs.size(); ++i)
         if (mm->allocs[i] == p) {
-          cudaFree(p);
+          hk::dev_free(p);
           mm->allocs.erase(mm->allocs.begin() + i);
           break;
         }

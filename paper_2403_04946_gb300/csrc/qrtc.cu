@@ -29,12 +29,32 @@ namespace {
 constexpr int kOuter = 128;
 
 // W2 = T^H W (forward) or T W (backward) for the compact WY factor given by
-// G (v_s^H v_u in G[s + ldg u], s < u) and tau: one warp per column l of W
-// (nbk x nt, ldw), each lane holding rows s = lane + 32 q.
-__global__ void wy_solve_kernel(const cplx* G, int ldg, const cplx* tau, int nbk, const cplx* W, int ldw, int nt,
-                                cplx* W2, int ldw2, int forward) {
+// G (v_s^H v_u in G[s + ldg u]; Hermitian) and tau: one warp per column l
+// of W (nbk x nt, ldw), each lane holding rows s = lane + 32 q.  The
+// triangle of G the solve reads and tau are staged in shared memory first
+// (the solve is a chain of nbk dependent steps; each step then reads shared
+// memory, not L2).  Packed column u of the staged triangle holds G[s, u] for
+// s > u (forward) or G[s, u] for s < u (backward).
+constexpr int kWyWarps = 4;
+
+__global__ void __launch_bounds__(32 * kWyWarps)
+    wy_solve_kernel(const cplx* G, int ldg, const cplx* tau, int nbk, const cplx* W, int ldw, int nt, cplx* W2,
+                    int ldw2, int forward) {
+  extern __shared__ __align__(16) unsigned char wy_raw[];
+  cplx* tri = reinterpret_cast<cplx*>(wy_raw);  // nbk (nbk - 1) / 2 packed
+  cplx* tsh = tri + (size_t)nbk * (nbk - 1) / 2;
+  // packed offset of column u: forward rows u+1..nbk-1, backward rows 0..u-1
+  auto off = [&](int u) -> int {
+    return forward ? u * (2 * nbk - u - 1) / 2 : u * (u - 1) / 2;
+  };
+  for (int u = 0; u < nbk; ++u) {
+    const int lo = forward ? u + 1 : 0, hi = forward ? nbk : u;
+    for (int s = lo + (int)threadIdx.x; s < hi; s += blockDim.x) tri[off(u) + (s - lo)] = G[s + (size_t)ldg * u];
+  }
+  for (int u = threadIdx.x; u < nbk; u += blockDim.x) tsh[u] = tau[u];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int l = blockIdx.x * kWyWarps + (threadIdx.x >> 5);
   if (l >= nt) return;
   constexpr int Q = kOuter / 32;
   cplx acc[Q];
@@ -50,20 +70,21 @@ __global__ void wy_solve_kernel(const cplx* G, int ldg, const cplx* tau, int nbk
 #pragma unroll
     for (int q = 0; q < Q; ++q)
       if (q == qu) own = acc[q];
-    const cplx t = __ldg(reinterpret_cast<const double2*>(tau) + u);
+    const cplx t = tsh[u];
     cplx w2 = forward ? cmul(cconj(t), own) : cmul(t, own);
     w2.x = __shfl_sync(0xffffffffu, w2.x, lu);
     w2.y = __shfl_sync(0xffffffffu, w2.y, lu);
     if (lane == lu) W2[u + (size_t)ldw2 * l] = w2;
+    const cplx* col = tri + off(u);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int s = lane + 32 * q;
       if (s >= nbk) continue;
       if (forward && s > u) {
-        // (T^-H)[s, u] = conj(G[u, s]) for u < s
-        acc[q] = csub(acc[q], cmulc(__ldg(reinterpret_cast<const double2*>(G) + u + (size_t)ldg * s), w2));
+        // (T^-H)[s, u] = conj(G[u, s]) = G[s, u]
+        acc[q] = csub(acc[q], cmul(col[s - u - 1], w2));
       } else if (!forward && s < u) {
-        acc[q] = csub(acc[q], cmul(__ldg(reinterpret_cast<const double2*>(G) + s + (size_t)ldg * u), w2));
+        acc[q] = csub(acc[q], cmul(col[s], w2));
       }
     }
   }
@@ -72,9 +93,23 @@ __global__ void wy_solve_kernel(const cplx* G, int ldg, const cplx* tau, int nbk
 cudaError_t wy_solve(const cplx* G, int ldg, const cplx* tau, int nbk, const cplx* W, int ldw, int nt, cplx* W2,
                      int ldw2, int forward, cudaStream_t s) {
   if (nt <= 0) return cudaSuccess;
-  const int warps = 8;
-  wy_solve_kernel<<<(nt + warps - 1) / warps, 32 * warps, 0, s>>>(G, ldg, tau, nbk, W, ldw, nt, W2, ldw2, forward);
+  const size_t smem = sizeof(cplx) * ((size_t)nbk * (nbk - 1) / 2 + nbk);
+  static cudaError_t attr = cudaFuncSetAttribute(wy_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(sizeof(cplx) * ((size_t)kOuter * (kOuter - 1) / 2 + kOuter)));
+  if (attr != cudaSuccess) return attr;
+  wy_solve_kernel<<<(nt + kWyWarps - 1) / kWyWarps, 32 * kWyWarps, smem, s>>>(G, ldg, tau, nbk, W, ldw, nt, W2, ldw2,
+                                                                             forward);
   return cudaGetLastError();
+}
+
+// G[s, u] <- conj(G[u, s]) for s > u: the Gram exactly Hermitian, so that
+// the forward solve (which reads the lower triangle, contiguous across the
+// lanes) and the backward solve (the upper one) use the same numbers.
+__global__ void hermitize_kernel(cplx* G, int ldg, int nb) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * nb) return;
+  const int s = idx % nb, u = idx / nb;
+  if (s > u) G[s + (size_t)ldg * u] = cconj(G[u + (size_t)ldg * s]);
 }
 
 // Carves the scratch for one panel step out of ws.
@@ -154,7 +189,11 @@ cudaError_t geqrf_tc(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, cplx* G
     if (e == cudaSuccess) e = tc_split(TcOperandView{Ap, lda, 1, nbk, mv, 0, 2, 0}, S, &oVB, bVB, s);
     cplx* G = Gout + (size_t)(j0 / kOuter) * kOuter * kOuter;
     if (e == cudaSuccess) e = tc_zgemm(oVH, oVB, G, kOuter, 1.0, 0, part, npart, &cws.bar->err, s);
-    pt.e(slot, pt.cls_tc, zflops(nbk, nbk, mv), 6);
+    if (e == cudaSuccess) {
+      hermitize_kernel<<<(nbk * nbk + 255) / 256, 256, 0, s>>>(G, kOuter, nbk);
+      e = cudaGetLastError();
+    }
+    pt.e(slot, pt.cls_tc, zflops(nbk, nbk, mv), 7);
     if (e != cudaSuccess || nt <= 0) continue;
     // trailing columns: W = V^H A_t, W2 = T^H W, A_t -= V W2
     cplx* At = A + j0 + (size_t)lda * (j0 + nbk);

@@ -153,13 +153,28 @@ DV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// (double)f * 2^E (negated if neg) from the bit pattern of f: sign, exponent
+// rebiased from 127 to 1023 plus E, significand shifted into place.  Zero
+// and FP32 subnormals give 0 (a subnormal low part sits below 2^-149 of its
+// high part); an exponent outside the double range saturates to 0 or inf.
+DV double f2d_scaled(float f, int E, int neg) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e8 = (u >> 23) & 0xFFu;
+  if (e8 == 0) return 0.0;
+  const long long sgn = (long long)((u >> 31) ^ (unsigned)neg) << 63;
+  const int e11 = (int)e8 - 127 + 1023 + E;
+  if (e11 <= 0) return 0.0;
+  if (e11 >= 2047) return __longlong_as_double(sgn | (0x7FFll << 52));
+  return __longlong_as_double(sgn | ((long long)e11 << 52) | ((long long)(u & 0x7FFFFFu) << 29));
+}
+
 struct TcArgs {
   int M, N, K, S, Kc, nchunks;
   const int* eA;  // [3][nchunks][M] scale exponents of the A digits
   const int* eB;  // [3][nchunks][N]
   cplx* out;      // out[z * zstride + m + ldo * n]
   long long ldo, zstride;
-  double alpha;   // out = alpha * result (+ out if accumulate)
+  int alpha_exp, alpha_neg;  // alpha = (-1)^alpha_neg 2^alpha_exp: out = alpha * result (+ out if accumulate)
   int accumulate;
   int* err;       // expiry record (the context's grid-barrier err field)
 };
@@ -176,7 +191,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int S = a.S;
   const int sbytes = stage_bytes(S);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * kTcN, z = blockIdx.z;
+  // N-tiles fastest: the CTAs that share an A-tile (the large digit planes)
+  // run together and find it in L2
+  const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN, z = blockIdx.z;
   const int k_begin = z * a.Kc;
   const int k_len = min(a.Kc, a.K - k_begin);
   const int nslab = (k_len + kSlab - 1) / kSlab;
@@ -257,6 +274,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     // ---- epilogue: warps 0-3, thread = output row ------------------------
+    // Every level accumulator is an exact FP32 integer; the levels, the
+    // per-component scales and the 3M combination are summed in
+    // double-float arithmetic on the FP32 pipe (error-free TwoSum steps),
+    // and only the final value is converted to FP64 and scaled (on this GPU
+    // the FP64 pipe is 1/64 of the FP32 one).
     const bool ok = mbar_wait(&acc_bar, 0, vabort, a.err);
     tc_fence_after();
     const int m = m0 + 32 * warp + lane;
@@ -270,49 +292,54 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       cplx* out = a.out + (size_t)z * a.zstride;
 #pragma unroll 1
       for (int h = 0; h < kTcN / 16; ++h) {
-        double cre[16], cim[16];
+        float th[3][16], tl[3][16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) cre[q] = cim[q] = 0.0;
-#pragma unroll 1
         for (int c = 0; c < 3; ++c) {
-          double t[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q) t[q] = 0.0;
 #pragma unroll 1
           for (int L = 0; L < S; ++L) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((c * S + L) * kTcN + 16 * h), v);
-            const double w = ldexp(1.0, -14 - 8 * L);
+            const int sh = -14 - 8 * L;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) t[q] = fma(w, (double)v[q], t[q]);
-          }
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int n = n0 + 16 * h + q;
-            const int eb = (n < a.N) ? eB[c * eBs + n] : 0;
-            const double tv = ldexp(t[q], ea[c] + eb);
-            if (c == 0) {
-              cre[q] += tv;
-              cim[q] -= tv;
-            } else if (c == 1) {
-              cre[q] -= tv;
-              cim[q] -= tv;
-            } else {
-              cim[q] += tv;
+            for (int q = 0; q < 16; ++q) {
+              const float x = scalbnf(v[q], sh);  // exact: an integer below 2^24 times a power of two
+              if (L == 0) {
+                th[c][q] = x;
+                tl[c][q] = 0.f;
+              } else {
+                df_add_part(th[c][q], tl[c][q], x, 0.f);
+              }
             }
           }
         }
-        if (m < a.M) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int n = n0 + 16 * h + q;
-            if (n < a.N) {
-              cplx* p = out + m + (size_t)a.ldo * n;
-              cplx r = mk(a.alpha * cre[q], a.alpha * cim[q]);
-              if (a.accumulate) r = cadd(*p, r);
-              *p = r;
-            }
-          }
+        for (int q = 0; q < 16; ++q) {
+          const int n = n0 + 16 * h + q;
+          if (m >= a.M || n >= a.N) continue;
+          int ex[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ex[c] = ea[c] + eB[c * eBs + n];
+          const int E0 = max(ex[0], max(ex[1], ex[2]));
+          // component values relative to 2^E0 (factors <= 1: exact scaling,
+          // or below the double-float precision of the largest one)
+          float h0 = scalbnf(th[0][q], ex[0] - E0), l0 = scalbnf(tl[0][q], ex[0] - E0);
+          float h1 = scalbnf(th[1][q], ex[1] - E0), l1 = scalbnf(tl[1][q], ex[1] - E0);
+          float h2 = scalbnf(th[2][q], ex[2] - E0), l2 = scalbnf(tl[2][q], ex[2] - E0);
+          // re = T1 - T2, im = T3 - T1 - T2
+          float rh = h0, rl = l0;
+          df_add_part(rh, rl, -h1, -l1);
+          float ih = h2, il = l2;
+          df_add_part(ih, il, -h0, -l0);
+          df_add_part(ih, il, -h1, -l1);
+          // hi 2^E0 + lo 2^E0 as doubles built from the FP32 bit patterns
+          // (exponent rebias plus E0 by integer arithmetic): one FP64
+          // addition per part
+          const int Es = E0 + a.alpha_exp;
+          cplx r = mk(f2d_scaled(rh, Es, a.alpha_neg) + f2d_scaled(rl, Es, a.alpha_neg),
+                      f2d_scaled(ih, Es, a.alpha_neg) + f2d_scaled(il, Es, a.alpha_neg));
+          cplx* p = out + m + (size_t)a.ldo * n;
+          if (a.accumulate) r = cadd(*p, r);
+          *p = r;
         }
       }
     }
@@ -358,54 +385,121 @@ DV void comps(cplx x, double (&c)[3]) {
   c[2] = x.x + x.y;
 }
 
-// Per (row, chunk, product component): exponent e with max |x| 2^-e < 1.
-// One warp per (row, chunk): lanes stride over the chunk.
-__global__ void split_exp_kernel(SplitView v, int Kc, int nchunks, int* e) {
-  const int warps = blockDim.x >> 5;
-  const long long task = (long long)blockIdx.x * warps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (task >= (long long)v.R * nchunks) return;
-  const int r = (int)(task % v.R), z = (int)(task / v.R);
-  const int k0 = z * Kc, k1 = min(v.K, k0 + Kc);
-  double mx[3] = {0.0, 0.0, 0.0};
-  for (int k = k0 + lane; k < k1; k += 32) {
-    double c[3];
-    comps(view_at(v, r, k), c);
-    for (int q = 0; q < 3; ++q) mx[q] = fmax(mx[q], fabs(c[q]));
+// Splitting, one CTA per (32 rows, K-chunk): pass 1 finds each row's
+// per-component exponent e (max |x| 2^-e < 1) over the chunk, pass 2 cuts
+// the digits.  Each 32 x 64 slab of the operand goes through shared memory,
+// read along whichever index is contiguous in memory and written as 64
+// consecutive BF16 digits per row and plane.  No FP64 arithmetic beyond one
+// addition (re + im): the magnitudes are compared as integers and the digits
+// cut from the IEEE bit pattern (on this GPU the FP64 pipe retires two
+// multiply-adds per clock per SM).
+constexpr int kSplitRows = 32;
+constexpr int kSplitThreads = 256;
+
+// |x| as an ordered integer key (the IEEE bits without the sign).
+DV long long mag_key(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll; }
+// e with |x| 2^-e < 1 for the value whose key is given (ilogb + 1; 0 for 0).
+DV int key_exponent(long long key) {
+  if (key == 0) return 0;
+  const int ex = (int)(key >> 52);
+  return ex == 0 ? -1021 : ex - 1022;  // subnormal: below 2^-1022
+}
+// round(v 2^(nbits - e)) as an integer, |v| < 2^e: from v = M 2^E (M the
+// 53-bit significand) by a rounding right shift.
+DV long long fixed_point(double v, int e, int nbits) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  long long M = b & 0xFFFFFFFFFFFFFll;
+  int E;
+  if (ex == 0) {
+    E = -1074;
+  } else {
+    M |= 1ll << 52;
+    E = ex - 1075;
   }
-  for (int q = 0; q < 3; ++q)
-    for (int o = 16; o >= 1; o >>= 1) mx[q] = fmax(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
-  if (lane == 0)
-    for (int q = 0; q < 3; ++q)
-      e[((size_t)q * nchunks + z) * v.R + r] = (mx[q] > 0.0) ? ilogb(mx[q]) + 1 : 0;
+  const int sh = E - e + nbits;
+  long long X;
+  if (M == 0 || sh < -62) X = 0;
+  else if (sh >= 0) X = M << sh;  // not reached for |v| < 2^e, nbits <= 46
+  else X = (M + (1ll << (-sh - 1))) >> (-sh);
+  return b < 0 ? -X : X;
 }
 
-// Digit planes: plane (q * S + j) holds digit j of component q, row-major
-// [R][ldk] BF16 (K contiguous).  One thread per (r, k).
-__global__ void split_digit_kernel(SplitView v, int Kc, int nchunks, const int* e, int S, __nv_bfloat16* planes,
-                                   long long ldk) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)v.R * v.K) return;
-  // k fastest when the operand is K-contiguous, r fastest otherwise (coalesced reads)
-  int r, k;
-  if (v.ks == 1) {
-    k = (int)(idx % v.K);
-    r = (int)(idx / v.K);
-  } else {
-    r = (int)(idx % v.R);
-    k = (int)(idx / v.R);
-  }
-  const int z = k / Kc;
-  double c[3];
-  comps(view_at(v, r, k), c);
-  const size_t plane = (size_t)v.R * ldk;
-  for (int q = 0; q < 3; ++q) {
-    double x = ldexp(c[q], -e[((size_t)q * nchunks + z) * v.R + r]);  // |x| < 1
-    for (int j = 0; j < S; ++j) {
-      const double d = rint(ldexp(x, 7 + 8 * j));  // |d| <= 128, exact in BF16
-      x -= ldexp(d, -7 - 8 * j);                    // exact
-      planes[(size_t)(q * S + j) * plane + (size_t)r * ldk + k] = __float2bfloat16_rn((float)d);
+DV void split_load(const SplitView& v, int r0, int k0, int k1, cplx (*tile)[kSlab + 1]) {
+  if (v.rs == 1 && v.ks != 1) {  // rows contiguous: consecutive threads along r
+    for (int idx = threadIdx.x; idx < kSplitRows * kSlab; idx += kSplitThreads) {
+      const int r = idx % kSplitRows, k = idx / kSplitRows;
+      tile[r][k] = (r0 + r < v.R && k0 + k < k1) ? view_at(v, r0 + r, k0 + k) : mk(0, 0);
     }
+  } else {  // K contiguous (or neither): consecutive threads along k
+    for (int idx = threadIdx.x; idx < kSplitRows * kSlab; idx += kSplitThreads) {
+      const int k = idx % kSlab, r = idx / kSlab;
+      tile[r][k] = (r0 + r < v.R && k0 + k < k1) ? view_at(v, r0 + r, k0 + k) : mk(0, 0);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSplitThreads)
+    split_kernel(SplitView v, int Kc, int nchunks, int S, int* e, __nv_bfloat16* planes, long long ldk) {
+  __shared__ cplx tile[kSplitRows][kSlab + 1];
+  __shared__ long long mx[3][kSplitThreads / kSplitRows][kSplitRows];
+  __shared__ int esh[3][kSplitRows];
+  const int r0 = blockIdx.x * kSplitRows, z = blockIdx.y;
+  const int kb = z * Kc, ke = min(v.K, kb + Kc);
+  const int tid = threadIdx.x;
+  // pass 1: largest magnitude per row and component
+  const int pr = tid % kSplitRows, pg = tid / kSplitRows;
+  long long k0m = 0, k1m = 0, k2m = 0;
+  for (int k0 = kb; k0 < ke; k0 += kSlab) {
+    split_load(v, r0, k0, ke, tile);
+    __syncthreads();
+    for (int k = pg; k < kSlab; k += kSplitThreads / kSplitRows) {
+      const cplx x = tile[pr][k];
+      k0m = max(k0m, mag_key(x.x));
+      k1m = max(k1m, mag_key(x.y));
+      k2m = max(k2m, mag_key(x.x + x.y));
+    }
+    __syncthreads();
+  }
+  mx[0][pg][pr] = k0m;
+  mx[1][pg][pr] = k1m;
+  mx[2][pg][pr] = k2m;
+  __syncthreads();
+  if (tid < 3 * kSplitRows) {
+    const int q = tid / kSplitRows, r = tid % kSplitRows;
+    long long g = 0;
+    for (int j = 0; j < kSplitThreads / kSplitRows; ++j) g = max(g, mx[q][j][r]);
+    const int ex = key_exponent(g);
+    esh[q][r] = ex;
+    if (r0 + r < v.R) e[((size_t)q * nchunks + z) * v.R + r0 + r] = ex;
+  }
+  __syncthreads();
+  // pass 2: balanced base-256 digits of round(x 2^(8S-1)), |x| = |v| 2^-e < 1:
+  // x ~ sum_j q_j 2^(-7-8j) with |q_j| <= 128
+  const size_t plane = (size_t)v.R * ldk;
+  const int nbits = 8 * S - 1;
+  const int kk = tid % kSlab, rg = tid / kSlab;
+  for (int k0 = kb; k0 < ke; k0 += kSlab) {
+    split_load(v, r0, k0, ke, tile);
+    __syncthreads();
+    if (k0 + kk < ke)
+      for (int r = rg; r < kSplitRows; r += kSplitThreads / kSlab) {
+        if (r0 + r >= v.R) break;
+        const cplx x = tile[r][kk];
+        const double c[3] = {x.x, x.y, x.x + x.y};
+        __nv_bfloat16* dst = planes + (size_t)(r0 + r) * ldk + k0 + kk;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          long long X = fixed_point(c[q], esh[q][r], nbits);
+          for (int j = S - 1; j >= 1; --j) {
+            const int dgt = (int)((X + 128) & 255) - 128;
+            X = (X - dgt) >> 8;
+            dst[(size_t)(q * S + j) * plane] = __float2bfloat16_rn((float)dgt);
+          }
+          dst[(size_t)(q * S) * plane] = __float2bfloat16_rn((float)X);
+        }
+      }
+    __syncthreads();
   }
 }
 
@@ -487,16 +581,8 @@ cudaError_t tc_split(const TcOperandView& ov, int S, TcOperand* out, void* buf, 
   out->ldk = ldk;
   out->nchunks = nchunks;
   SplitView v{ov.X, ov.rs, ov.ks, ov.R, ov.K, ov.conj, ov.tri_mode, ov.tri};
-  {
-    const long long tasks = (long long)ov.R * nchunks;
-    const int threads = 256, per = threads / 32;
-    split_exp_kernel<<<(unsigned)((tasks + per - 1) / per), threads, 0, s>>>(v, Kc, nchunks, out->e);
-  }
-  {
-    const long long n = (long long)ov.R * ov.K;
-    split_digit_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, Kc, nchunks, out->e, S,
-                                                                    reinterpret_cast<__nv_bfloat16*>(buf), ldk);
-  }
+  const dim3 grid((ov.R + kSplitRows - 1) / kSplitRows, nchunks);
+  split_kernel<<<grid, kSplitThreads, 0, s>>>(v, Kc, nchunks, S, out->e, reinterpret_cast<__nv_bfloat16*>(buf), ldk);
   return cudaGetLastError();
 }
 
@@ -526,12 +612,17 @@ cudaError_t tc_zgemm(const TcOperand& A, const TcOperand& B, cplx* out, long lon
   a.eA = A.e;
   a.eB = B.e;
   a.err = err;
-  const dim3 grid((M + kTcM - 1) / kTcM, (N + kTcN - 1) / kTcN, nz);
+  const dim3 grid((N + kTcN - 1) / kTcN, (M + kTcM - 1) / kTcM, nz);
+  // alpha must be a signed power of two (the callers use +-1)
+  int aexp = 0;
+  const double am = std::frexp(std::fabs(alpha), &aexp);
+  if (am != 0.5) return cudaErrorInvalidValue;
   if (nz == 1) {
     a.out = out;
     a.ldo = ldo;
     a.zstride = 0;
-    a.alpha = alpha;
+    a.alpha_exp = aexp - 1;
+    a.alpha_neg = alpha < 0.0;
     a.accumulate = accumulate;
     tc_zgemm_kernel<<<grid, kTcThreads, smem, s>>>(ma, mb, a);
     return cudaGetLastError();
@@ -540,7 +631,8 @@ cudaError_t tc_zgemm(const TcOperand& A, const TcOperand& B, cplx* out, long lon
   a.out = part;
   a.ldo = M;
   a.zstride = (long long)M * N;
-  a.alpha = 1.0;
+  a.alpha_exp = 0;
+  a.alpha_neg = 0;
   a.accumulate = 0;
   tc_zgemm_kernel<<<grid, kTcThreads, smem, s>>>(ma, mb, a);
   e = cudaGetLastError();

@@ -694,4 +694,19 @@ cudaError_t gemm_uh_r(const cplx* U, int ldu, int M, int K, const cplx* R, int l
   return cudaGetLastError();
 }
 
+// ---- watchdog check -----------------------------------------------------------
+__global__ void watchdog_kernel(GridBar* bar) {
+  if (blockIdx.x == 0) return;  // never arrives: the others' wait must expire
+  GridSync gs{bar, 0u};
+  grid_sync(gs);
+}
+
+cudaError_t watchdog_probe(const CoopWs& ws, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  GridBar* bar = ws.bar;
+  void* args[] = {&bar};
+  return cudaLaunchCooperativeKernel((void*)watchdog_kernel, dim3(2), dim3(32), args, 0, s);
+}
+
 }  // namespace hk

@@ -36,6 +36,7 @@ def main():
     ap.add_argument("--surrogate", action="store_true", help="the surrogate network only")
     ap.add_argument("--profile", action="store_true", help="print the per-class profile record")
     ap.add_argument("--tensor", action="store_true", help="mixed precision with the tensor-core QR")
+    ap.add_argument("--steps", type=int, default=1, help="RK4 steps with --step (the first sets up workspaces)")
     args = ap.parse_args()
     from paper_2403_04946_gb300 import binding
     import synthetic
@@ -60,11 +61,12 @@ def main():
     if args.profile:
         print_profile(ctx.hopf_profile_read(reset=True))
     if args.step:
-        t0 = time.time()
-        ctx.hopf_step(t, 1.2e-5, 1)
-        print(f"hopf_step: {time.time() - t0:.3f} s")
-        if args.profile:
-            print_profile(ctx.hopf_profile_read(reset=True))
+        for s in range(args.steps):
+            t0 = time.time()
+            ctx.hopf_step(t, 1.2e-5, 1)
+            print(f"hopf_step {s}: {time.time() - t0:.3f} s")
+            if args.profile:
+                print_profile(ctx.hopf_profile_read(reset=True))
     ctx.tt_free(big)
     ctx.tt_free(t)
     ctx.close()
