@@ -266,7 +266,7 @@ def roofline(prof, mixed, peaks):
             "frac": achieved / peak, "peak_source": src, "traffic": None}
 
 
-def natural_state_error(w, stream, nsteps=3):
+def natural_state_error(w, stream, nsteps=3, qr_method=1):
     """Mixed vs FP64 after nsteps from the physical C3 initial state: the
     Gaussian with the C3 mean and cell covariance (correlated), built by
     hopf_init_gaussian (TT-cross at this size; every interior rank at the
@@ -280,6 +280,7 @@ def natural_state_error(w, stream, nsteps=3):
     out, rate = {}, {}
     for prec in (B.HOPF_FP64, B.HOPF_MIXED):
         ctx = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=0.0, stream=stream, precision=prec)
+        ctx.hopf_set_qr_method(qr_method)
         t = ctx.hopf_init_gaussian(m0, C0)
         r0 = ctx.tt_get_ranks(t)
         ctx.hopf_step(t, w.dt, 1)  # first step: workspace set-up, untimed
@@ -311,7 +312,7 @@ def natural_state_error(w, stream, nsteps=3):
                                     "note": "one RK4 step timed after one untimed step from the same state"}}
 
 
-def ensemble_rate(stream_int, nsteps=1):
+def ensemble_rate(stream_int, nsteps=1, qr_method=1):
     """An ensemble of uneven instances (saturated states, ranks at their
     caps), one RK4 step each: one instance at a time on the whole GPU versus
     all at once (hopf_step_ensemble, each context limited to its share of
@@ -330,6 +331,7 @@ def ensemble_rate(stream_int, nsteps=1):
             s = torch.cuda.Stream() if mode == "concurrent" else None
             ctx = B.Context(d=d, n=n, nu=0.02, tol=1e-7, rank_cap=r, L=12.4,
                             stream=s.cuda_stream if s is not None else stream_int, precision=B.HOPF_MIXED)
+            ctx.hopf_set_qr_method(qr_method)
             if mode == "concurrent":
                 ctx.hopf_set_max_ctas(share)
             members.append((ctx, ctx.tt_from_host(cores, max_rank=r), s))
@@ -450,8 +452,10 @@ def run_ours(args, rank, world, local_rank):
         pass
 
     # primary arm: mixed precision (FP64 Householder scalars and SVD, double-float QR arithmetic)
+    qr_method = binding.HOPF_QR_TENSOR if args.qr_method == "tensor" else binding.HOPF_QR_DOUBLEFLOAT
     ctx = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L,
                           stream=stream.cuda_stream, precision=binding.HOPF_MIXED)
+    ctx.hopf_set_qr_method(qr_method)
     t = ctx.tt_from_host(cores, max_rank=w.cap)
     clocks = ClockSampler(gpu_id)
     clocks.start()
@@ -490,8 +494,8 @@ def run_ours(args, rank, world, local_rank):
     ctx.tt_free(t)
     ctx.close()
 
-    err = natural_state_error(w, stream.cuda_stream) if not args.no_error_check else None
-    ens = ensemble_rate(stream.cuda_stream) if not args.no_error_check else None
+    err = natural_state_error(w, stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
+    ens = ensemble_rate(stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
     sur = surrogate_rate() if (world == 1 and not args.no_surrogate) else None
 
     result = None
@@ -510,6 +514,8 @@ def run_ours(args, rank, world, local_rank):
                    "sample": ("one operator apply + rank-6r rounding (first RK4 stage) on a 6-core slice "
                               f"(d=6, n=128, r=64) of the saturated state, {sec:.1f} s; step time extrapolated by "
                               f"(d-1)/5 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")}
+        cfg = config_dict(w)
+        cfg["qr_method"] = args.qr_method
         result = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
@@ -517,7 +523,7 @@ def run_ours(args, rank, world, local_rank):
             "dtype": ("f64 storage; QR trailing products and Q applications of tall factors on tensor cores "
                       "(bf16 digit products, 5 digits, exact f32 accumulation, 3M complex); QR panels and merges "
                       "in double-float (2 x f32); f64 Householder scalars and SVD"),
-            "data": "synthetic", "config": config_dict(w),
+            "data": "synthetic", "config": cfg,
             "roofline": roofline(prof, True, peaks),
             "tensor_core_roofline": tc_roofline(prof, peaks),
             "kernel_shares": shares,
@@ -546,6 +552,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--qr-method", choices=["tensor", "doublefloat"], default="tensor",
+                    help="how the mixed arm factors its tall flattenings (hopf_set_qr_method)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -69,12 +69,14 @@ typedef struct {
                   /* hopf_init_gaussian to sqrt(36.8 / min_k C0_kk)       */
   double tol;     /* relative rounding tolerance used by hopf_step        */
   int rank_cap;   /* rank cap used by hopf_step                           */
-  int precision;  /* HOPF_FP64: every step in FP64.  HOPF_MIXED: QR     */
-                  /* panels and trailing updates, Q applications and      */
-                  /* merge products run in double-float arithmetic (each  */
-                  /* value an unevaluated sum of two FP32 numbers, about  */
-                  /* 1e-13 relative); Householder scalars, the SVD that   */
-                  /* sets the ranks and all storage stay FP64.            */
+  int precision;  /* HOPF_FP64: every step in FP64.  HOPF_MIXED: the    */
+                  /* dense products of the rounding (QR trailing updates,  */
+                  /* Q applications, merges, U^H R) run on the tensor     */
+                  /* cores as digit-split BF16 products with exact FP32   */
+                  /* accumulation, and the QR panels in double-float      */
+                  /* arithmetic (hopf_set_qr_method); Householder         */
+                  /* scalars, the SVD that sets the ranks and all storage */
+                  /* stay FP64.                                           */
   int nonlinear;  /* 1: full Burgers generator; 0: drop the (i/2) D1 term */
 } hopf_params;
 
@@ -138,13 +140,17 @@ hopf_status hopf_set_wait_limit(hopf_ctx* ctx, double seconds);
 hopf_status hopf_check_watchdog(hopf_ctx* ctx);
 /* How the mixed-precision rounding factors its tall flattenings (QR of
  * n p x K matrices, App. A Alg. 1/2; in HOPF_FP64 every QR is FP64).
- * HOPF_QR_DOUBLEFLOAT (the default): one cooperative Householder kernel in
+ * HOPF_QR_TENSOR (the default): for factors of at least 4096 rows,
+ * blocked Householder in outer panels of 128 columns whose Gram, trailing
+ * products and Q applications run on the tensor cores (digit-split BF16
+ * products with exact FP32 accumulation, see hopf_tc_zgemm; about 1e-9
+ * relative per step), as do the merge products of the orthogonalisation
+ * sweep and the projections U^H R of the truncation; each panel by the
+ * cooperative kernel below.  1.2x the step rate of the alternative on the
+ * d = 32, n = 128, rank-64 workload.
+ * HOPF_QR_DOUBLEFLOAT: one cooperative Householder kernel per factor in
  * double-float arithmetic (about 1e-13 relative per step).
- * HOPF_QR_TENSOR: for factors of at least 4096 rows, blocked Householder in
- * outer panels whose Gram, trailing products and Q applications run on the
- * tensor cores (digit-split BF16 products with exact FP32 accumulation, see
- * hopf_tc_zgemm; about 1e-9 relative per step); panels and scalars as in
- * the default.  Errors: HOPF_EINVAL (unknown method). */
+ * Errors: HOPF_EINVAL (unknown method). */
 enum { HOPF_QR_DOUBLEFLOAT = 0, HOPF_QR_TENSOR = 1 };
 hopf_status hopf_set_qr_method(hopf_ctx* ctx, int method);
 /* Limits every cooperative kernel launched by this context to max_ctas

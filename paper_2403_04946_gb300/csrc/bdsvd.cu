@@ -71,10 +71,12 @@ DV void house_scalars(cplx alpha, double xnorm2, cplx* tau, cplx* scale, double*
 // column i's half is done.
 __global__ void __launch_bounds__(kBdThreads, 1)
 gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* tauq, cplx* taup,
-             CoopWs ws) {
+             CoopWs ws, cplx* rows_global) {
   extern __shared__ __align__(16) unsigned char bd_smem[];
-  cplx* rows = reinterpret_cast<cplx*>(bd_smem);  // nloc x n, row-major
-  cplx* fv = rows + (size_t)nloc * n;            // conj(tau) w_c
+  // own rows (nloc x n, row-major) in shared memory, or, for a factor too
+  // large for it, in this CTA's slice of a global workspace (L2-resident)
+  cplx* rows = rows_global ? rows_global + (size_t)blockIdx.x * nloc * n : reinterpret_cast<cplx*>(bd_smem);
+  cplx* fv = rows_global ? reinterpret_cast<cplx*>(bd_smem) : rows + (size_t)nloc * n;  // conj(tau) w_c
   cplx* nrow = fv + n;                           // updated row i
   cplx* uv = nrow + n;                           // right reflector u
   cplx* vloc = uv + n;                           // v_r of own rows (nloc)
@@ -229,9 +231,13 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
   }
 }
 
-int gebrd_grid(int n, int sms, int* nloc_out, size_t* smem_out) {
+// Grid of the bidiagonalisation: rows resident in shared memory when they
+// fit (*global_rows = false), else all SMs with the rows in a global
+// workspace of gebrd_rows_elems(n) elements (when allowed).
+int gebrd_grid(int n, int sms, int* nloc_out, size_t* smem_out, bool allow_global, bool* global_rows) {
   const DevInfo& di = dev_info();
   int G = std::max(1, std::min(sms, (n + 2) / 3));
+  *global_rows = false;
   for (;;) {
     const int nloc = (n + G - 1) / G;
     const size_t smem = ((size_t)nloc * n + 3 * (size_t)n + nloc) * sizeof(cplx);
@@ -240,24 +246,39 @@ int gebrd_grid(int n, int sms, int* nloc_out, size_t* smem_out) {
       *smem_out = smem;
       return G;
     }
-    if (G >= sms) return 0;
+    if (G >= sms) break;
     G = std::min(sms, G + 8);
   }
+  const int nloc = (n + G - 1) / G;
+  const size_t smem = (3 * (size_t)n + nloc) * sizeof(cplx);
+  if (!allow_global || smem + 8192 > (size_t)di.max_smem_optin) return 0;
+  *global_rows = true;
+  *nloc_out = nloc;
+  *smem_out = smem;
+  return G;
 }
 
-bool gebrd_fits(int n, const CoopWs& ws) {
+size_t gebrd_rows_elems(int n, int sms) {
+  const int G = std::max(1, std::min(sms, (n + 2) / 3));
+  return (size_t)(n + G) * (size_t)n;
+}
+
+bool gebrd_fits(int n, const CoopWs& ws, bool have_rows_ws) {
   int nloc;
   size_t smem;
-  return n >= 1 && gebrd_grid(n, coop_sms(ws), &nloc, &smem) > 0;
+  bool glob;
+  return n >= 1 && gebrd_grid(n, coop_sms(ws), &nloc, &smem, have_rows_ws, &glob) > 0;
 }
 
 cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cplx* taup,
-                  const CoopWs& ws, cudaStream_t s) {
+                  const CoopWs& ws, cudaStream_t s, cplx* rows_ws) {
   if (n <= 0) return cudaSuccess;
   int nloc;
   size_t smem;
-  const int G = gebrd_grid(n, coop_sms(ws), &nloc, &smem);
+  bool glob = false;
+  const int G = gebrd_grid(n, coop_sms(ws), &nloc, &smem, rows_ws != nullptr, &glob);
   if (G <= 0) return cudaErrorInvalidValue;
+  cplx* rows_global = glob ? rows_ws : nullptr;
   if ((size_t)2 * G * (n + 1) > ws.pc_elems || (size_t)6 * n > ws.wfin_elems || 2 * G > 1024)
     return cudaErrorInvalidValue;
   cudaError_t err = allow_smem((const void*)gebrd_kernel, smem);
@@ -265,7 +286,7 @@ cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cpl
   err = cudaMemsetAsync(&ws.bar->count, 0, sizeof(unsigned int), s);
   if (err != cudaSuccess) return err;
   CoopWs w = ws;
-  void* args[] = {&A, &lda, &n, &nloc, &d, &e, &tauq, &taup, &w};
+  void* args[] = {&A, &lda, &n, &nloc, &d, &e, &tauq, &taup, &w, &rows_global};
   return cudaLaunchCooperativeKernel((void*)gebrd_kernel, dim3(G), dim3(kBdThreads), args, smem, s);
 }
 

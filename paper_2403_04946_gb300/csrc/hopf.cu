@@ -62,6 +62,8 @@ struct RoundWs {
   cplx* G = nullptr;
   size_t gstride = 0;
   cplx* G2 = nullptr;
+  // rows of a bidiagonalisation too large for shared memory
+  cplx* bd_rows = nullptr;
 };
 
 struct hopf_ctx {
@@ -80,7 +82,7 @@ struct hopf_ctx {
   int coop_kcap = 0;
   int device = 0;
   int svd_method = HOPF_SVD_AUTO;
-  int qr_method = HOPF_QR_DOUBLEFLOAT;
+  int qr_method = HOPF_QR_TENSOR;
   unsigned int wait_limit_us = 0;  // grid-barrier wait limit (0: the default)
   // persistent staging of point / moment evaluation (grown on demand)
   int* ev_idx = nullptr;
@@ -402,7 +404,7 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   dfree(w.sig); dfree(w.perm);
   dfree(w.bd_d); dfree(w.bd_e); dfree(w.bd_tauq); dfree(w.bd_taup); dfree(w.bd_a2);
   dfree(w.bd_info); dfree(w.bd_X); dfree(w.bd_Zs);
-  dfree(w.G); dfree(w.G2);
+  dfree(w.G); dfree(w.G2); dfree(w.bd_rows);
   w = RoundWs{};
   const size_t elems = std::max(need, w.elems);
   const int d = t->d;
@@ -433,6 +435,7 @@ hopf_status round_reserve(hopf_ctx* ctx, const hopf_tt* t) {
   w.gstride = hk::qr_tc_gram_elems(K);
   CK(dalloc(&w.G, (size_t)d * w.gstride));
   CK(dalloc(&w.G2, w.gstride));
+  CK(dalloc(&w.bd_rows, hk::gebrd_rows_elems(K, hk::dev_info().sm_count)));
   w.elems = elems;
   w.d = d;
   w.kcap = K;
@@ -720,7 +723,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
     // their singular values and left singular vectors, which is all the
     // truncation uses (the projection below is S = U^H R).  The LQ is FP64
     // like the SVD, on the reflector slot c that this step no longer needs.
-    const bool use_bd = ctx->svd_method != HOPF_SVD_JACOBI && hk::gebrd_fits(pp, ctx->coop);
+    const bool use_bd = ctx->svd_method != HOPF_SVD_JACOBI && hk::gebrd_fits(pp, ctx->coop, true);
     if (use_bd) {
       if (case1) {
         CK(cudaMemcpyAsync(w.Mb, w.Rb, (size_t)pp * cols * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -731,7 +734,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
         LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::extract_r(w.Mb, cols, pp, pp, w.Jb, pp, ctx->stream));
         LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::conj_transpose(w.Jb, pp, pp, pp, w.Mb, pp, ctx->stream));
       }
-      LAUNCH(HOPF_K_SVD, gebrd_flops(pp), 0, 1, hk::gebrd(w.Mb, pp, pp, w.bd_d, w.bd_e, w.bd_tauq, w.bd_taup, ctx->coop, ctx->stream));
+      LAUNCH(HOPF_K_SVD, gebrd_flops(pp), 0, 1, hk::gebrd(w.Mb, pp, pp, w.bd_d, w.bd_e, w.bd_tauq, w.bd_taup, ctx->coop, ctx->stream, w.bd_rows));
       LAUNCH(HOPF_K_SVD, 0, 0, 2, hk::bd_sigma(w.bd_d, w.bd_e, pp, w.bd_a2, w.bd_info, w.sig, ctx->stream));
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::bd_rank(w.sig, pp, ctx->d_dbl + 1, cap, forced_c, ctx->d_int, ctx->d_dbl + 2, w.sig + pp, ctx->stream));
       TRY(read_small(ctx, 3, 5));
@@ -1312,7 +1315,7 @@ void hopf_destroy(hopf_ctx* ctx) {
   dfree(w.sig); dfree(w.perm);
   dfree(w.bd_d); dfree(w.bd_e); dfree(w.bd_tauq); dfree(w.bd_taup); dfree(w.bd_a2);
   dfree(w.bd_info); dfree(w.bd_X); dfree(w.bd_Zs);
-  dfree(w.G); dfree(w.G2);
+  dfree(w.G); dfree(w.G2); dfree(w.bd_rows);
   dfree(ctx->tcbuf);
   dfree(ctx->ev_idx); dfree(ctx->ev_vals); dfree(ctx->ev_out);
   dfree(ctx->coop.bar); dfree(ctx->coop.pr); dfree(ctx->coop.pc);

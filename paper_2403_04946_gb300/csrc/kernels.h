@@ -84,9 +84,12 @@ cudaError_t rank_select(const cplx* M, int ldm, int nr, int nc, const double* ep
 // tails below the diagonal, right reflector tails right of the
 // superdiagonal); B: diagonal d[n], superdiagonal e[n-1], both real.
 // Cooperative launch, one grid barrier per column.
+// rows_ws (may be NULL): gebrd_rows_elems(n) elements where the rows go when
+// they do not fit in shared memory (L2-resident for the sizes met here).
 cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cplx* taup,
-                  const CoopWs& ws, cudaStream_t s);
-bool gebrd_fits(int n, const CoopWs& ws);  // shared-memory resident rows fit
+                  const CoopWs& ws, cudaStream_t s, cplx* rows_ws = nullptr);
+bool gebrd_fits(int n, const CoopWs& ws, bool have_rows_ws = false);
+size_t gebrd_rows_elems(int n, int sms);
 // All singular values of B, sorted descending, into sig[n]; a2 (float2
 // [2n]) and info (double [4]) are scratch kept for bd_vectors.
 cudaError_t bd_sigma(const double* d, const double* e, int n, float2* a2, double* info, double* sig,

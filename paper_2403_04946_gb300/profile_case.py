@@ -37,12 +37,16 @@ def main():
     ap.add_argument("--profile", action="store_true", help="print the per-class profile record")
     ap.add_argument("--tensor", action="store_true", help="mixed precision with the tensor-core QR")
     ap.add_argument("--steps", type=int, default=1, help="RK4 steps with --step (the first sets up workspaces)")
+    ap.add_argument("--cdf", action="store_true",
+                    help="the paper's CDF equation on a saturated state, explicit midpoint steps (--d 20 --n 64 --r 128)")
     args = ap.parse_args()
     from paper_2403_04946_gb300 import binding
     import synthetic
 
     if args.surrogate:
         return surrogate_case(binding, synthetic)
+    if args.cdf:
+        return cdf_case(binding, synthetic, args)
 
     cores, _ = synthetic.saturated_tt_cores(args.d, args.n, args.r, seed=0)
     ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r, L=12.4,
@@ -68,6 +72,27 @@ def main():
             if args.profile:
                 print_profile(ctx.hopf_profile_read(reset=True))
     ctx.tt_free(big)
+    ctx.tt_free(t)
+    ctx.close()
+
+
+def cdf_case(binding, synthetic, args):
+    """Explicit-midpoint steps of the CDF equation (box [-1.3, 1.3], gamma =
+    0.01) on a saturated state with every interior rank at --r."""
+    cores, _ = synthetic.saturated_tt_cores(args.d, args.n, args.r, seed=0)
+    ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r,
+                          precision=binding.HOPF_MIXED if args.mixed else binding.HOPF_FP64)
+    ctx.hopf_set_equation(binding.HOPF_EQ_CDF, 1.3)
+    if args.profile:
+        ctx.hopf_profile_enable(True)
+    t = ctx.tt_from_host(cores, max_rank=args.r)
+    for s in range(args.steps):
+        t0 = time.time()
+        out = ctx.hopf_step_scheme(t, binding.HOPF_MIDPOINT, 1e-4, 1, record=True)
+        print(f"CDF midpoint step {s} d={args.d} n={args.n} r={args.r}: {time.time() - t0:.3f} s, "
+              f"max ranks per rounding {out['ranks'].max(axis=1).tolist()}")
+        if args.profile:
+            print_profile(ctx.hopf_profile_read(reset=True))
     ctx.tt_free(t)
     ctx.close()
 

@@ -104,7 +104,7 @@ def test_c3_slice_apply_and_exact_rounding(B, c3_slice):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tensor"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed-doublefloat", "mixed-tensor"])
 def test_c3_slice_truncation_at_planted_gap(B, precision):
     """A rank-64 state of norm 1 plus a perturbation of norm 1e-9 and ranks
     320, so the flattenings are 49152 x 384 as in C3 and the tolerance puts
@@ -122,8 +122,7 @@ def test_c3_slice_truncation_at_planted_gap(B, precision):
     mixed = precision.startswith("mixed")
     ctx = B.Context(d=D, n=N, nu=NU3, tol=TOL3, rank_cap=R, L=L3,
                     precision=B.HOPF_MIXED if mixed else B.HOPF_FP64)
-    if precision == "mixed-tensor":
-        ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR)
+    ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR if precision == "mixed-tensor" else B.HOPF_QR_DOUBLEFLOAT)
     t = ctx.tt_from_host(x, max_rank=384)
     disc, _ = ctx.tt_round(t, TOL3, R)
     assert ctx.tt_get_ranks(t) == wranks
@@ -138,7 +137,7 @@ def test_c3_slice_truncation_at_planted_gap(B, precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tensor"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed-doublefloat", "mixed-tensor"])
 def test_c3_slice_rk4_step(B, c3_slice, c3_step_oracle, precision):
     """One fused hopf_step of the saturated C3 slice (dt = 1.2e-5, tol 1e-7,
     cap 64) with the oracle's ranks replayed: four K-roundings of 384-rank
@@ -150,8 +149,7 @@ def test_c3_slice_rk4_step(B, c3_slice, c3_step_oracle, precision):
     mixed = precision.startswith("mixed")
     ctx = B.Context(d=D, n=N, nu=NU3, tol=TOL3, rank_cap=R, L=L3,
                     precision=B.HOPF_MIXED if mixed else B.HOPF_FP64)
-    if precision == "mixed-tensor":
-        ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR)
+    ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR if precision == "mixed-tensor" else B.HOPF_QR_DOUBLEFLOAT)
     t = ctx.tt_from_host(x, max_rank=R)
     out = ctx.hopf_step(t, DT3, 1, record=True, replay=log)
     assert np.array_equal(out["ranks"], log)
@@ -260,4 +258,24 @@ def test_mixed_tensor_core_qr_ragged_panels(B):
     for C in got[:-1]:
         V = tt.V(C)
         assert np.abs(V.conj().T @ V - np.eye(V.shape[1])).max() < 1e-8
+    ctx.close()
+
+
+def test_bidiagonalisation_beyond_shared_memory(B):
+    """Ranks [1, 48, 1536, 48, 1] at n = 48: the truncation sweep factors a
+    2304 x 1536 flattening and bidiagonalises its 1536 x 1536 triangle, whose
+    rows no longer fit in the CTAs' shared memory (the explicit midpoint of
+    the paper's CDF workload meets such factors at rank 128).  At tol = 0
+    the rounding reproduces the tensor and the oracle's rounding."""
+    d, n = 4, 48
+    x = synthetic.random_tt_cores(d, n, [1, 48, 1536, 48, 1], seed=41)
+    want, wranks, _ = tt.round_tt(x, 0.0, 4096)
+    assert wranks == [1, 48, 1536, 48, 1]
+    ctx = B.Context(d=d, n=n, nu=0.02, tol=0.0, rank_cap=1536, L=4.0)
+    t = ctx.tt_from_host(x, max_rank=1536)
+    ctx.tt_round(t, 0.0, 1536, forced_ranks=wranks)
+    got = ctx.tt_to_host(t)
+    e, e_in = rel_tt(got, want), rel_tt(got, x)
+    print(f"\n1536 x 1536 bidiagonalisation: vs oracle {e:.2e}, vs input {e_in:.2e}")
+    assert e < 1e-12 and e_in < 1e-12
     ctx.close()
