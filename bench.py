@@ -312,6 +312,35 @@ def natural_state_error(w, stream, nsteps=3, qr_method=1):
                                     "note": "one RK4 step timed after one untimed step from the same state"}}
 
 
+def paper_workload(stream_int, qr_method=1, d=20, n=64, r=128):
+    """The paper's own experiment at its largest size (Sec. 5.1): the CDF
+    equation with N = 20, n = 64 points per variable on [-1.3, 1.3]^20 and
+    the explicit step-truncation midpoint scheme, on a saturated synthetic
+    state with every interior rank at 128 (the paper reports ranks above
+    100).  One untimed step (workspaces), one timed step."""
+    import torch
+    from paper_2403_04946_gb300 import binding as B
+    import synthetic
+    cores, _ = synthetic.saturated_tt_cores(d, n, r, seed=0)
+    ctx = B.Context(d=d, n=n, nu=0.01, tol=1e-7, rank_cap=r, stream=stream_int, precision=B.HOPF_MIXED)
+    ctx.hopf_set_qr_method(qr_method)
+    ctx.hopf_set_equation(B.HOPF_EQ_CDF, 1.3)
+    t = ctx.tt_from_host(cores, max_rank=r)
+    ctx.hopf_step_scheme(t, B.HOPF_MIDPOINT, 1e-4, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.hopf_step_scheme(t, B.HOPF_MIDPOINT, 1e-4, 1)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ctx.tt_free(t)
+    ctx.close()
+    return {"equation": "CDF (Eq. cdf-burgers, alpha = 0), box [-1.3, 1.3]^20", "d": d, "n": n, "rank": r,
+            "scheme": "explicit step-truncation midpoint (3 roundings per step)", "precision": "mixed",
+            "seconds_per_step": sec,
+            "paper_context": {"seconds_per_step": 45 * 60, "hardware": "Intel i9-7980XE workstation, CPU, FP64",
+                              "ranks": "above 100", "note": "context only: other hardware and precision"}}
+
+
 def ensemble_rate(stream_int, nsteps=1, qr_method=1):
     """An ensemble of uneven instances (saturated states, ranks at their
     caps), one RK4 step each: one instance at a time on the whole GPU versus
@@ -497,6 +526,7 @@ def run_ours(args, rank, world, local_rank):
     err = natural_state_error(w, stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
     ens = ensemble_rate(stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
     sur = surrogate_rate() if (world == 1 and not args.no_surrogate) else None
+    paper = paper_workload(stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
 
     result = None
     if rank == 0:
@@ -532,6 +562,7 @@ def run_ours(args, rank, world, local_rank):
             "mixed_vs_fp64_error": err,
             "ensemble": ens,
             "surrogate": sur,
+            "paper_workload": paper,
             "apply_gbs": apply_gbs,
             "jacobi_sweeps_per_svd": prof["svd"].get("sweeps", 0) / max(1, prof["svd"].get("count", 0)),
             "cpu_baseline": cpu,
