@@ -34,6 +34,55 @@ namespace hk {
 
 constexpr int kBdThreads = 256;
 
+// Values other CTAs published are read kBdBatch at a time per lane: the
+// loads of a batch are independent and in flight together, one L2 round
+// trip per batch on a path every column waits for; sums keep their order.
+constexpr int kBdBatch = 8;
+DV double sum_published(const double* p, int G) {  // lane-strided partial sum
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int g0 = lane; g0 < G; g0 += 32 * kBdBatch) {
+    double v[kBdBatch];
+#pragma unroll
+    for (int u = 0; u < kBdBatch; ++u) v[u] = (g0 + 32 * u < G) ? __ldcg(p + g0 + 32 * u) : 0.0;
+#pragma unroll
+    for (int u = 0; u < kBdBatch; ++u)
+      if (g0 + 32 * u < G) s += v[u];
+  }
+  return s;
+}
+DV cplx sum_published(const cplx* p, size_t stride, int G) {
+  const int lane = threadIdx.x & 31;
+  cplx s = mk(0, 0);
+  for (int g0 = lane; g0 < G; g0 += 32 * kBdBatch) {
+    cplx v[kBdBatch];
+#pragma unroll
+    for (int u = 0; u < kBdBatch; ++u) v[u] = (g0 + 32 * u < G) ? __ldcg(p + (size_t)(g0 + 32 * u) * stride) : mk(0, 0);
+#pragma unroll
+    for (int u = 0; u < kBdBatch; ++u)
+      if (g0 + 32 * u < G) s = cadd(s, v[u]);
+  }
+  return s;
+}
+// Sum over the block delivered to warp 0 only (the other warps' FP64 work
+// in a block-wide reduction costs more, on this GPU's narrow FP64 pipe,
+// than the column's arithmetic).  Warps whose `has` is false contribute
+// zero without reducing.  Ends with __syncthreads (so it also publishes
+// the block's shared-memory writes made before it).
+DV double sum_to_warp0(double v, bool has, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (has) v = warp_sum(v);
+  if (lane == 0) red[w] = has ? v : 0.0;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (lane < nw) ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  __syncthreads();
+  return s;
+}
+
 DV void house_scalars(cplx alpha, double xnorm2, cplx* tau, cplx* scale, double* beta) {
   // H^H [alpha; x] = [beta; 0] with H = I - tau v v^H, v = [1; x * scale]
   if (xnorm2 == 0.0 && alpha.y == 0.0) {
@@ -111,7 +160,7 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
     // (a) partial sums over own rows r > i
     double sq = 0.0;
     for (int lr = lr0 + tid; lr < nact; lr += blockDim.x) sq += cabs2(R(lr, i));
-    sq = block_sum(sq, dred);
+    sq = sum_to_warp0(sq, lr0 + 32 * wid < nact, dred);
     for (int c = i + 1 + tid; c < n; c += blockDim.x) {
       cplx acc = mk(0, 0);
       for (int lr = lr0; lr < nact; ++lr) acc = cfmac(R(lr, i), R(lr, c), acc);
@@ -124,9 +173,7 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
     if (grid_failed(ws.bar)) return;
     // (b1) left reflector of column i (every CTA), reduction of its columns
     if (wid == 0) {
-      double s2 = 0.0;
-      for (int gg = lane; gg < G; gg += 32) s2 += __ldcg(pr + gg);
-      s2 = warp_sum(s2);
+      const double s2 = warp_sum(sum_published(pr, G));
       if (lane == 0) {
         cplx tq, sc;
         double beta;
@@ -141,9 +188,7 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
     const cplx ctq = cconj(tq), cscq = cconj(scq);
     for (int cc = g + wid * G; cc < C; cc += nw * G) {
       const int c = i + 1 + cc;
-      cplx acc = mk(0, 0);
-      for (int gg = lane; gg < G; gg += 32) acc = cadd(acc, __ldcg(pc + (size_t)gg * pstride + c));
-      acc = warp_sum(acc);
+      const cplx acc = warp_sum(sum_published(pc + c, pstride, G));
       if (lane == 0) {
         const cplx a_ic = __ldcg(rowb + c);
         const cplx f = cmul(ctq, cadd(a_ic, cmul(cscq, acc)));
@@ -163,7 +208,7 @@ gebrd_kernel(cplx* A, int lda, int n, int nloc, double* dg, double* eg, cplx* ta
       nrow[c] = nr;
       if (c >= i + 2) sqp += cabs2(nr);
     }
-    sqp = block_sum(sqp, dred);  // its barriers also publish fv / nrow / vloc
+    sqp = sum_to_warp0(sqp, i + 1 + 32 * wid < n, dred);  // its barriers also publish fv / nrow / vloc
     if (owner && tid == 0) {
       R(i / G, i) = bc[2];
       dg[i] = bc[2].x;

@@ -174,23 +174,38 @@ struct GridSync {
   unsigned int target;  // used by thread 0 of each CTA
 };
 
+// Arrival is a release reduction (the CTA's writes, ordered before it by
+// the CTA barrier, become visible with it; the arriving thread does not
+// wait for a returned value), polling an acquire load: one L2 round trip
+// after the last arrival instead of a fence, a returning atomic and a
+// trailing fence.
+DV void bar_arrive_release(unsigned int* p) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+DV unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 DV void grid_sync(GridSync& gs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile int* verr = &gs.bar->err;
     gs.target += gridDim.x * gridDim.y * gridDim.z;
     if (*verr == 0) {
-      __threadfence();
-      atomicAdd(&gs.bar->count, 1u);
-      volatile unsigned int* vc = &gs.bar->count;
+      bar_arrive_release(&gs.bar->count);
       const unsigned int lim = *((volatile unsigned int*)&gs.bar->limit_us);
       const uint64_t limit_ns = lim ? (uint64_t)lim * 1000ull : kBarrierTimeoutNs;
-      const uint64_t t0 = global_ns();
+      uint64_t t0 = 0;
       unsigned int spins = 0;
-      while ((int)(*vc - gs.target) < 0) {
+      while ((int)(ld_acquire_gpu(&gs.bar->count) - gs.target) < 0) {
         if (((++spins) & 31u) == 0u) {
           if (*verr != 0) break;
-          if (global_ns() - t0 > limit_ns) {
+          const uint64_t now = global_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if (now - t0 > limit_ns) {
             atomicExch(&gs.bar->err, 1);
             break;
           }
@@ -198,7 +213,6 @@ DV void grid_sync(GridSync& gs) {
         __nanosleep(32);
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }

@@ -284,8 +284,10 @@ __device__ int grid_scale_exponent(const cplx* A, int lda, int r0, int r1, int k
   }
   grid_sync(gs);
   if (grid_failed(bar)) return 0;
+  // every warp takes the maximum over the CTAs' values, lanes in parallel
   double g = 0.0;
-  for (int c = 0; c < (int)gridDim.x; ++c) g = fmax(g, __ldcg(slot + c));
+  for (int c = threadIdx.x & 31; c < (int)gridDim.x; c += 32) g = fmax(g, __ldcg(slot + c));
+  for (int o = 16; o >= 1; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
   return (g > 0.0) ? ilogb(g) + 1 : 0;
 }
 
@@ -306,11 +308,27 @@ __device__ void to_df_in_place(cplx* buf, int n) {
   __syncthreads();
 }
 
+// Partials that other CTAs published are read kLoadBatch at a time: the
+// loads of a batch are independent and in flight together (one L2 round
+// trip per batch instead of one per CTA, on a path every column waits for);
+// the additions keep their order.
+constexpr int kLoadBatch = 8;
+
 // Sum over the G per-CTA partials of entry e (stride pstride) by one warp.
 __device__ __forceinline__ cplx reduce_partials(const cplx* pc, size_t pstride, int G, size_t e) {
   const int lane = threadIdx.x & 31;
   cplx acc = mk(0, 0);
-  for (int g = lane; g < G; g += 32) acc = cadd(acc, ld_cg(pc + (size_t)g * pstride + e));
+  for (int g0 = lane; g0 < G; g0 += 32 * kLoadBatch) {
+    cplx v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int g = g0 + 32 * u;
+      v[u] = (g < G) ? ld_cg(pc + (size_t)g * pstride + e) : mk(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u)
+      if (g0 + 32 * u < G) acc = cadd(acc, v[u]);
+  }
   return warp_sum(acc);
 }
 
@@ -324,6 +342,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
   cplx* wl = Ts + (size_t)nb * nb;  // [2*kNbMax]
   __shared__ double dred[32];
   __shared__ cplx bc[4];
+  __shared__ df2 bcd[4];  // mixed: conj(tau), conj(scale), scale, beta as double-float values
 
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -384,8 +403,18 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         // the FP32 range
         double sq = 0.0;
         for (int i = ilo + tid; i < r1; i += blockDim.x) sq += cabs2(df_to(xt[i - r0]));
-        sq = block_sum(sq, dred);
-        if (tid == 0) prp[g] = sq;
+        // only thread 0 needs the CTA's sum: warp sums in the warps that
+        // hold rows, then warp 0 over them (the FP64 pipe is 1/64 of the
+        // FP32 rate: a block-wide FP64 reduction in every warp costs more
+        // than the column's arithmetic)
+        if (ilo + 32 * wid < r1) sq = warp_sum(sq);
+        if (lane == 0) dred[wid] = sq;
+        __syncthreads();
+        if (wid == 0) {
+          double v = (lane < nw) ? dred[lane] : 0.0;
+          v = warp_sum(v);
+          if (lane == 0) prp[g] = v;
+        }
         // up to four columns per warp, interleaved (independent chains)
         for (int cb = wid; cb < nrem; cb += 4 * nw) {
           df2 acc[4] = {df_zero(), df_zero(), df_zero(), df_zero()};
@@ -435,13 +464,22 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
       if (grid_failed(ws.bar)) return;
       // (b) the reflector (zlarfg conventions: beta real, v_jj = 1), in FP64
       if (wid == 0) {
+        // the pivot row's entry alpha is loaded with the first batch of
+        // partial norms (both are one L2 round trip away)
+        cplx al;
+        if constexpr (MIXED) al = df_to(ld_cg_df(rowp));
+        else al = ld_cg(rowp);
         double s2 = 0.0;
-        for (int gg = lane; gg < G; gg += 32) s2 += ld_cg(prp + gg);
+        for (int g0 = lane; g0 < G; g0 += 32 * kLoadBatch) {
+          double v[kLoadBatch];
+#pragma unroll
+          for (int u = 0; u < kLoadBatch; ++u) v[u] = (g0 + 32 * u < G) ? ld_cg(prp + g0 + 32 * u) : 0.0;
+#pragma unroll
+          for (int u = 0; u < kLoadBatch; ++u)
+            if (g0 + 32 * u < G) s2 += v[u];
+        }
         s2 = warp_sum(s2);
         if (lane == 0) {
-          cplx al;
-          if constexpr (MIXED) al = df_to(ld_cg_df(rowp));
-          else al = ld_cg(rowp);
           cplx tu, sc;
           double beta;
           if (s2 == 0.0 && al.y == 0.0) {
@@ -463,31 +501,59 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
             const int es = (smax > 0.0) ? ilogb(smax) : 0;
             sc = mk(scalbn(sc.x, -es), scalbn(sc.y, -es));
             esc_sh = es;
+            bcd[0] = df_from(cconj(tu));
+            bcd[1] = df_from(cconj(sc));
+            bcd[2] = df_from(sc);
+            bcd[3] = df_from(mk(beta, 0.0));
           }
           bc[0] = tu;
           bc[1] = sc;
           bc[2] = mk(beta, 0.0);
         }
       }
-      // raw sums over the CTAs of the dot products (tpc threads per column)
-      if (nrem > 0) {
+      // raw sums over the CTAs of the dot products (tpc threads per
+      // column); in mixed precision warp 0 is left out, so that these sums
+      // run while it forms the reflector
+      const int skip = MIXED ? 32 : 0;
+      if (nrem > 0 && tid >= skip) {
+        const int nthr = blockDim.x - skip, t2 = tid - skip;
         int tpc = 32;
-        while (tpc > 1 && tpc * nrem > (int)blockDim.x) tpc >>= 1;
-        const int per = blockDim.x / tpc, sub = tid % tpc;
+        while (tpc > 1 && tpc * nrem > nthr) tpc >>= 1;
+        const int per = nthr / tpc, sub = t2 % tpc;
         for (int base = 0; base < nrem; base += per) {
-          const int c = base + tid / tpc;
-          const bool valid = c < nrem;
+          const int c = base + t2 / tpc;
+          const bool valid = c < nrem && t2 / tpc < per;
+          const cplx* src = ws.pc + tail0 + (size_t)par * nb + c;
           if constexpr (MIXED) {
             df2 acc = df_zero();
             if (valid)
-              for (int gg = sub; gg < G; gg += tpc)
-                acc = df_cadd(acc, ld_cg_df(ws.pc + (size_t)gg * pstride + tail0 + (size_t)par * nb + c));
+              for (int g0 = sub; g0 < G; g0 += tpc * kLoadBatch) {
+                df2 v[kLoadBatch];
+#pragma unroll
+                for (int u = 0; u < kLoadBatch; ++u) {
+                  const int gg = g0 + tpc * u;
+                  v[u] = (gg < G) ? ld_cg_df(src + (size_t)gg * pstride) : df_zero();
+                }
+#pragma unroll
+                for (int u = 0; u < kLoadBatch; ++u)
+                  if (g0 + tpc * u < G) acc = df_cadd(acc, v[u]);
+              }
             for (int o = 1; o < tpc; o <<= 1) acc = df_cadd(acc, df_shfl_xor(acc, o));
             if (valid && sub == 0) reinterpret_cast<df2*>(praw)[c] = acc;
           } else {
             cplx acc = mk(0, 0);
             if (valid)
-              for (int gg = sub; gg < G; gg += tpc) acc = cadd(acc, ld_cg(ws.pc + (size_t)gg * pstride + tail0 + (size_t)par * nb + c));
+              for (int g0 = sub; g0 < G; g0 += tpc * kLoadBatch) {
+                cplx v[kLoadBatch];
+#pragma unroll
+                for (int u = 0; u < kLoadBatch; ++u) {
+                  const int gg = g0 + tpc * u;
+                  v[u] = (gg < G) ? ld_cg(src + (size_t)gg * pstride) : mk(0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < kLoadBatch; ++u)
+                  if (g0 + tpc * u < G) acc = cadd(acc, v[u]);
+              }
             for (int o = 1; o < tpc; o <<= 1) {
               acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
               acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -501,7 +567,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
       // f_c = conj(tau) (a_c[jj] + conj(scale) raw_c) into wl; scale column t
       if constexpr (MIXED) {
         df2* Pd = reinterpret_cast<df2*>(P);
-        const df2 ctu = df_from(cconj(tu)), csc = df_from(cconj(sc)), scd = df_from(sc);
+        const df2 ctu = bcd[0], csc = bcd[1], scd = bcd[2];
         const int es = esc_sh;
         for (int c = tid; c < nrem; c += blockDim.x) {
           df2 cr = df_zero();
@@ -518,7 +584,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
           df_cmac(v, xt[i - r0], scd);
           xt[i - r0] = df_scalb(df_cadd(v, df_zero()), es);
         }
-        if (tid == 0 && jj >= r0 && jj < r1) xt[jj - r0] = df_from(bc[2]);
+        if (tid == 0 && jj >= r0 && jj < r1) xt[jj - r0] = bcd[3];
       } else {
         for (int c = tid; c < nrem; c += blockDim.x) {
           const cplx w = cadd(ld_cg(rowp + 1 + c), cmul(cconj(sc), praw[c]));

@@ -31,73 +31,129 @@ constexpr int kOuter = 128;
 // W2 = T^H W (forward) or T W (backward) for the compact WY factor given by
 // G (v_s^H v_u in G[s + ldg u]; Hermitian) and tau: one warp per column l
 // of W (nbk x nt, ldw), each lane holding rows s = lane + 32 q.  The
-// triangle of G the solve reads and tau are staged in shared memory first
-// (the solve is a chain of nbk dependent steps; each step then reads shared
-// memory, not L2).  Packed column u of the staged triangle holds G[s, u] for
-// s > u (forward) or G[s, u] for s < u (backward).
+// recurrence runs in double-float arithmetic on the FP32 pipe (a chain of
+// FP64 multiply-adds waits on this GPU's narrow FP64 pipe at every step);
+// its ~2^-48 relative rounding is far below the tensor-core products'
+// error.  The triangle of G it reads and tau are packed once per panel
+// (wy_pack_kernel: negated, in double-float form, column u of the triangle
+// holding -G[s, u] for s > u (forward) or s < u (backward)) and copied into
+// shared memory by every CTA (the solve is a chain of nbk dependent steps;
+// each step then reads shared memory, not L2).
 constexpr int kWyWarps = 4;
 
-__global__ void __launch_bounds__(32 * kWyWarps)
-    wy_solve_kernel(const cplx* G, int ldg, const cplx* tau, int nbk, const cplx* W, int ldw, int nt, cplx* W2,
-                    int ldw2, int forward) {
-  extern __shared__ __align__(16) unsigned char wy_raw[];
-  cplx* tri = reinterpret_cast<cplx*>(wy_raw);  // nbk (nbk - 1) / 2 packed
-  cplx* tsh = tri + (size_t)nbk * (nbk - 1) / 2;
-  // packed offset of column u: forward rows u+1..nbk-1, backward rows 0..u-1
-  auto off = [&](int u) -> int {
-    return forward ? u * (2 * nbk - u - 1) / 2 : u * (u - 1) / 2;
-  };
-  for (int u = 0; u < nbk; ++u) {
-    const int lo = forward ? u + 1 : 0, hi = forward ? nbk : u;
-    for (int s = lo + (int)threadIdx.x; s < hi; s += blockDim.x) tri[off(u) + (s - lo)] = G[s + (size_t)ldg * u];
+DV int wy_off(int u, int nbk, int forward) {  // packed offset of column u
+  return forward ? u * (2 * nbk - u - 1) / 2 : u * (u - 1) / 2;
+}
+HD size_t wy_packed_elems(int nbk) { return (size_t)nbk * (nbk - 1) / 2 + nbk; }
+
+__global__ void wy_pack_kernel(const cplx* G, int ldg, const cplx* tau, int nbk, int forward, df2* packed) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nbk * nbk) return;
+  const int s = idx % nbk, u = idx / nbk;
+  if (forward ? s > u : s < u) {
+    const cplx gv = G[s + (size_t)ldg * u];
+    packed[wy_off(u, nbk, forward) + (forward ? s - u - 1 : s)] = df_from(mk(-gv.x, -gv.y));
   }
-  for (int u = threadIdx.x; u < nbk; u += blockDim.x) tsh[u] = tau[u];
+  // forward: w2_u = conj(tau_u) (...); backward: w2_u = tau_u (...)
+  if (s == u) packed[(size_t)nbk * (nbk - 1) / 2 + u] = df_from(forward ? cconj(tau[u]) : tau[u]);
+}
+
+__global__ void __launch_bounds__(32 * kWyWarps)
+    wy_solve_kernel(const df2* packed, int nbk, const cplx* W, int ldw, int nt, cplx* W2, int ldw2, int forward) {
+  extern __shared__ __align__(16) unsigned char wy_raw[];
+  df2* tri = reinterpret_cast<df2*>(wy_raw);  // nbk (nbk - 1) / 2 packed
+  df2* tsh = tri + (size_t)nbk * (nbk - 1) / 2;
+  auto off = [&](int u) -> int { return wy_off(u, nbk, forward); };
+  {
+    // coalesced 16-byte loads, eight in flight per thread
+    const float4* src = reinterpret_cast<const float4*>(packed);
+    float4* dst = reinterpret_cast<float4*>(wy_raw);
+    const int n16 = (int)wy_packed_elems(nbk);
+    constexpr int U = 8;
+    for (int e0 = threadIdx.x; e0 < n16; e0 += U * blockDim.x) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < n16) v[u] = __ldg(src + e);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < n16) dst[e] = v[u];
+      }
+    }
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int l = blockIdx.x * kWyWarps + (threadIdx.x >> 5);
   if (l >= nt) return;
   constexpr int Q = kOuter / 32;
-  cplx acc[Q];
+  // the column scaled by a power of two to a maximum below one (the FP32
+  // exponent range of the double-float parts is then never left; W2 = T^H W
+  // is linear in W, so the scale comes back exactly at the end)
+  cplx wv[Q];
+  double mx = 0.0;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int s = lane + 32 * q;
-    acc[q] = (s < nbk) ? W[s + (size_t)ldw * l] : mk(0, 0);
+    wv[q] = (s < nbk) ? W[s + (size_t)ldw * l] : mk(0, 0);
+    mx = fmax(mx, fmax(fabs(wv[q].x), fabs(wv[q].y)));
+  }
+  for (int o = 16; o >= 1; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int E = (mx > 0.0) ? ilogb(mx) + 1 : 0;
+  df2 acc[Q], mine[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    acc[q] = df_from(mk(scalbn(wv[q].x, -E), scalbn(wv[q].y, -E)));
+    mine[q] = df_zero();
   }
   for (int step = 0; step < nbk; ++step) {
     const int u = forward ? step : nbk - 1 - step;
     const int qu = u >> 5, lu = u & 31;
-    cplx own = mk(0, 0);
+    df2 own = df_zero();
 #pragma unroll
     for (int q = 0; q < Q; ++q)
       if (q == qu) own = acc[q];
-    const cplx t = tsh[u];
-    cplx w2 = forward ? cmul(cconj(t), own) : cmul(t, own);
-    w2.x = __shfl_sync(0xffffffffu, w2.x, lu);
-    w2.y = __shfl_sync(0xffffffffu, w2.y, lu);
-    if (lane == lu) W2[u + (size_t)ldw2 * l] = w2;
-    const cplx* col = tri + off(u);
+    df2 w2 = df_zero();
+    df_cmac(w2, tsh[u], own);  // valid on lane lu
+    w2 = df2{__shfl_sync(0xffffffffu, w2.rh, lu), __shfl_sync(0xffffffffu, w2.ih, lu),
+             __shfl_sync(0xffffffffu, w2.rl, lu), __shfl_sync(0xffffffffu, w2.il, lu)};
+    if (lane == lu) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (q == qu) mine[q] = w2;
+    }
+    const df2* col = tri + off(u);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int s = lane + 32 * q;
       if (s >= nbk) continue;
-      if (forward && s > u) {
-        // (T^-H)[s, u] = conj(G[u, s]) = G[s, u]
-        acc[q] = csub(acc[q], cmul(col[s - u - 1], w2));
-      } else if (!forward && s < u) {
-        acc[q] = csub(acc[q], cmul(col[s], w2));
-      }
+      // forward: (T^-H)[s, u] = conj(G[u, s]) = G[s, u] for s > u
+      if (forward && s > u) df_cmac(acc[q], col[s - u - 1], w2);
+      else if (!forward && s < u) df_cmac(acc[q], col[s], w2);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int s = lane + 32 * q;
+    if (s < nbk) {
+      const cplx v = df_to(mine[q]);
+      W2[s + (size_t)ldw2 * l] = mk(scalbn(v.x, E), scalbn(v.y, E));
     }
   }
 }
 
+// `packed` holds wy_packed_elems(nbk) double-float values of scratch.
 cudaError_t wy_solve(const cplx* G, int ldg, const cplx* tau, int nbk, const cplx* W, int ldw, int nt, cplx* W2,
-                     int ldw2, int forward, cudaStream_t s) {
+                     int ldw2, int forward, df2* packed, cudaStream_t s) {
   if (nt <= 0) return cudaSuccess;
-  const size_t smem = sizeof(cplx) * ((size_t)nbk * (nbk - 1) / 2 + nbk);
+  const size_t smem = sizeof(df2) * wy_packed_elems(nbk);
   static cudaError_t attr = cudaFuncSetAttribute(wy_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(sizeof(cplx) * ((size_t)kOuter * (kOuter - 1) / 2 + kOuter)));
+                                                 (int)(sizeof(df2) * wy_packed_elems(kOuter)));
   if (attr != cudaSuccess) return attr;
-  wy_solve_kernel<<<(nt + kWyWarps - 1) / kWyWarps, 32 * kWyWarps, smem, s>>>(G, ldg, tau, nbk, W, ldw, nt, W2, ldw2,
+  wy_pack_kernel<<<(nbk * nbk + 255) / 256, 256, 0, s>>>(G, ldg, tau, nbk, forward, packed);
+  wy_solve_kernel<<<(nt + kWyWarps - 1) / kWyWarps, 32 * kWyWarps, smem, s>>>(packed, nbk, W, ldw, nt, W2, ldw2,
                                                                              forward);
   return cudaGetLastError();
 }
@@ -148,6 +204,7 @@ size_t qr_tc_scratch_bytes(int m, int k, int S) {
   add(tc_operand_bytes(nt, kOuter, S, Kc)); // W2
   add(std::max(tc_part_elems(kOuter, nt, m), tc_part_elems(kOuter, kOuter, m)) * sizeof(cplx));
   add((size_t)kOuter * nt * sizeof(cplx) * 2);  // W, W2
+  add(wy_packed_elems(kOuter) * sizeof(df2));   // packed WY triangle
   return b + 1024;
 }
 
@@ -181,6 +238,7 @@ cudaError_t geqrf_tc(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, cplx* G
     cplx* part = static_cast<cplx*>(c.take(npart * sizeof(cplx)));
     cplx* W = static_cast<cplx*>(c.take((size_t)nbk * std::max(nt, 1) * sizeof(cplx)));
     cplx* W2 = static_cast<cplx*>(c.take((size_t)nbk * std::max(nt, 1) * sizeof(cplx)));
+    df2* packed = static_cast<df2*>(c.take(wy_packed_elems(nbk) * sizeof(df2)));
     if (!c.ok) return cudaErrorInvalidValue;
     // G = V^H V (reflector s along rows, entries i along K)
     TcOperand oVH, oVB, oX, oV, oW2;
@@ -202,7 +260,7 @@ cudaError_t geqrf_tc(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, cplx* G
     if (e == cudaSuccess) e = tc_zgemm(oVH, oX, W, nbk, 1.0, 0, part, npart, &cws.bar->err, s);
     pt.e(slot, pt.cls_tc, zflops(nbk, nt, mv), 4);
     slot = pt.b();
-    if (e == cudaSuccess) e = wy_solve(G, kOuter, tau + j0, nbk, W, nbk, nt, W2, nbk, 1, s);
+    if (e == cudaSuccess) e = wy_solve(G, kOuter, tau + j0, nbk, W, nbk, nt, W2, nbk, 1, packed, s);
     pt.e(slot, pt.cls_small, 0.0, 1);
     slot = pt.b();
     if (e == cudaSuccess) e = tc_split(TcOperandView{W2, nbk, 1, nt, nbk, 0, 0, 0}, S, &oW2, bW2, s);
@@ -232,6 +290,7 @@ cudaError_t ormqr_tc(const cplx* A, int lda, int m, int p, const cplx* tau, cons
     cplx* part = static_cast<cplx*>(c.take(std::max<size_t>(npart, 1) * sizeof(cplx)));
     cplx* W = static_cast<cplx*>(c.take((size_t)nbk * q * sizeof(cplx)));
     cplx* W2 = static_cast<cplx*>(c.take((size_t)nbk * q * sizeof(cplx)));
+    df2* packed = static_cast<df2*>(c.take(wy_packed_elems(nbk) * sizeof(df2)));
     if (!c.ok) return cudaErrorInvalidValue;
     TcOperand oVH, oX, oV, oW2;
     int slot = pt.b();
@@ -241,7 +300,7 @@ cudaError_t ormqr_tc(const cplx* A, int lda, int m, int p, const cplx* tau, cons
     pt.e(slot, pt.cls_tc, zflops(nbk, q, mv), 6);
     slot = pt.b();
     if (e == cudaSuccess)
-      e = wy_solve(Gin + (size_t)j * kOuter * kOuter, kOuter, tau + j0, nbk, W, nbk, q, W2, nbk, 0, s);
+      e = wy_solve(Gin + (size_t)j * kOuter * kOuter, kOuter, tau + j0, nbk, W, nbk, q, W2, nbk, 0, packed, s);
     pt.e(slot, pt.cls_small, 0.0, 1);
     slot = pt.b();
     if (e == cudaSuccess) e = tc_split(TcOperandView{W2, nbk, 1, q, nbk, 0, 0, 0}, S, &oW2, bW2, s);

@@ -168,6 +168,11 @@ DV double f2d_scaled(float f, int E, int neg) {
   return __longlong_as_double(sgn | ((long long)e11 << 52) | ((long long)(u & 0x7FFFFFu) << 29));
 }
 
+// 2^d as a float for -126 <= d <= 127 (exact), 0 below: multiplying by it
+// scales exactly while the result stays normal.  A component scaled by
+// less than 2^-126 against the largest one weighs below 2^-126 of |A||B|.
+DV float pow2f(int d) { return d >= -126 ? __int_as_float((127 + d) << 23) : 0.f; }
+
 struct TcArgs {
   int M, N, K, S, Kc, nchunks;
   const int* eA;  // [3][nchunks][M] scale exponents of the A digits
@@ -279,9 +284,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // double-float arithmetic on the FP32 pipe (error-free TwoSum steps),
     // and only the final value is converted to FP64 and scaled (on this GPU
     // the FP64 pipe is 1/64 of the FP32 one).
+    const int m = m0 + 32 * warp + lane;
+    cplx* out = a.out + (size_t)z * a.zstride;
+    // the values an accumulating product adds to, 16 columns at a time,
+    // loaded ahead (independent loads in flight together): the first half
+    // while the MMAs run, the second before its accumulators are read
+    cplx pre[16];
+    auto prefetch = [&](int h) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int n = n0 + 16 * h + q;
+        pre[q] = (a.accumulate && m < a.M && n < a.N) ? out[m + (size_t)a.ldo * n] : mk(0, 0);
+      }
+    };
+    prefetch(0);
     const bool ok = mbar_wait(&acc_bar, 0, vabort, a.err);
     tc_fence_after();
-    const int m = m0 + 32 * warp + lane;
     if (ok && !*vabort) {
       const int* eA = a.eA + (size_t)z * a.M;
       const int* eB = a.eB + (size_t)z * a.N;
@@ -289,9 +307,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       int ea[3] = {0, 0, 0};
       if (m < a.M)
         for (int c = 0; c < 3; ++c) ea[c] = eA[c * eAs + m];
-      cplx* out = a.out + (size_t)z * a.zstride;
 #pragma unroll 1
       for (int h = 0; h < kTcN / 16; ++h) {
+        if (h > 0) prefetch(h);
         float th[3][16], tl[3][16];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -299,10 +317,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int L = 0; L < S; ++L) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((c * S + L) * kTcN + 16 * h), v);
-            const int sh = -14 - 8 * L;
+            const float w = pow2f(-14 - 8 * L);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-              const float x = scalbnf(v[q], sh);  // exact: an integer below 2^24 times a power of two
+              const float x = v[q] * w;  // exact: an integer below 2^24 times a power of two
               if (L == 0) {
                 th[c][q] = x;
                 tl[c][q] = 0.f;
@@ -322,9 +340,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int E0 = max(ex[0], max(ex[1], ex[2]));
           // component values relative to 2^E0 (factors <= 1: exact scaling,
           // or below the double-float precision of the largest one)
-          float h0 = scalbnf(th[0][q], ex[0] - E0), l0 = scalbnf(tl[0][q], ex[0] - E0);
-          float h1 = scalbnf(th[1][q], ex[1] - E0), l1 = scalbnf(tl[1][q], ex[1] - E0);
-          float h2 = scalbnf(th[2][q], ex[2] - E0), l2 = scalbnf(tl[2][q], ex[2] - E0);
+          const float w0 = pow2f(ex[0] - E0), w1 = pow2f(ex[1] - E0), w2 = pow2f(ex[2] - E0);
+          float h0 = th[0][q] * w0, l0 = tl[0][q] * w0;
+          float h1 = th[1][q] * w1, l1 = tl[1][q] * w1;
+          float h2 = th[2][q] * w2, l2 = tl[2][q] * w2;
           // re = T1 - T2, im = T3 - T1 - T2
           float rh = h0, rl = l0;
           df_add_part(rh, rl, -h1, -l1);
@@ -337,9 +356,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int Es = E0 + a.alpha_exp;
           cplx r = mk(f2d_scaled(rh, Es, a.alpha_neg) + f2d_scaled(rl, Es, a.alpha_neg),
                       f2d_scaled(ih, Es, a.alpha_neg) + f2d_scaled(il, Es, a.alpha_neg));
-          cplx* p = out + m + (size_t)a.ldo * n;
-          if (a.accumulate) r = cadd(*p, r);
-          *p = r;
+          if (a.accumulate) r = cadd(pre[q], r);
+          out[m + (size_t)a.ldo * n] = r;
         }
       }
     }
@@ -425,6 +443,42 @@ DV long long fixed_point(double v, int e, int nbits) {
   return b < 0 ? -X : X;
 }
 
+// BF16 bits of a small integer (|d| <= 128: exact in BF16, so the upper
+// half of its FP32 bits).
+DV unsigned int bf16_bits(int d) { return __float_as_uint((float)d) >> 16; }
+
+// The S balanced base-256 digits of two fixed-point values, digit j of both
+// as one 32-bit word (first value in the low half) at dst[j * pstride].
+// |X| <= 2^39 (S = 5): after the lowest digit the rest can reach 2^31 (a
+// value within 2^-32 of its power-of-two scale), after the second it is
+// below 2^24, so the first two steps run in 64 bits and the rest in 32.
+DV void digit_pair(long long X0, long long X1, int S, unsigned int* dst, size_t pstride) {
+  if (S == 1) {  // one digit: the value itself (|X| <= 128)
+    dst[0] = bf16_bits((int)X0) | (bf16_bits((int)X1) << 16);
+    return;
+  }
+  int d0 = (int)((X0 + 128) & 255) - 128, d1 = (int)((X1 + 128) & 255) - 128;
+  X0 = (X0 - d0) >> 8;
+  X1 = (X1 - d1) >> 8;
+  dst[(size_t)(S - 1) * pstride] = bf16_bits(d0) | (bf16_bits(d1) << 16);
+  if (S == 2) {
+    dst[0] = bf16_bits((int)X0) | (bf16_bits((int)X1) << 16);
+    return;
+  }
+  d0 = (int)((X0 + 128) & 255) - 128;
+  d1 = (int)((X1 + 128) & 255) - 128;
+  int y0 = (int)((X0 - d0) >> 8), y1 = (int)((X1 - d1) >> 8);
+  dst[(size_t)(S - 2) * pstride] = bf16_bits(d0) | (bf16_bits(d1) << 16);
+  for (int j = S - 3; j >= 1; --j) {
+    d0 = ((y0 + 128) & 255) - 128;
+    d1 = ((y1 + 128) & 255) - 128;
+    y0 = (y0 - d0) >> 8;
+    y1 = (y1 - d1) >> 8;
+    dst[(size_t)j * pstride] = bf16_bits(d0) | (bf16_bits(d1) << 16);
+  }
+  dst[0] = bf16_bits(y0) | (bf16_bits(y1) << 16);
+}
+
 DV void split_load(const SplitView& v, int r0, int k0, int k1, cplx (*tile)[kSlab + 1]) {
   if (v.rs == 1 && v.ks != 1) {  // rows contiguous: consecutive threads along r
     for (int idx = threadIdx.x; idx < kSplitRows * kSlab; idx += kSplitThreads) {
@@ -475,28 +529,30 @@ __global__ void __launch_bounds__(kSplitThreads)
   }
   __syncthreads();
   // pass 2: balanced base-256 digits of round(x 2^(8S-1)), |x| = |v| 2^-e < 1:
-  // x ~ sum_j q_j 2^(-7-8j) with |q_j| <= 128
+  // x ~ sum_j q_j 2^(-7-8j) with |q_j| <= 128.  Each thread cuts two
+  // consecutive K-values of a row and stores each digit pair as one 32-bit
+  // word (K-chunks and slabs start at even K, ldk is even).
   const size_t plane = (size_t)v.R * ldk;
   const int nbits = 8 * S - 1;
-  const int kk = tid % kSlab, rg = tid / kSlab;
+  const int kp = tid % (kSlab / 2), rg = tid / (kSlab / 2);
+  constexpr int kRowStep = kSplitThreads / (kSlab / 2);
   for (int k0 = kb; k0 < ke; k0 += kSlab) {
     split_load(v, r0, k0, ke, tile);
     __syncthreads();
+    const int kk = 2 * kp;
     if (k0 + kk < ke)
-      for (int r = rg; r < kSplitRows; r += kSplitThreads / kSlab) {
+      for (int r = rg; r < kSplitRows; r += kRowStep) {
         if (r0 + r >= v.R) break;
-        const cplx x = tile[r][kk];
-        const double c[3] = {x.x, x.y, x.x + x.y};
-        __nv_bfloat16* dst = planes + (size_t)(r0 + r) * ldk + k0 + kk;
+        // the second value of the pair is zero beyond ke (the loader's fill)
+        const cplx x0 = tile[r][kk], x1 = tile[r][kk + 1];
+        const double c0[3] = {x0.x, x0.y, x0.x + x0.y};
+        const double c1[3] = {x1.x, x1.y, x1.x + x1.y};
+        unsigned int* dst = reinterpret_cast<unsigned int*>(planes + (size_t)(r0 + r) * ldk + k0 + kk);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          long long X = fixed_point(c[q], esh[q][r], nbits);
-          for (int j = S - 1; j >= 1; --j) {
-            const int dgt = (int)((X + 128) & 255) - 128;
-            X = (X - dgt) >> 8;
-            dst[(size_t)(q * S + j) * plane] = __float2bfloat16_rn((float)dgt);
-          }
-          dst[(size_t)(q * S) * plane] = __float2bfloat16_rn((float)X);
+          const int e = esh[q][r];
+          digit_pair(fixed_point(c0[q], e, nbits), fixed_point(c1[q], e, nbits), S, dst + (size_t)(q * S) * (plane / 2),
+                     plane / 2);
         }
       }
     __syncthreads();

@@ -5,7 +5,7 @@ operator apply (hopf_apply_op) and one rounding (tt_round) at rank 6r, plus
 one fused hopf_step when --step is given.  Sized by --d/--n/--r so a capture
 stays small (d=4, n=128, r=64 holds about 2.5 GB on the device).
 
-  python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64 [--mixed [--tensor]] [--profile]
+  python -m paper_2403_04946_gb300.profile_case --d 4 --n 128 --r 64 [--mixed [--qr-method doublefloat]] [--profile]
 
 With --surrogate it instead runs the surrogate network alone on seeded
 synthetic data (26 -> 256 x 4 -> 14, 4 members): 20 training steps of batch
@@ -35,7 +35,8 @@ def main():
     ap.add_argument("--mixed", action="store_true", help="HOPF_MIXED precision")
     ap.add_argument("--surrogate", action="store_true", help="the surrogate network only")
     ap.add_argument("--profile", action="store_true", help="print the per-class profile record")
-    ap.add_argument("--tensor", action="store_true", help="mixed precision with the tensor-core QR")
+    ap.add_argument("--qr-method", choices=["tensor", "doublefloat"], default="tensor",
+                    help="mixed precision QR: tensor-core products (default) or double-float on the FP32 pipe")
     ap.add_argument("--steps", type=int, default=1, help="RK4 steps with --step (the first sets up workspaces)")
     ap.add_argument("--cdf", action="store_true",
                     help="the paper's CDF equation on a saturated state, explicit midpoint steps (--d 20 --n 64 --r 128)")
@@ -51,8 +52,8 @@ def main():
     cores, _ = synthetic.saturated_tt_cores(args.d, args.n, args.r, seed=0)
     ctx = binding.Context(d=args.d, n=args.n, nu=0.01, tol=args.tol, rank_cap=args.r, L=12.4,
                           precision=binding.HOPF_MIXED if args.mixed else binding.HOPF_FP64)
-    if args.tensor:
-        ctx.hopf_set_qr_method(binding.HOPF_QR_TENSOR)
+    if args.mixed:
+        ctx.hopf_set_qr_method(binding.HOPF_QR_TENSOR if args.qr_method == "tensor" else binding.HOPF_QR_DOUBLEFLOAT)
     t = ctx.tt_from_host(cores, max_rank=args.r)
     big = ctx.tt_create(6 * args.r)
     if args.profile:

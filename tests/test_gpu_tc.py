@@ -65,6 +65,25 @@ def test_error_falls_eight_bits_per_digit(ctx, digits, M, N, K, opA, opB):
     assert rel <= 2.0 ** (-8 * digits + 5)  # 5 digits: 2.9e-11
 
 
+@pytest.mark.parametrize("digits", [2, 3, 5])
+def test_values_just_below_a_power_of_two(ctx, digits):
+    """Entries within 2^-32 .. 2^-50 below a power of two (and their
+    negatives): the row scale puts them at the top of the digit range, where
+    the integer carried into the next digit is largest (a value like
+    Phi(a) = 1 - 1e-12 near a = 0).  Same error bound as random data."""
+    rng = np.random.default_rng(7 + digits)
+    M, N, K = 130, 40, 200
+    gaps = 2.0 ** -rng.integers(32, 51, (M, K))
+    A = (1.0 - gaps) * rng.choice([-1.0, 1.0], (M, K)) * 2.0 ** rng.integers(-3, 4, (M, 1))
+    A = A + 1j * (1.0 - gaps[::-1]) * rng.choice([-1.0, 1.0], (M, K))
+    B = rng.standard_normal((K, N)) + 1j * (1.0 - 2.0 ** -rng.integers(32, 51, (K, N)))
+    want = A @ B
+    scale = np.abs(A) @ np.abs(B)
+    got = ctx.hopf_tc_zgemm(A, B, 0, 0, digits=digits)
+    rel = float(np.max(np.abs(got - want) / scale))
+    assert rel <= 2.0 ** (-8 * digits + 5)
+
+
 def test_rejects_bad_arguments(ctx):
     from paper_2403_04946_gb300 import binding
     A = np.ones((4, 4), dtype=complex)
