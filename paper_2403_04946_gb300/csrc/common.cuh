@@ -59,6 +59,73 @@ HD df2 df_from(cplx a) {
   return df2{rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih)};
 }
 HD cplx df_to(df2 a) { return make_double2((double)a.rh + (double)a.rl, (double)a.ih + (double)a.il); }
+
+// Conversions between FP64 and double-float by integer arithmetic on the
+// IEEE bit patterns (on this GPU an FP64 conversion, scaling or addition
+// occupies the narrow FP64 pipe; these use the integer and FP32 pipes).
+// (double)f * 2^E (negated if neg) from the bit pattern of f: sign, exponent
+// rebiased from 127 to 1023 plus E, significand shifted into place.  Zero
+// and FP32 subnormals give 0 (a subnormal low part sits below 2^-149 of its
+// high part); an exponent outside the double range saturates to 0 or inf.
+DV double f2d_scaled(float f, int E, int neg) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e8 = (u >> 23) & 0xFFu;
+  if (e8 == 0) return 0.0;
+  const long long sgn = (long long)((u >> 31) ^ (unsigned)neg) << 63;
+  const int e11 = (int)e8 - 127 + 1023 + E;
+  if (e11 <= 0) return 0.0;
+  if (e11 >= 2047) return __longlong_as_double(sgn | (0x7FFll << 52));
+  return __longlong_as_double(sgn | ((long long)e11 << 52) | ((long long)(u & 0x7FFFFFu) << 29));
+}
+
+// 2^d as a float for -126 <= d <= 127 (exact), 0 below: multiplying by it
+// scales exactly while the result stays normal.
+DV float pow2f(int d) { return d >= -126 ? __int_as_float((127 + d) << 23) : 0.f; }
+
+// x 2^-E as a double-float pair (hi, lo): hi is the 53-bit significand
+// rounded to 24 bits, lo the remainder (|lo| <= ulp(hi) / 2, itself rounded
+// to 24 bits).  Values whose hi part would fall below the FP32 normal range
+// (|x 2^-E| < 2^-126), zeros and FP64 subnormals give (0, 0).
+DV void df_split_scaled(double x, int E, float& hi, float& lo) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int e = ex - 1023 - E;  // |x| 2^-E = M 2^(e - 52), M in [2^52, 2^53)
+  if (ex == 0 || e < -126) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  const long long M = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+  long long Mh = (M + (1ll << 28)) >> 29;  // 24 bits, or 2^24 after a carry
+  const int r = (int)(M - (Mh << 29));     // |r| <= 2^28
+  int eh = e;
+  if (Mh == (1ll << 24)) {
+    Mh >>= 1;
+    eh += 1;
+  }
+  const unsigned int sgn = (unsigned int)((unsigned long long)b >> 63) << 31;
+  if (eh > 127) {  // beyond the FP32 range
+    hi = __uint_as_float(sgn | 0x7F800000u);
+    lo = 0.f;
+    return;
+  }
+  hi = __uint_as_float(sgn | ((unsigned int)(eh + 127) << 23) | ((unsigned int)Mh & 0x7FFFFFu));
+  // r 2^(e - 52) in two exact steps (e - 52 can be below -126)
+  const int s1 = (e - 52) / 2;
+  const float l = (float)r * pow2f(s1) * pow2f(e - 52 - s1);
+  lo = sgn ? -l : l;
+}
+DV df2 df_from_scaled(cplx a, int E) {
+  df2 r;
+  df_split_scaled(a.x, E, r.rh, r.rl);
+  df_split_scaled(a.y, E, r.ih, r.il);
+  return r;
+}
+// (hi + lo) 2^E in FP64: the two parts converted exactly from their bits,
+// one FP64 addition.
+DV cplx df_to_scaled(const df2& a, int E) {
+  return make_double2(f2d_scaled(a.rh, E, 0) + f2d_scaled(a.rl, E, 0), f2d_scaled(a.ih, E, 0) + f2d_scaled(a.il, E, 0));
+}
 // (hi, lo) += a * b for double-float reals a = (ah, al), b = (bh, bl):
 // exact product of the high parts (TwoProduct with an FMA), exact sum
 // (TwoSum), the low-order cross terms added to lo.

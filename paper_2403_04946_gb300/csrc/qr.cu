@@ -184,7 +184,7 @@ __device__ void partial_vhx_f(const df2* P, int R, int r0, int lo, int hi, int n
       }
       reduce_scatter<CH>(acc, lane);
       const int s = s0 + rs_index<CH>(lane);
-      if (rs_writer<CH>(lane) && s < nbk) out[s + (size_t)nbk * l] = df_to(acc[0]);
+      if (rs_writer<CH>(lane) && s < nbk) out[s + (size_t)nbk * l] = df_to_scaled(acc[0], 0);
     }
   }
 }
@@ -200,7 +200,7 @@ __device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
     const int l = l0 + w;
     if (l < ncol && lane < nbk) {
       const cplx wv = ld_cg(w2 + lane + (size_t)nbk * l);
-      wsh[w][lane] = df_from(mk(-wv.x, -wv.y));
+      wsh[w][lane] = df_from_scaled(mk(-wv.x, -wv.y), 0);
     }
     __syncwarp();
     if (l < ncol) {
@@ -239,7 +239,9 @@ __device__ void update_x_f(const df2* P, int R, int r0, int lo, int hi, int nbk,
 // FP64 and double-float form, in place (one CTA's rows), with a power-of-two
 // scale: df = A * 2^-E on the way in, A = df * 2^E on the way out.  The
 // scale keeps every entry below 1 in magnitude, so the FP32 exponent range
-// of the double-float parts (and of their products) is never exceeded.
+// of the double-float parts (and of their products) is never exceeded
+// (entries below 2^-126 of the largest one become zero).  Integer
+// conversions: no FP64 instructions.
 __device__ void rows_to_df(cplx* A, int lda, int r0, int r1, int c0, int c1, int E) {
   const int nr = r1 - r0;
   if (nr <= 0) return;
@@ -247,7 +249,7 @@ __device__ void rows_to_df(cplx* A, int lda, int r0, int r1, int c0, int c1, int
     const int c = c0 + (int)(e / nr), i = r0 + (int)(e % nr);
     cplx* p = A + i + (size_t)lda * c;
     const cplx v = *p;
-    *reinterpret_cast<df2*>(p) = df_from(mk(scalbn(v.x, -E), scalbn(v.y, -E)));
+    *reinterpret_cast<df2*>(p) = df_from_scaled(v, E);
   }
 }
 __device__ void rows_to_fp64(cplx* A, int lda, int r0, int r1, int c0, int c1, int E) {
@@ -256,8 +258,7 @@ __device__ void rows_to_fp64(cplx* A, int lda, int r0, int r1, int c0, int c1, i
   for (long long e = threadIdx.x; e < (long long)nr * (c1 - c0); e += blockDim.x) {
     const int c = c0 + (int)(e / nr), i = r0 + (int)(e % nr);
     cplx* p = A + i + (size_t)lda * c;
-    const cplx v = df_to(*reinterpret_cast<const df2*>(p));
-    *p = mk(scalbn(v.x, E), scalbn(v.y, E));
+    *p = df_to_scaled(*reinterpret_cast<const df2*>(p), E);
   }
 }
 
@@ -297,17 +298,6 @@ DV df2 df_scalb(const df2& a, int e) {
   return df2{scalbnf(a.rh, e), scalbnf(a.ih, e), scalbnf(a.rl, e), scalbnf(a.il, e)};
 }
 
-// Rewrites each of the first n FP64 complex values of buf as a double-float
-// value in the same 16 bytes.
-__device__ void to_df_in_place(cplx* buf, int n) {
-  df2* out = reinterpret_cast<df2*>(buf);
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const cplx v = buf[e];
-    out[e] = df_from(v);
-  }
-  __syncthreads();
-}
-
 // Partials that other CTAs published are read kLoadBatch at a time: the
 // loads of a batch are independent and in flight together (one L2 round
 // trip per batch instead of one per CTA, on a path every column waits for);
@@ -343,6 +333,8 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
   __shared__ double dred[32];
   __shared__ cplx bc[4];
   __shared__ df2 bcd[4];  // mixed: conj(tau), conj(scale), scale, beta as double-float values
+  __shared__ float2 dredf[32];
+  __shared__ int dtiny[32];
 
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -399,21 +391,44 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
       if constexpr (MIXED) {
         const df2* Pd = reinterpret_cast<const df2*>(P);
         const df2* xt = Pd + (size_t)t * R;
-        // the squared norm in FP64: squares of small entries would leave
-        // the FP32 range
-        double sq = 0.0;
-        for (int i = ilo + tid; i < r1; i += blockDim.x) sq += cabs2(df_to(xt[i - r0]));
-        // only thread 0 needs the CTA's sum: warp sums in the warps that
-        // hold rows, then warp 0 over them (the FP64 pipe is 1/64 of the
-        // FP32 rate: a block-wide FP64 reduction in every warp costs more
-        // than the column's arithmetic)
-        if (ilo + 32 * wid < r1) sq = warp_sum(sq);
-        if (lane == 0) dred[wid] = sq;
+        // The squared norm in double-float arithmetic (rows are scaled
+        // below 1), published in FP64; only thread 0 needs the CTA's sum:
+        // warp sums in the warps that hold rows, then warp 0 over them (the
+        // FP64 pipe runs at 1/64 of the FP32 rate).  A square or its low
+        // part would leave the FP32 range for entries below 2^-39; a column
+        // made only of such entries still needs its norm to full relative
+        // precision (the reflector is unitary only with it), so a CTA that
+        // holds one sums its squares in FP64 instead.
+        float qh = 0.f, ql = 0.f;
+        bool tiny = false;
+        for (int i = ilo + tid; i < r1; i += blockDim.x) {
+          const df2 x = xt[i - r0];
+          const float mx = fmaxf(fabsf(x.rh), fabsf(x.ih));
+          tiny |= (mx > 0.f && mx < 0x1p-39f);
+          df_mac(qh, ql, x.rh, x.rl, x.rh, x.rl);
+          df_mac(qh, ql, x.ih, x.il, x.ih, x.il);
+        }
+        if (ilo + 32 * wid < r1)
+          for (int o = 16; o >= 1; o >>= 1)
+            df_add_part(qh, ql, __shfl_xor_sync(0xffffffffu, qh, o), __shfl_xor_sync(0xffffffffu, ql, o));
+        tiny = __any_sync(0xffffffffu, tiny);
+        if (lane == 0) {
+          dredf[wid] = make_float2(qh, ql);
+          dtiny[wid] = tiny ? 1 : 0;
+        }
         __syncthreads();
         if (wid == 0) {
-          double v = (lane < nw) ? dred[lane] : 0.0;
-          v = warp_sum(v);
-          if (lane == 0) prp[g] = v;
+          if (__any_sync(0xffffffffu, lane < nw && dtiny[lane])) {
+            double v = 0.0;
+            for (int i = ilo + lane; i < r1; i += 32) v += cabs2(df_to_scaled(xt[i - r0], 0));
+            v = warp_sum(v);
+            if (lane == 0) prp[g] = v;
+          } else {
+            float2 v = (lane < nw) ? dredf[lane] : make_float2(0.f, 0.f);
+            for (int o = 16; o >= 1; o >>= 1)
+              df_add_part(v.x, v.y, __shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+            if (lane == 0) prp[g] = f2d_scaled(v.x, 0, 0) + f2d_scaled(v.y, 0, 0);
+          }
         }
         // up to four columns per warp, interleaved (independent chains)
         for (int cb = wid; cb < nrem; cb += 4 * nw) {
@@ -467,7 +482,7 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
         // the pivot row's entry alpha is loaded with the first batch of
         // partial norms (both are one L2 round trip away)
         cplx al;
-        if constexpr (MIXED) al = df_to(ld_cg_df(rowp));
+        if constexpr (MIXED) al = df_to_scaled(ld_cg_df(rowp), 0);
         else al = ld_cg(rowp);
         double s2 = 0.0;
         for (int g0 = lane; g0 < G; g0 += 32 * kLoadBatch) {
@@ -501,10 +516,10 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
             const int es = (smax > 0.0) ? ilogb(smax) : 0;
             sc = mk(scalbn(sc.x, -es), scalbn(sc.y, -es));
             esc_sh = es;
-            bcd[0] = df_from(cconj(tu));
-            bcd[1] = df_from(cconj(sc));
-            bcd[2] = df_from(sc);
-            bcd[3] = df_from(mk(beta, 0.0));
+            bcd[0] = df_from_scaled(cconj(tu), 0);
+            bcd[1] = df_from_scaled(cconj(sc), 0);
+            bcd[2] = df_from_scaled(sc, 0);
+            bcd[3] = df_from_scaled(mk(beta, 0.0), 0);
           }
           bc[0] = tu;
           bc[1] = sc;
@@ -631,9 +646,8 @@ geqrf_kernel(cplx* A, int lda, int m, int k, cplx* tau, cplx* Tg, int nb, int R,
       for (int i = r0 + tid; i < r1; i += blockDim.x) {
         const size_t e = (size_t)t * R + (i - r0);
         if (MIXED) {
-          const cplx v = df_to(reinterpret_cast<const df2*>(P)[e]);
           const int sh = (i <= j0 + t) ? E : 0;  // R part scaled back, reflector tails scale-free
-          A[i + (size_t)lda * (j0 + t)] = mk(scalbn(v.x, sh), scalbn(v.y, sh));
+          A[i + (size_t)lda * (j0 + t)] = df_to_scaled(reinterpret_cast<const df2*>(P)[e], sh);
         } else {
           A[i + (size_t)lda * (j0 + t)] = P[e];
         }
@@ -775,7 +789,7 @@ ormqr_kernel(const cplx* A, int lda, int m, int p, const cplx* Tg, int nb, cplx*
         if (i < j0 + t) v = mk(0, 0);
         else if (i == j0 + t) v = mk(1, 0);
         else v = A[i + (size_t)lda * (j0 + t)];
-        if (MIXED) reinterpret_cast<df2*>(P)[(size_t)t * R + (i - r0)] = df_from(v);
+        if (MIXED) reinterpret_cast<df2*>(P)[(size_t)t * R + (i - r0)] = df_from_scaled(v, 0);
         else P[(size_t)t * R + (i - r0)] = v;
       }
     // the panel's Gram (strict upper triangle) and tau (diagonal), packed

@@ -153,26 +153,6 @@ DV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// (double)f * 2^E (negated if neg) from the bit pattern of f: sign, exponent
-// rebiased from 127 to 1023 plus E, significand shifted into place.  Zero
-// and FP32 subnormals give 0 (a subnormal low part sits below 2^-149 of its
-// high part); an exponent outside the double range saturates to 0 or inf.
-DV double f2d_scaled(float f, int E, int neg) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int e8 = (u >> 23) & 0xFFu;
-  if (e8 == 0) return 0.0;
-  const long long sgn = (long long)((u >> 31) ^ (unsigned)neg) << 63;
-  const int e11 = (int)e8 - 127 + 1023 + E;
-  if (e11 <= 0) return 0.0;
-  if (e11 >= 2047) return __longlong_as_double(sgn | (0x7FFll << 52));
-  return __longlong_as_double(sgn | ((long long)e11 << 52) | ((long long)(u & 0x7FFFFFu) << 29));
-}
-
-// 2^d as a float for -126 <= d <= 127 (exact), 0 below: multiplying by it
-// scales exactly while the result stays normal.  A component scaled by
-// less than 2^-126 against the largest one weighs below 2^-126 of |A||B|.
-DV float pow2f(int d) { return d >= -126 ? __int_as_float((127 + d) << 23) : 0.f; }
-
 struct TcArgs {
   int M, N, K, S, Kc, nchunks;
   const int* eA;  // [3][nchunks][M] scale exponents of the A digits

@@ -409,6 +409,26 @@ def test_mixed_round_close_to_fp64(B):
     assert err < 1e-5
 
 
+@pytest.mark.parametrize("qr_method", [0, 1])
+def test_mixed_round_with_tiny_columns(B, qr_method):
+    """Columns far below the matrix's largest entry (1e-22 of it: their
+    squares leave the FP32 range) next to O(1) ones, in a lossless mixed
+    rounding: every reflector must stay unitary, so the result reproduces
+    the input at the mixed path's precision."""
+    d, n = 5, 16
+    base = synthetic.random_tt_cores(d, n, [1, 4, 4, 4, 4, 1], seed=81)
+    tiny = synthetic.random_tt_cores(d, n, [1, 6, 6, 6, 6, 1], seed=82)
+    tiny[0] = tiny[0] * 1e-22
+    x = tt.tt_sum([(1.0, base), (1.0, tiny)])
+    ctx = B.Context(d=d, n=n, nu=0.05, tol=1e-10, rank_cap=64, L=3.0, precision=B.HOPF_MIXED)
+    ctx.hopf_set_qr_method(qr_method)
+    tx = ctx.tt_from_host(x, max_rank=max(tt.ranks(x)))
+    ctx.tt_round(tx, 0.0, 10 ** 6)
+    err = rel(tt.full(ctx.tt_to_host(tx)), tt.full(x))
+    assert err < 1e-10
+    ctx.close()
+
+
 def test_mixed_step_c1_within_1e6(B):
     """C1, 20 RK4 steps in mixed precision with the oracle's ranks: relative
     L2 error to the FP64 oracle <= 1e-6 (the mixed-precision target)."""
