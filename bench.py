@@ -245,7 +245,27 @@ def tc_roofline(prof, peaks):
             "bf16_tflops_achieved": achieved * TC_BF16_PER_FP64EQ, "traffic": None}
 
 
-def roofline(prof, mixed, peaks):
+# DRAM traffic of one 128-column mixed panel launch of geqrf_kernel, from the
+# ncu capture summarised in profiles/geqrf_panel_16128x128_mixed.md:
+# dram__bytes_read.sum + dram__bytes_write.sum = 35.4 MB for a 16128 x 128
+# panel, i.e. bytes per panel element (the panel is read once; its write-back
+# stays in L2).  Traffic grows with the panel's rows, so a launch of m rows
+# moves about this many bytes per element of its m x 128 panel.
+PANEL_COLS = 128
+PANEL_DRAM_BYTES_PER_ELEM = (33.218304e6 + 2.177024e6) / (16128 * PANEL_COLS)
+
+
+def panel_traffic(pd):
+    """DRAM bytes per launch of the mixed tensor-core path's panel kernel,
+    scaled from the capture by the mean panel rows m, recovered from the
+    mean FLOPs per launch F = 8 m k^2 - 8 k^3 / 3 (k = 128)."""
+    launches = max(pd.get("timed_launches", 0), 1)
+    k = float(PANEL_COLS)
+    m = (pd["flops"] / launches + 8.0 * k ** 3 / 3.0) / (8.0 * k * k)
+    return PANEL_DRAM_BYTES_PER_ELEM * m * k
+
+
+def roofline(prof, mixed, peaks, tensor_qr=False):
     """Dominant contraction kernel class (largest device time among classes
     with an algorithmic FLOP count) against the peak of its own arithmetic."""
     cls = [k for k in prof if isinstance(prof[k], dict) and prof[k].get("flops", 0) > 0 and prof[k]["ms"] > 0]
@@ -262,8 +282,15 @@ def roofline(prof, mixed, peaks):
     else:
         peak = FP64_PEAK_TFLOPS
         src = "FP64 FMA: 152 SMs x 4 FLOP/clk x 2.07 GHz (derived; DFMA microbenchmark measured 1.19)"
-    return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_source": src, "traffic": None}
+    out = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "peak_source": src, "traffic": None}
+    if mixed and tensor_qr and dom == "qr":
+        # only the tensor-core path's panel kernel has counters taken since
+        # its last change; the whole-matrix variants' captures predate it
+        out["traffic"] = panel_traffic(pd)
+        out["traffic_source"] = ("ncu dram__bytes of one 16128 x 128 panel launch (35.4 MB), scaled to the mean "
+                                 "launch's panel rows")
+    return out
 
 
 def natural_state_error(w, stream, nsteps=3, qr_method=1):
@@ -554,7 +581,7 @@ def run_ours(args, rank, world, local_rank):
                       "(bf16 digit products, 5 digits, exact f32 accumulation, 3M complex); QR panels and merges "
                       "in double-float (2 x f32); f64 Householder scalars and SVD"),
             "data": "synthetic", "config": cfg,
-            "roofline": roofline(prof, True, peaks),
+            "roofline": roofline(prof, True, peaks, tensor_qr=(qr_method == binding.HOPF_QR_TENSOR)),
             "tensor_core_roofline": tc_roofline(prof, peaks),
             "kernel_shares": shares,
             "fp64": {"value": replica_rate(args.steps, el64, world), "unit": "steps/s", "ms_per_step": el64 / args.steps * 1e3,

@@ -251,22 +251,23 @@ cudaError_t geqrf_tc(cplx* A, int lda, int m, int k, cplx* tau, cplx* T, cplx* G
       hermitize_kernel<<<(nbk * nbk + 255) / 256, 256, 0, s>>>(G, kOuter, nbk);
       e = cudaGetLastError();
     }
-    pt.e(slot, pt.cls_tc, zflops(nbk, nbk, mv), 7);
+    // launches: two splits, the product, its chunk reduction (K > one chunk), hermitize
+    pt.e(slot, pt.cls_tc, zflops(nbk, nbk, mv), 4 + (mv > Kc));
     if (e != cudaSuccess || nt <= 0) continue;
     // trailing columns: W = V^H A_t, W2 = T^H W, A_t -= V W2
     cplx* At = A + j0 + (size_t)lda * (j0 + nbk);
     slot = pt.b();
     e = tc_split(TcOperandView{At, lda, 1, nt, mv, 0, 0, 0}, S, &oX, bX, s);
     if (e == cudaSuccess) e = tc_zgemm(oVH, oX, W, nbk, 1.0, 0, part, npart, &cws.bar->err, s);
-    pt.e(slot, pt.cls_tc, zflops(nbk, nt, mv), 4);
+    pt.e(slot, pt.cls_tc, zflops(nbk, nt, mv), 2 + (mv > Kc));
     slot = pt.b();
     if (e == cudaSuccess) e = wy_solve(G, kOuter, tau + j0, nbk, W, nbk, nt, W2, nbk, 1, packed, s);
-    pt.e(slot, pt.cls_small, 0.0, 1);
+    pt.e(slot, pt.cls_small, 0.0, 2);  // pack + solve
     slot = pt.b();
     if (e == cudaSuccess) e = tc_split(TcOperandView{W2, nbk, 1, nt, nbk, 0, 0, 0}, S, &oW2, bW2, s);
     if (e == cudaSuccess) e = tc_split(TcOperandView{Ap, 1, lda, mv, nbk, 0, 3, 0}, S, &oV, bV, s);
     if (e == cudaSuccess) e = tc_zgemm(oV, oW2, At, lda, -1.0, 1, nullptr, 0, &cws.bar->err, s);
-    pt.e(slot, pt.cls_tc, zflops(mv, nt, nbk), 5);
+    pt.e(slot, pt.cls_tc, zflops(mv, nt, nbk), 3);  // two splits, one chunk
   }
   return e;
 }
@@ -297,16 +298,16 @@ cudaError_t ormqr_tc(const cplx* A, int lda, int m, int p, const cplx* tau, cons
     e = tc_split(TcOperandView{Ap, lda, 1, nbk, mv, 1, 2, 0}, S, &oVH, bVH, s);
     if (e == cudaSuccess) e = tc_split(TcOperandView{Cj, ldc, 1, q, mv, 0, 0, 0}, S, &oX, bX, s);
     if (e == cudaSuccess) e = tc_zgemm(oVH, oX, W, nbk, 1.0, 0, part, npart, err, s);
-    pt.e(slot, pt.cls_tc, zflops(nbk, q, mv), 6);
+    pt.e(slot, pt.cls_tc, zflops(nbk, q, mv), 3 + (mv > Kc));
     slot = pt.b();
     if (e == cudaSuccess)
       e = wy_solve(Gin + (size_t)j * kOuter * kOuter, kOuter, tau + j0, nbk, W, nbk, q, W2, nbk, 0, packed, s);
-    pt.e(slot, pt.cls_small, 0.0, 1);
+    pt.e(slot, pt.cls_small, 0.0, 2);
     slot = pt.b();
     if (e == cudaSuccess) e = tc_split(TcOperandView{W2, nbk, 1, q, nbk, 0, 0, 0}, S, &oW2, bW2, s);
     if (e == cudaSuccess) e = tc_split(TcOperandView{Ap, 1, lda, mv, nbk, 0, 3, 0}, S, &oV, bV, s);
     if (e == cudaSuccess) e = tc_zgemm(oV, oW2, Cj, ldc, -1.0, 1, nullptr, 0, err, s);
-    pt.e(slot, pt.cls_tc, zflops(mv, q, nbk), 5);
+    pt.e(slot, pt.cls_tc, zflops(mv, q, nbk), 3);
   }
   return e;
 }
