@@ -512,6 +512,8 @@ def run_ours(args, rank, world, local_rank):
     ctx = binding.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=L,
                           stream=stream.cuda_stream, precision=binding.HOPF_MIXED)
     ctx.hopf_set_qr_method(qr_method)
+    if not args.no_autotune:
+        ctx.hopf_set_autotune(True)  # shapes are tuned during the warm-up steps
     t = ctx.tt_from_host(cores, max_rank=w.cap)
     clocks = ClockSampler(gpu_id)
     clocks.start()
@@ -538,6 +540,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_s = maxover(time.perf_counter() - t0)
     out_bytes = ctx.tt_size(t) * 8
+    tune_table = ctx.hopf_get_autotune()
     ctx.tt_free(t)
     ctx.close()
 
@@ -573,6 +576,7 @@ def run_ours(args, rank, world, local_rank):
                               f"(d-1)/5 bonds x {STEP_PER_KROUND:.3f} rounding units per RK4 step")}
         cfg = config_dict(w)
         cfg["qr_method"] = args.qr_method
+        cfg["autotune"] = not args.no_autotune
         result = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
@@ -584,6 +588,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline(prof, True, peaks, tensor_qr=(qr_method == binding.HOPF_QR_TENSOR)),
             "tensor_core_roofline": tc_roofline(prof, peaks),
             "kernel_shares": shares,
+            "autotune": tune_table,
             "fp64": {"value": replica_rate(args.steps, el64, world), "unit": "steps/s", "ms_per_step": el64 / args.steps * 1e3,
                      "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},
             "mixed_vs_fp64_error": err,
@@ -610,6 +615,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --qr-method for every shape instead of the per-shape autotuned configuration")
     ap.add_argument("--qr-method", choices=["tensor", "doublefloat"], default="tensor",
                     help="how the mixed arm factors its tall flattenings (hopf_set_qr_method)")
     args = ap.parse_args()

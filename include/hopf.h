@@ -153,6 +153,28 @@ hopf_status hopf_check_watchdog(hopf_ctx* ctx);
  * Errors: HOPF_EINVAL (unknown method). */
 enum { HOPF_QR_DOUBLEFLOAT = 0, HOPF_QR_TENSOR = 1 };
 hopf_status hopf_set_qr_method(hopf_ctx* ctx, int method);
+/* Autotuning of the mixed-precision tall-factor QR (no counterpart in the
+ * paper; the factorisations themselves are App. A Alg. 1/2).  With enable =
+ * 1, the first QR of every new shape (m rows, p = min(m, k) reflectors, for
+ * factors the tensor-core form applies to) times four configurations on
+ * copies of the matrix, two runs each: tensor-core products or double-float
+ * kernel alone (hopf_set_qr_method) x the cooperative panel kernel on all
+ * the context's SMs or half of them; the fastest is used from then on for
+ * that shape, for the factorisation and the application of its Q alike.
+ * Results differ between configurations at the mixed path's rounding level
+ * (about 1e-9 relative per step), so a tuned run is reproducible only with
+ * the same table.  The first QR of a shape costs about nine times one QR
+ * and two temporary copies of the matrix in device memory.  enable = 0
+ * clears the table (the hopf_set_qr_method choice applies everywhere).
+ * Errors: HOPF_EINVAL. */
+hopf_status hopf_set_autotune(hopf_ctx* ctx, int enable);
+/* The autotuning table: *count receives the number of tuned shapes; the
+ * first min(cap, *count) entries are written as shapes[4 i ..] = (m, p,
+ * method chosen, CTAs chosen: 0 = all) and ms[4 i ..] = the candidates'
+ * times in milliseconds (tensor-core on all SMs, tensor-core on half,
+ * double-float on all, double-float on half; +inf for a candidate that was
+ * not run).  Host arrays, caller-owned.  Errors: HOPF_EINVAL. */
+hopf_status hopf_get_autotune(const hopf_ctx* ctx, int* shapes, float* ms, int cap, int* count);
 /* Limits every cooperative kernel launched by this context to max_ctas
  * CTAs, one per SM (0, the default: all SMs).  Several contexts whose
  * limits add up to at most the SM count run their solves concurrently on

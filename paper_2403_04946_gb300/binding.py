@@ -41,6 +41,8 @@ SIGNATURES = {
     "hopf_set_nu": (_i, [_vp, _d]),
     "hopf_set_svd_method": (_i, [_vp, _i]),
     "hopf_set_qr_method": (_i, [_vp, _i]),
+    "hopf_set_autotune": (_i, [_vp, _i]),
+    "hopf_get_autotune": (_i, [_vp, _pi, C.POINTER(C.c_float), _i, _pi]),
     "hopf_set_wait_limit": (_i, [_vp, _d]),
     "hopf_check_watchdog": (_i, [_vp]),
     "hopf_set_allocator": (_i, [_vp, _vp, _vp]),
@@ -245,6 +247,27 @@ class Context:
 
     def hopf_set_qr_method(self, method):
         self._check(self.lib.hopf_set_qr_method(self.h, int(method)))
+
+    def hopf_set_autotune(self, enable=True):
+        self._check(self.lib.hopf_set_autotune(self.h, 1 if enable else 0))
+
+    def hopf_get_autotune(self):
+        """The autotuning table: one dict per tuned shape."""
+        cnt = C.c_int()
+        self._check(self.lib.hopf_get_autotune(self.h, None, None, 0, C.byref(cnt)))
+        n = cnt.value
+        shapes = (C.c_int * (4 * max(n, 1)))()
+        ms = (C.c_float * (4 * max(n, 1)))()
+        self._check(self.lib.hopf_get_autotune(self.h, shapes, ms, n, C.byref(cnt)))
+        names = ["tensor_all", "tensor_half", "doublefloat_all", "doublefloat_half"]
+        out = []
+        for i in range(n):
+            out.append({"m": shapes[4 * i], "p": shapes[4 * i + 1],
+                        "method": "tensor" if shapes[4 * i + 2] == HOPF_QR_TENSOR else "doublefloat",
+                        "ctas": shapes[4 * i + 3] or "all",
+                        "ms": {names[j]: (None if ms[4 * i + j] == float("inf") else round(ms[4 * i + j], 3))
+                               for j in range(4)}})
+        return out
 
     def hopf_set_svd_method(self, method):
         self._check(self.lib.hopf_set_svd_method(self.h, int(method)))

@@ -83,6 +83,13 @@ struct hopf_ctx {
   int device = 0;
   int svd_method = HOPF_SVD_AUTO;
   int qr_method = HOPF_QR_TENSOR;
+  // per-shape choice of the tall-factor QR configuration (hopf_set_autotune)
+  struct QrTune {
+    int m, p, method, ctas;
+    float ms[4];
+  };
+  int autotune = 0;
+  std::vector<QrTune> tune;
   unsigned int wait_limit_us = 0;  // grid-barrier wait limit (0: the default)
   // persistent staging of point / moment evaluation (grown on demand)
   int* ev_idx = nullptr;
@@ -583,11 +590,45 @@ hk::PhaseTimer phase_timer(hopf_ctx* ctx, int cls_panel) {
   return pt;
 }
 
-// Householder QR of the m x k matrix A (lda) in place: in mixed precision
-// and for tall factors the blocked form with tensor-core products (G
-// receives its panel Grams), otherwise the cooperative kernel alone.
-hopf_status qr_factor(hopf_ctx* ctx, cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb, cplx* G) {
-  if (use_tc(ctx, m, std::min(m, k))) {
+// A configuration of the tall-factor QR: how the products run (the
+// tensor-core blocked form or the double-float kernel alone) and how many
+// CTAs (SMs) the cooperative panel kernel spreads over (0: all the
+// context's).  The factorisation and the application of its Q must use
+// the same one (the panel layout depends on the CTA count).
+struct QrConf {
+  int method, ctas;
+};
+
+const hopf_ctx::QrTune* tune_find(const hopf_ctx* ctx, int m, int p) {
+  for (const auto& t : ctx->tune)
+    if (t.m == m && t.p == p) return &t;
+  return nullptr;
+}
+
+QrConf qr_conf(const hopf_ctx* ctx, int m, int p) {
+  if (ctx->autotune)
+    if (const hopf_ctx::QrTune* t = tune_find(ctx, m, p)) return QrConf{t->method, t->ctas};
+  return QrConf{ctx->qr_method, 0};
+}
+
+// Limits the context's cooperative kernels to `ctas` CTAs while in scope.
+struct CtaCap {
+  hopf_ctx* ctx;
+  int saved;
+  CtaCap(hopf_ctx* c, int ctas) : ctx(c), saved(c->coop.max_ctas) {
+    if (ctas > 0) ctx->coop.max_ctas = ctas;
+  }
+  ~CtaCap() { ctx->coop.max_ctas = saved; }
+};
+
+bool conf_tc(const hopf_ctx* ctx, const QrConf& c, int m, int p) {
+  return ctx->p.precision == HOPF_MIXED && c.method == HOPF_QR_TENSOR && hk::qr_tc_applies(m, p);
+}
+
+hopf_status qr_factor_conf(hopf_ctx* ctx, const QrConf& c, cplx* A, int lda, int m, int k, cplx* tau, cplx* T,
+                           int* nb, cplx* G) {
+  CtaCap cap(ctx, c.ctas);
+  if (conf_tc(ctx, c, m, std::min(m, k))) {
     TRY(tc_reserve(ctx, m, k));
     *nb = 32;
     CK(hk::geqrf_tc(A, lda, m, k, tau, T, G, ctx->tcbuf, ctx->tcbytes, ctx->coop, kTcDigits, ctx->stream,
@@ -598,10 +639,93 @@ hopf_status qr_factor(hopf_ctx* ctx, cplx* A, int lda, int m, int k, cplx* tau, 
   return HOPF_OK;
 }
 
-// C <- Q C with the Q of qr_factor (same m and p = min(m, k)).
+// Times every candidate configuration on copies of A (two runs each, the
+// faster counts) and records the fastest for the shape (m, min(m, k)).
+// Device scratch for the copies and outputs is taken for the duration.
+hopf_status tune_qr(hopf_ctx* ctx, const cplx* A, int lda, int m, int k) {
+  const int p = std::min(m, k);
+  const size_t elems = (size_t)m * k;
+  const int all = hk::coop_sms(ctx->coop);
+  const QrConf cand[4] = {{HOPF_QR_TENSOR, 0}, {HOPF_QR_TENSOR, std::max(1, all / 2)}, {HOPF_QR_DOUBLEFLOAT, 0},
+                          {HOPF_QR_DOUBLEFLOAT, std::max(1, all / 2)}};
+  cplx *orig = nullptr, *work = nullptr, *tau = nullptr, *T = nullptr, *G = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  hopf_status st = HOPF_OK;
+  hopf_ctx::QrTune tu{m, p, ctx->qr_method, 0, {INFINITY, INFINITY, INFINITY, INFINITY}};
+  // the candidates' launches are not part of the caller's profile
+  const bool prof_was = ctx->prof_on;
+  const hopf_profile prof_saved = ctx->prof;
+  ctx->prof_on = false;
+  auto run = [&]() -> hopf_status {
+    CK(dalloc(&orig, elems));
+    CK(dalloc(&work, elems));
+    CK(dalloc(&tau, (size_t)k));
+    CK(dalloc(&T, (size_t)((k + 31) / 32) * 32 * 32));
+    CK(dalloc(&G, hk::qr_tc_gram_elems(k)));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaMemcpy2DAsync(orig, (size_t)m * sizeof(cplx), A, (size_t)lda * sizeof(cplx), (size_t)m * sizeof(cplx), k,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int i = 0; i < 4; ++i) {
+      if (i % 2 == 1 && cand[i].ctas >= all) continue;  // no smaller share to try
+      float best = INFINITY;
+      for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaMemcpyAsync(work, orig, elems * sizeof(cplx), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaEventRecord(e0, ctx->stream));
+        int nb = 32;
+        const hopf_status r = qr_factor_conf(ctx, cand[i], work, m, m, k, tau, T, &nb, G);
+        if (r != HOPF_OK) return r;
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        TRY(check_barrier(ctx));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+      }
+      tu.ms[i] = best;
+    }
+    int bi = -1;
+    for (int i = 0; i < 4; ++i)
+      if (std::isfinite(tu.ms[i]) && (bi < 0 || tu.ms[i] < tu.ms[bi])) bi = i;
+    if (bi >= 0) {
+      tu.method = cand[bi].method;
+      tu.ctas = cand[bi].ctas;
+    }
+    return HOPF_OK;
+  };
+  st = run();
+  ctx->prof_on = prof_was;
+  ctx->prof = prof_saved;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(ctx->stream);
+  dfree(orig);
+  dfree(work);
+  dfree(tau);
+  dfree(T);
+  dfree(G);
+  if (st == HOPF_OK) ctx->tune.push_back(tu);
+  return st;
+}
+
+// Householder QR of the m x k matrix A (lda) in place: in mixed precision
+// and for tall factors the blocked form with tensor-core products (G
+// receives its panel Grams), otherwise the cooperative kernel alone; with
+// autotuning on, the configuration measured fastest for the shape.
+hopf_status qr_factor(hopf_ctx* ctx, cplx* A, int lda, int m, int k, cplx* tau, cplx* T, int* nb, cplx* G) {
+  const int p = std::min(m, k);
+  if (ctx->autotune && ctx->p.precision == HOPF_MIXED && hk::qr_tc_applies(m, p) && !tune_find(ctx, m, p))
+    TRY(tune_qr(ctx, A, lda, m, k));
+  return qr_factor_conf(ctx, qr_conf(ctx, m, p), A, lda, m, k, tau, T, nb, G);
+}
+
+// C <- Q C with the Q of qr_factor (same m and p = min(m, k), same
+// configuration).
 hopf_status qr_apply(hopf_ctx* ctx, const cplx* A, int lda, int m, int p, const cplx* tau, const cplx* T, int nb,
                      const cplx* G, cplx* C, int ldc, int q) {
-  if (use_tc(ctx, m, p)) {
+  const QrConf c = qr_conf(ctx, m, p);
+  CtaCap cap(ctx, c.ctas);
+  if (conf_tc(ctx, c, m, p)) {
     TRY(tc_reserve(ctx, m, q));
     CK(hk::ormqr_tc(A, lda, m, p, tau, G, C, ldc, q, ctx->tcbuf, ctx->tcbytes, &ctx->coop.bar->err, kTcDigits,
                     ctx->stream, phase_timer(ctx, HOPF_K_APPLYQ)));
@@ -1425,6 +1549,29 @@ hopf_status hopf_set_qr_method(hopf_ctx* ctx, int method) {
   if (!ctx) return HOPF_EINVAL;
   if (method != HOPF_QR_DOUBLEFLOAT && method != HOPF_QR_TENSOR) return fail(ctx, HOPF_EINVAL, "unknown QR method %d", method);
   ctx->qr_method = method;
+  return HOPF_OK;
+}
+
+hopf_status hopf_set_autotune(hopf_ctx* ctx, int enable) {
+  if (!ctx) return HOPF_EINVAL;
+  if (enable != 0 && enable != 1) return fail(ctx, HOPF_EINVAL, "enable must be 0 or 1");
+  ctx->autotune = enable;
+  if (!enable) ctx->tune.clear();
+  return HOPF_OK;
+}
+
+hopf_status hopf_get_autotune(const hopf_ctx* ctx, int* shapes, float* ms, int cap, int* count) {
+  if (!ctx || !count || cap < 0 || (cap > 0 && (!shapes || !ms))) return HOPF_EINVAL;
+  *count = (int)ctx->tune.size();
+  const int n = std::min(cap, *count);
+  for (int i = 0; i < n; ++i) {
+    const hopf_ctx::QrTune& t = ctx->tune[i];
+    shapes[4 * i + 0] = t.m;
+    shapes[4 * i + 1] = t.p;
+    shapes[4 * i + 2] = t.method;
+    shapes[4 * i + 3] = t.ctas;
+    for (int j = 0; j < 4; ++j) ms[4 * i + j] = t.ms[j];
+  }
   return HOPF_OK;
 }
 

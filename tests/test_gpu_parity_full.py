@@ -137,21 +137,29 @@ def test_c3_slice_truncation_at_planted_gap(B, precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed-doublefloat", "mixed-tensor"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed-doublefloat", "mixed-tensor", "mixed-autotuned"])
 def test_c3_slice_rk4_step(B, c3_slice, c3_step_oracle, precision):
     """One fused hopf_step of the saturated C3 slice (dt = 1.2e-5, tol 1e-7,
     cap 64) with the oracle's ranks replayed: four K-roundings of 384-rank
     operator outputs, three roundings at 128 and one at 320.  FP64 within
     1e-10 of oracle.tt.rk4_step; mixed within 1e-6 for Phi, mean and
-    covariance."""
+    covariance, also when every tall shape's QR configuration is picked by
+    the autotuner (the table then lists the shapes with their timings)."""
     x = c3_slice[0]
     want, log = c3_step_oracle
     mixed = precision.startswith("mixed")
     ctx = B.Context(d=D, n=N, nu=NU3, tol=TOL3, rank_cap=R, L=L3,
                     precision=B.HOPF_MIXED if mixed else B.HOPF_FP64)
-    ctx.hopf_set_qr_method(B.HOPF_QR_TENSOR if precision == "mixed-tensor" else B.HOPF_QR_DOUBLEFLOAT)
+    ctx.hopf_set_qr_method(B.HOPF_QR_DOUBLEFLOAT if precision == "mixed-doublefloat" else B.HOPF_QR_TENSOR)
+    if precision == "mixed-autotuned":
+        ctx.hopf_set_autotune(True)
     t = ctx.tt_from_host(x, max_rank=R)
     out = ctx.hopf_step(t, DT3, 1, record=True, replay=log)
+    if precision == "mixed-autotuned":
+        table = ctx.hopf_get_autotune()
+        print("\nautotune", table)
+        assert table and all(e["m"] >= 4096 for e in table)
+        assert all(e["ms"]["tensor_all"] and e["ms"]["doublefloat_all"] for e in table)
     assert np.array_equal(out["ranks"], log)
     got = ctx.tt_to_host(t)
     e, ep = rel_tt(got, want), sampled(got, want, 13)
