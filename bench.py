@@ -409,6 +409,59 @@ def ensemble_rate(stream_int, nsteps=1, qr_method=1):
             "speedup": out["concurrent"] / out["sequential"]}
 
 
+def c4_sample(stream_int, count=4, nsteps=1, qr_method=1):
+    """The first `count` draws of the C4 ensemble generator (seed 0..): d in
+    8..48, n in {64, 96, 128}, nu, sigma, ell and four Fourier modes of the
+    mean drawn per instance, cap 64, tol 1e-7, dt 1e-5, mixed precision; each
+    from its own Gaussian initial state (hopf_cell_moments +
+    hopf_init_gaussian).  After one untimed step (workspaces), one RK4 step
+    of every instance one at a time on the whole GPU, then one all at once
+    (hopf_step_ensemble, equal SM shares).  Ensemble steps per second, wall
+    clock."""
+    import torch
+    from paper_2403_04946_gb300 import binding as B
+    import synthetic
+    draws = [synthetic.ensemble_member(s) for s in range(count)]
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    share = max(1, sms // count)
+    t0 = time.perf_counter()
+    members = []
+    for w in draws:
+        s = torch.cuda.Stream()
+        ctx = B.Context(d=w.d, n=w.n, nu=w.nu, tol=w.tol, rank_cap=w.cap, L=0.0, stream=s.cuda_stream,
+                        precision=B.HOPF_MIXED)
+        ctx.hopf_set_qr_method(qr_method)
+        m0, C0 = ctx.hopf_cell_moments(w.alpha, w.beta, w.sigma, w.ell)
+        t = ctx.hopf_init_gaussian(m0, C0)
+        members.append((ctx, t, s, max(ctx.tt_get_ranks(t))))
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t0
+    for (c, t, _, _), w in zip(members, draws):
+        c.hopf_step(t, w.dt, nsteps)  # workspaces
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (c, t, _, _), w in zip(members, draws):
+        c.hopf_step(t, w.dt, nsteps)
+    torch.cuda.synchronize()
+    seq = len(draws) * nsteps / (time.perf_counter() - t0)
+    for c, _, _, _ in members:
+        c.hopf_set_max_ctas(share)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.hopf_step_ensemble([(c, t) for c, t, _, _ in members], draws[0].dt, nsteps)
+    torch.cuda.synchronize()
+    conc = len(draws) * nsteps / (time.perf_counter() - t0)
+    ranks = [max(c.tt_get_ranks(t)) for c, t, _, _ in members]
+    for c, t, _, _ in members:
+        c.tt_free(t)
+        c.close()
+    return {"generator": "C4 (synthetic.ensemble_member), seeds 0..%d" % (count - 1),
+            "instances": [{"d": w.d, "n": w.n, "initial_max_rank": m[3], "max_rank_after": r}
+                          for w, m, r in zip(draws, members, ranks)],
+            "initial_states_s": t_init, "sms_per_instance_concurrent": share, "precision": "mixed",
+            "steps_per_s_sequential": seq, "steps_per_s_concurrent": conc, "speedup": conc / seq}
+
+
 def surrogate_rate(ntrain=128, ncalib=16, nheld=24, iters=3000, batch=128):
     """The learned surrogate on the C4 parameter distribution at the C1 grid
     (d=4, n=24, dt=1e-2, T = 0.01..0.1): solver-made training data, GPU
@@ -555,6 +608,8 @@ def run_ours(args, rank, world, local_rank):
 
     err = natural_state_error(w, stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
     ens = ensemble_rate(stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
+    c4 = c4_sample(stream.cuda_stream, count=args.c4_count, qr_method=qr_method) \
+        if (not args.no_error_check and args.c4_count > 0) else None
     sur = surrogate_rate() if (world == 1 and not args.no_surrogate) else None
     paper = paper_workload(stream.cuda_stream, qr_method=qr_method) if not args.no_error_check else None
 
@@ -593,6 +648,7 @@ def run_ours(args, rank, world, local_rank):
                      "roofline": roofline(prof64, False, peaks), "kernel_shares": shares64},
             "mixed_vs_fp64_error": err,
             "ensemble": ens,
+            "c4_sample": c4,
             "surrogate": sur,
             "paper_workload": paper,
             "apply_gbs": apply_gbs,
@@ -615,6 +671,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--c4-count", type=int, default=4,
+                    help="instances of the C4 ensemble generator stepped alone and together (0: skip)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --qr-method for every shape instead of the per-shape autotuned configuration")
     ap.add_argument("--qr-method", choices=["tensor", "doublefloat"], default="tensor",
