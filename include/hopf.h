@@ -398,7 +398,11 @@ hopf_status tt_set_from_host(hopf_tt* t, const int* ranks, const double* cores);
  * member, `members` members back to back ([members][P]).  The library keeps
  * FP32 master parameters and Adam moments; products read BF16 copies of the
  * weights (round to nearest even) with FP32 activations and FP32
- * accumulation; biases stay FP32.
+ * accumulation; biases stay FP32.  The products run on the tensor cores
+ * (BF16 x BF16 -> FP32): an FP32 operand enters as three BF16 parts
+ * (hi + mid + lo, 24 significant bits), so the result is the FP32 product
+ * up to FP32 accumulation rounding.  A bounded wait that expires inside
+ * them returns HOPF_ETIMEOUT. 
  *
  * Normalisation.  hopf_mlp_set_data stores a data set and its per-column
  * mean and population standard deviation (1 for a constant column).  The

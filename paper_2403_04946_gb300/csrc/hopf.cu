@@ -1350,6 +1350,8 @@ hopf_status init_cross(hopf_ctx* ctx, const double* m0, const double* C0, hopf_t
 hopf_ctx* hopf_internal_tt_ctx(const hopf_tt* t) { return t->ctx; }
 cudaStream_t hopf_internal_stream(const hopf_ctx* ctx) { return ctx->stream; }
 int hopf_internal_device(const hopf_ctx* ctx) { return ctx->device; }
+int* hopf_internal_wait_record(hopf_ctx* ctx) { return &ctx->coop.bar->err; }
+hopf_status hopf_internal_check_waits(hopf_ctx* ctx) { return check_barrier(ctx); }
 hopf_status hopf_internal_tt_view(const hopf_tt* t, const double2* const** d_ptrs, const int** d_ranks,
                                   int* d, int* n, int* maxr) {
   *d_ptrs = t->d_ptrs;

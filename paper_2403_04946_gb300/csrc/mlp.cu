@@ -2,13 +2,18 @@
 // weights, FP32 activations and FP32 accumulation, trained by Adam on the
 // solver's outputs, every step a kernel of this file.
 //
-// Sizes are small (widths of a few hundred, batches of a few hundred to a
-// few thousand), so the products are plain tiled SIMT kernels: 64 x 64
-// output tiles, 16-deep K slabs staged in shared memory, a 4 x 4 register
-// block per thread, the ensemble members on gridDim.z.  A training step is
-// about twenty launches; it is captured once as a CUDA graph and replayed,
-// with the step number read from device memory so that the same graph
-// walks through the batch-index and learning-rate tables.
+// The products run on the tensor cores (tcgen05.mma, BF16 x BF16 -> FP32 in
+// tensor memory, operands staged by TMA): weights are BF16, and every FP32
+// operand (activations, gradients) is carried as three BF16 parts
+// x = p0 + p1 + p2 (each the BF16 rounding of what the previous parts
+// leave: 24 significant bits, all of FP32's), so the sum of the part
+// products in one FP32 accumulator is the FP32-activation product up to
+// FP32 accumulation rounding.  Parts products below 2^-24 of the leading one
+// are skipped (pairs i + j > 2).  128 x 128 output tiles, the ensemble
+// members on gridDim.z, fused bias / GELU / GELU' epilogues.  A training
+// step is about thirty launches; it is captured once as a CUDA graph and
+// replayed, with the step number read from device memory so that the same
+// graph walks through the batch-index and learning-rate tables.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -19,6 +24,7 @@
 #include <vector>
 
 #include "../../include/hopf.h"
+#include "tcgen05.cuh"
 
 // The library's device allocator (hopf.cu: cudaMalloc or the caller's
 // functions, hopf_set_allocator) and its count of live objects.
@@ -33,10 +39,13 @@ typedef __nv_bfloat16 bf16;
 // Internal accessors defined in hopf.cu.
 cudaStream_t hopf_internal_stream(const hopf_ctx* ctx);
 void hopf_internal_set_error(hopf_ctx* ctx, const char* msg);
+// The device record a kernel's expired bounded wait is written to, and the
+// host check of it (HOPF_ETIMEOUT once a wait expired; resets the record).
+int* hopf_internal_wait_record(hopf_ctx* ctx);
+hopf_status hopf_internal_check_waits(hopf_ctx* ctx);
 
 namespace {
 
-constexpr int kTM = 64, kTN = 64, kTK = 16, kGemmThreads = 256;
 constexpr int kMaxDim = 4096, kMaxMembers = 64;
 constexpr float kBeta1 = 0.9f, kBeta2 = 0.999f, kAdamEps = 1e-8f;
 
@@ -51,12 +60,14 @@ __device__ __forceinline__ float ld(const bf16* p) { return __bfloat162float(*p)
 enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_GELU = 2, EPI_GELU_GRAD = 3 };
 
 // C(m, n) = sum_k A(m, k) B(k, n) for member e = blockIdx.z, with
-// A(m, k) = A[e ame + m sam + k sak] and B(k, n) = B[e bme + k sbk + n sbn].
+// A(m, k) = A[e ame + m sam + k sak] and B(k, n) = B[e bme + k sbk + n sbn]
+// (A in FP32, B in FP32 or BF16: b_bf16).
 struct GemmArgs {
   const void* A;
   long long sam, sak, ame;
   const void* B;
   long long sbk, sbn, bme;
+  int b_bf16;
   int M, N, K;
   int epi;
   const float* bias;  // EPI_BIAS*: bias[e biasme + n]
@@ -69,64 +80,163 @@ struct GemmArgs {
   long long ldzp, zpme;
 };
 
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(kGemmThreads) mlp_gemm_kernel(GemmArgs a) {
-  __shared__ float As[kTK][kTM + 4];
-  __shared__ float Bs[kTK][kTN + 4];
-  const int e = blockIdx.z;
-  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-  const TA* A = static_cast<const TA*>(a.A) + e * a.ame;
-  const TB* B = static_cast<const TB*>(a.B) + e * a.bme;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const bool a_kfast = (a.sak == 1), b_nfast = (a.sbn == 1);
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < a.K; k0 += kTK) {
-    // Consecutive threads walk the operand's unit-stride index.
-    for (int q = tid; q < kTM * kTK; q += kGemmThreads) {
-      const int mm = a_kfast ? q / kTK : q % kTM;
-      const int kk = a_kfast ? q % kTK : q / kTM;
-      const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < a.M && gk < a.K) ? ld(A + gm * a.sam + gk * a.sak) : 0.f;
+// ---- tensor-core products ----------------------------------------------------
+constexpr int kMmM = 128, kMmN = 128;   // output tile
+constexpr int kMmParts = 3;             // BF16 parts of an FP32 operand
+constexpr int kMmThreads = 192;         // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
+constexpr int kMmStages = 2;
+constexpr int kMmTmemCols = kMmN;       // one FP32 accumulator column per output column
+constexpr uint32_t kMmIdesc = hk::umma_idesc_bf16(kMmM, kMmN);
+static_assert(hk::kTmaSlab == 64, "one K slab is one 128-byte TMA box row");
+
+__host__ __device__ constexpr int mm_a_plane() { return kMmM * 64 * 2; }  // 16 KB
+__host__ __device__ constexpr int mm_b_plane() { return kMmN * 64 * 2; }  // 16 KB
+__host__ __device__ constexpr int mm_stage(int sa, int sb) { return sa * mm_a_plane() + sb * mm_b_plane(); }
+size_t mm_smem_bytes() { return (size_t)kMmStages * mm_stage(kMmParts, kMmParts) + 1024; }
+
+// Parts of an operand view for the tensor cores: X(r, k) = X[e xme + r srow
+// + k sk] (FP32 or BF16) for r < R, k < K, written as S BF16 parts in
+// K-major planes P[e][j][r][ldk] (zero for k >= K).  Part j is the BF16
+// rounding of X minus parts 0..j-1 (exact in FP32).
+template <typename T>
+__global__ void to_parts_kernel(const T* X, long long srow, long long sk, long long xme, int R, int K, int S,
+                                bf16* P, int ldk) {
+  const int e = blockIdx.y;
+  const long long n = (long long)R * ldk;
+  bf16* out = P + (long long)e * S * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n; idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / ldk), k = (int)(idx % ldk);
+    float v = (k < K) ? ld(X + e * xme + r * srow + k * sk) : 0.f;
+    for (int j = 0; j < S; ++j) {
+      const bf16 q = __float2bfloat16_rn(v);
+      out[(long long)j * n + idx] = q;
+      v -= __bfloat162float(q);
     }
-    for (int q = tid; q < kTK * kTN; q += kGemmThreads) {
-      const int nn = b_nfast ? q % kTN : q / kTK;
-      const int kk = b_nfast ? q / kTN : q % kTK;
-      const int gn = n0 + nn, gk = k0 + kk;
-      Bs[kk][nn] = (gn < a.N && gk < a.K) ? ld(B + gk * a.sbk + gn * a.sbn) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTK; ++kk) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty + 16 * i;
-    if (m >= a.M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx + 16 * j;
-      if (n >= a.N) continue;
-      float v = acc[i][j];
-      if (a.epi == EPI_BIAS || a.epi == EPI_BIAS_GELU) v += a.bias[e * a.biasme + n];
-      if (a.epi == EPI_GELU_GRAD) v *= gelu_grad(a.Zp[e * a.zpme + m * a.ldzp + n]);
-      a.C[e * a.cme + m * a.ldc + n] = v;
-      if (a.epi == EPI_BIAS_GELU) a.H[e * a.hme + m * a.ldh + n] = gelu(v);
+}
+
+struct MmArgs {
+  int M, N, nslab;  // output M x N, K in slabs of 64 (zero-padded)
+  int SA, SB;       // parts of A and B
+  int a_shared;     // every member reads member 0's A parts
+  GemmArgs g;       // epilogue and output layout (A/B fields unused)
+  int* err;         // expiry record of a bounded wait
+};
+
+// C(m, n) = sum_k A(m, k) B(n, k) for member e = blockIdx.z, over the part
+// pairs (i, j), i + j < max(SA, SB), all into one FP32 accumulator; one CTA
+// per 128 x 128 output tile.  Warp 4 streams the K slabs of the parts into
+// a two-stage ring with TMA, warp 5 issues the MMAs, warps 0-3 read the
+// accumulator back (a thread per row) and apply the epilogue.  Waits are
+// bounded like those of the complex product kernel.
+__global__ void __launch_bounds__(kMmThreads, 1)
+    mlp_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, MmArgs a) {
+  extern __shared__ unsigned char mm_smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kMmStages], empty_bar[kMmStages], acc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(mm_smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kMmM, n0 = blockIdx.x * kMmN, e = blockIdx.z;
+  const int SA = a.SA, SB = a.SB, smax = SA > SB ? SA : SB;
+  const int sbytes = mm_stage(SA, SB);
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kMmStages; ++st) {
+      hk::mbar_init(&full_bar[st], 1);
+      hk::mbar_init(&empty_bar[st], 1);
     }
+    hk::mbar_init(&acc_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(hk::smem_u32(&tmem_slot)),
+                 "r"(kMmTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  hk::tc_fence_before();
+  __syncthreads();
+  hk::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* vabort = &abort_flag;
+  const int za = (a.a_shared ? 0 : e) * SA, zb = e * SB;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int st = 0; st < a.nslab; ++st) {
+        const int slot = st % kMmStages;
+        if (st >= kMmStages && !hk::mbar_wait(&empty_bar[slot], ((st / kMmStages) - 1) & 1, vabort, a.err)) break;
+        unsigned char* base = smem + (size_t)slot * sbytes;
+        hk::mbar_expect_tx(&full_bar[slot], (uint32_t)sbytes);
+        for (int j = 0; j < SA; ++j)
+          hk::tma_load_3d(base + (size_t)j * mm_a_plane(), &mapA, &full_bar[slot], st * 64, m0, za + j);
+        for (int j = 0; j < SB; ++j)
+          hk::tma_load_3d(base + (size_t)SA * mm_a_plane() + (size_t)j * mm_b_plane(), &mapB, &full_bar[slot], st * 64,
+                          n0, zb + j);
+        issued = st + 1;
+      }
+      for (int st = issued > kMmStages ? issued - kMmStages : 0; st < issued; ++st) {
+        const uint64_t t0 = global_ns();
+        while (!hk::mbar_try_wait(&full_bar[st % kMmStages], (st / kMmStages) & 1))
+          if (global_ns() - t0 > hk::kTcWaitNs) break;
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      for (int st = 0; st < a.nslab; ++st) {
+        const int slot = st % kMmStages;
+        if (!hk::mbar_wait(&full_bar[slot], (st / kMmStages) & 1, vabort, a.err)) break;
+        hk::tc_fence_after();
+        const uint32_t abase = hk::smem_u32(smem + (size_t)slot * sbytes);
+        const uint32_t bbase = abase + (uint32_t)(SA * mm_a_plane());
+        bool first = (st == 0);
+        for (int i = 0; i < SA; ++i)
+          for (int j = 0; j < SB; ++j) {
+            if (i + j >= smax) continue;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = hk::sw128_desc(abase + (uint32_t)(i * mm_a_plane() + kk * 32));
+              const uint64_t bd = hk::sw128_desc(bbase + (uint32_t)(j * mm_b_plane() + kk * 32));
+              hk::umma(tmem, ad, bd, kMmIdesc, first ? 0u : 1u);
+              first = false;
+            }
+          }
+        hk::umma_commit(&empty_bar[slot]);
+      }
+      hk::umma_commit(&acc_bar);
+    }
+  } else {
+    const bool ok = hk::mbar_wait(&acc_bar, 0, vabort, a.err);
+    hk::tc_fence_after();
+    const int m = m0 + 32 * warp + lane;
+    const GemmArgs& g = a.g;
+    if (ok && !*vabort) {
+#pragma unroll 1
+      for (int h = 0; h < kMmN / 16; ++h) {
+        float v[16];
+        hk::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * h), v);
+        if (m >= a.M) continue;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int n = n0 + 16 * h + q;
+          if (n >= a.N) continue;
+          float x = v[q];
+          if (g.epi == EPI_BIAS || g.epi == EPI_BIAS_GELU) x += g.bias[e * g.biasme + n];
+          if (g.epi == EPI_GELU_GRAD) x *= gelu_grad(g.Zp[e * g.zpme + (long long)m * g.ldzp + n]);
+          g.C[e * g.cme + (long long)m * g.ldc + n] = x;
+          if (g.epi == EPI_BIAS_GELU) g.H[e * g.hme + (long long)m * g.ldh + n] = gelu(x);
+        }
+      }
+    }
+  }
+  hk::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    hk::tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmTmemCols) : "memory");
   }
 }
 
@@ -339,6 +449,8 @@ struct hopf_mlp {
   float *lr = nullptr, *loss = nullptr;
   long long it_cap = 0;
   double *qx = nullptr, *qy = nullptr, *qb = nullptr, *qm = nullptr, *qbase = nullptr, *qscale = nullptr;
+  bf16 *pa = nullptr, *pb = nullptr;  // BF16 parts of the tensor-core products' operands
+  size_t pa_elems = 0, pb_elems = 0;
   std::vector<void*> allocs;
 };
 
@@ -387,14 +499,72 @@ void layer_dims(const hopf_mlp_params& p, std::vector<int>& dims) {
   dims.push_back(p.n_out);
 }
 
-cudaError_t launch_gemm_f_bf(const GemmArgs& a, int members, cudaStream_t s) {
-  dim3 grid((a.N + kTN - 1) / kTN, (a.M + kTM - 1) / kTM, members);
-  mlp_gemm_kernel<float, bf16><<<grid, kGemmThreads, 0, s>>>(a);
-  return cudaGetLastError();
+int rup64(long long x) { return (int)((x + 63) / 64 * 64); }
+
+// The product kernel's shared-memory limit, raised once per process (before
+// any stream capture: hopf_mlp_create).
+cudaError_t mm_prepare() {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, []() {
+    attr = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mm_smem_bytes());
+  });
+  return attr;
 }
-cudaError_t launch_gemm_f_f(const GemmArgs& a, int members, cudaStream_t s) {
-  dim3 grid((a.N + kTN - 1) / kTN, (a.M + kTM - 1) / kTM, members);
-  mlp_gemm_kernel<float, float><<<grid, kGemmThreads, 0, s>>>(a);
+
+// Parts scratch for a model (elements of each buffer): A operands are the
+// activations (batch x width, forward and dX) or the output gradients
+// transposed (width x batch, dW); B operands the weights (one part) or the
+// activations transposed (dW).
+void parts_sizes(const hopf_mlp_params& p, const std::vector<int>& dims, size_t* pa, size_t* pb) {
+  const long long mb = p.max_batch;
+  int dmax = 0;
+  for (int d : dims) dmax = std::max(dmax, d);
+  const size_t a1 = (size_t)mb * rup64(dmax), a2 = (size_t)dmax * rup64(mb);
+  *pa = (size_t)p.members * kMmParts * std::max(a1, a2);
+  *pb = (size_t)p.members * kMmParts * (size_t)dmax * rup64(std::max<long long>(mb, dmax));
+}
+
+// C = A B (GemmArgs layout) on the tensor cores: the operands are cut into
+// BF16 parts (three for FP32, one for BF16) in K-major planes, then one
+// tensor-core launch over all members.  a_shared: every member reads member
+// 0's A (ame = 0).
+cudaError_t launch_gemm(hopf_mlp* mm, const GemmArgs& g, int members) {
+  const int M = g.M, N = g.N, K = g.K;
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  const int ldk = rup64(K);
+  const int SA = kMmParts, SB = g.b_bf16 ? 1 : kMmParts;
+  const int a_shared = g.ame == 0 && members > 1;
+  const int ma = a_shared ? 1 : members;
+  if ((size_t)ma * SA * M * ldk > mm->pa_elems || (size_t)members * SB * N * ldk > mm->pb_elems)
+    return cudaErrorInvalidValue;
+  cudaStream_t s = mm->s;
+  // A(m, k) = A[e ame + m sam + k sak]; B as rows n, K-values k: B[e bme + n sbn + k sbk]
+  to_parts_kernel<float><<<dim3(blocks_for((long long)M * ldk, 256, 1024), ma), 256, 0, s>>>(
+      static_cast<const float*>(g.A), g.sam, g.sak, g.ame, M, K, SA, mm->pa, ldk);
+  if (g.b_bf16)
+    to_parts_kernel<bf16><<<dim3(blocks_for((long long)N * ldk, 256, 1024), members), 256, 0, s>>>(
+        static_cast<const bf16*>(g.B), g.sbn, g.sbk, g.bme, N, K, SB, mm->pb, ldk);
+  else
+    to_parts_kernel<float><<<dim3(blocks_for((long long)N * ldk, 256, 1024), members), 256, 0, s>>>(
+        static_cast<const float*>(g.B), g.sbn, g.sbk, g.bme, N, K, SB, mm->pb, ldk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mapA, mapB;
+  e = hk::plane_map(&mapA, mm->pa, ldk, ldk, M, ma * SA, kMmM);
+  if (e == cudaSuccess) e = hk::plane_map(&mapB, mm->pb, ldk, ldk, N, members * SB, kMmN);
+  if (e != cudaSuccess) return e;
+  MmArgs args{};
+  args.M = M;
+  args.N = N;
+  args.nslab = ldk / 64;
+  args.SA = SA;
+  args.SB = SB;
+  args.a_shared = a_shared;
+  args.g = g;
+  args.err = hopf_internal_wait_record(mm->ctx);
+  const dim3 grid((N + kMmN - 1) / kMmN, (M + kMmM - 1) / kMmM, members);
+  mlp_tc_kernel<<<grid, kMmThreads, mm_smem_bytes(), s>>>(mapA, mapB, args);
   return cudaGetLastError();
 }
 
@@ -413,6 +583,7 @@ cudaError_t forward(hopf_mlp* mm, int batch, bool x0_shared) {
     a.sbk = 1;
     a.sbn = fi;
     a.bme = P;
+    a.b_bf16 = 1;
     a.M = batch;
     a.N = fo;
     a.K = fi;
@@ -429,7 +600,7 @@ cudaError_t forward(hopf_mlp* mm, int batch, bool x0_shared) {
     } else {
       a.epi = EPI_BIAS;
     }
-    cudaError_t e = launch_gemm_f_bf(a, mm->p.members, mm->s);
+    cudaError_t e = launch_gemm(mm, a, mm->p.members);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -458,7 +629,7 @@ cudaError_t backward(hopf_mlp* mm, int batch) {
     a.C = mm->g + mm->woff[l];
     a.ldc = fi;
     a.cme = P;
-    cudaError_t e = launch_gemm_f_f(a, mm->p.members, mm->s);
+    cudaError_t e = launch_gemm(mm, a, mm->p.members);
     if (e != cudaSuccess) return e;
     colsum_kernel<<<dim3((fo + 255) / 256, mm->p.members), 256, 0, mm->s>>>(Gc, fo, gme, batch, fo,
                                                                             mm->g + mm->boff[l], P);
@@ -473,6 +644,7 @@ cudaError_t backward(hopf_mlp* mm, int batch) {
     b.sbk = fi;
     b.sbn = 1;
     b.bme = P;
+    b.b_bf16 = 1;
     b.M = batch;
     b.N = fi;
     b.K = fo;
@@ -483,7 +655,7 @@ cudaError_t backward(hopf_mlp* mm, int batch) {
     b.Zp = mm->Z[l - 1];
     b.ldzp = fi;
     b.zpme = mb * fi;
-    if ((e = launch_gemm_f_bf(b, mm->p.members, mm->s)) != cudaSuccess) return e;
+    if ((e = launch_gemm(mm, b, mm->p.members)) != cudaSuccess) return e;
     std::swap(Gc, Gn);
   }
   return cudaSuccess;
@@ -591,7 +763,8 @@ hopf_status hopf_mlp_create(hopf_ctx* ctx, const hopf_mlp_params* p, const float
   };
   hopf_status st = HOPF_OK;
   do {
-    cudaError_t e = cudaStreamCreateWithFlags(&mm->s, cudaStreamNonBlocking);
+    cudaError_t e = mm_prepare();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mm->s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = malloc_track(mm, &mm->w, tot);
     if (e == cudaSuccess) e = malloc_track(mm, &mm->m, tot);
     if (e == cudaSuccess) e = malloc_track(mm, &mm->v, tot);
@@ -614,6 +787,9 @@ hopf_status hopf_mlp_create(hopf_ctx* ctx, const hopf_mlp_params* p, const float
     if (e == cudaSuccess) e = malloc_track(mm, &mm->qm, (size_t)M * mb * p->n_out);
     if (e == cudaSuccess) e = malloc_track(mm, &mm->qbase, (size_t)mb * p->n_out);
     if (e == cudaSuccess) e = malloc_track(mm, &mm->qscale, (size_t)mb);
+    parts_sizes(*p, mm->dims, &mm->pa_elems, &mm->pb_elems);
+    if (e == cudaSuccess) e = malloc_track(mm, &mm->pa, mm->pa_elems);
+    if (e == cudaSuccess) e = malloc_track(mm, &mm->pb, mm->pb_elems);
     if (e == cudaSuccess) e = join_ctx(mm);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mm->w, init, tot * sizeof(float), cudaMemcpyHostToDevice, mm->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mm->m, 0, tot * sizeof(float), mm->s);
@@ -750,7 +926,7 @@ hopf_status hopf_mlp_train(hopf_mlp* mm, int iters, int batch, const int* idx, c
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   MCK(e);
-  return HOPF_OK;
+  return hopf_internal_check_waits(mm->ctx);
 }
 
 hopf_status hopf_mlp_loss_grad(hopf_mlp* mm, int batch, const int* idx, float* loss, float* grad) {
@@ -781,7 +957,7 @@ hopf_status hopf_mlp_loss_grad(hopf_mlp* mm, int batch, const int* idx, float* l
   MCK(cudaMemcpyAsync(loss, mm->loss, (size_t)M * sizeof(float), cudaMemcpyDeviceToHost, mm->s));
   MCK(cudaMemcpyAsync(grad, mm->g, (size_t)M * mm->P * sizeof(float), cudaMemcpyDeviceToHost, mm->s));
   MCK(cudaStreamSynchronize(mm->s));
-  return HOPF_OK;
+  return hopf_internal_check_waits(mm->ctx);
 }
 
 hopf_status hopf_mlp_predict(hopf_mlp* mm, int nq, const double* x, const double* base, const double* scale,
@@ -820,7 +996,7 @@ hopf_status hopf_mlp_predict(hopf_mlp* mm, int nq, const double* x, const double
                             (size_t)c * n_out * sizeof(double), cudaMemcpyDeviceToHost, mm->s));
     MCK(cudaStreamSynchronize(mm->s));
   }
-  return HOPF_OK;
+  return hopf_internal_check_waits(mm->ctx);
 }
 
 }  // extern "C"

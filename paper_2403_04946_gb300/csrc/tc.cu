@@ -40,6 +40,7 @@
 #include <mutex>
 
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace hk {
 
@@ -52,106 +53,16 @@ constexpr int kMaxDigits = 5;    // 3 products x 5 levels x 32 columns = 480 TME
 constexpr int kTmemCols = 512;
 constexpr int kStages = 2;
 constexpr int kTcThreads = 192;  // warps 0-3 epilogue, 4 producer, 5 MMA
-constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint64_t kWaitNs = kTcWaitNs;
+static_assert(kTmaSlab == 64, "digit slabs are one 128-byte TMA box row");
 
 __host__ __device__ constexpr int a_plane_bytes() { return kTcM * kSlab * 2; }  // 16 KB
 __host__ __device__ constexpr int b_plane_bytes() { return kTcN * kSlab * 2; }  // 4 KB
 __host__ __device__ int stage_bytes(int S) { return S * (a_plane_bytes() + b_plane_bytes()); }
 size_t tc_smem_bytes(int S) { return (size_t)kStages * stage_bytes(S) + 1024; }
 
-DV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+constexpr uint32_t kIdesc = umma_idesc_bf16(kTcM, kTcN);
 
-DV void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-DV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-DV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase of `bar` with the given parity.  Returns false if the
-// kernel is aborting (flag set by another role) or the wait expired (then
-// the flag is set here and the expiry recorded in *err).
-DV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
-  uint64_t t0 = 0;
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0u) {
-      if (*abort_flag) return false;
-      const uint64_t now = global_ns();
-      if (t0 == 0) {
-        t0 = now;
-      } else if (now - t0 > kWaitNs) {
-        *abort_flag = 1;
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-
-DV void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major BF16 tile written by TMA with
-// the 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart.
-DV uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address / 16
-  d |= (uint64_t)1 << 16;                   // leading-dimension offset (unused with this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;         // stride between 8-row atoms / 16
-  d |= (uint64_t)1 << 46;                   // descriptor version of tcgen05
-  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: dense BF16 x BF16 -> FP32, both operands K-major,
-// M = 128, N = kTcN.
-constexpr uint32_t kIdesc = (1u << 4)                      // D in FP32
-                            | (1u << 7)                    // A in BF16
-                            | (1u << 10)                   // B in BF16
-                            | ((uint32_t)(kTcN >> 3) << 17)  // N / 8
-                            | ((uint32_t)(kTcM >> 4) << 24);  // M / 16
-
-DV void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          dtmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
-      : "memory");
-}
-DV void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-DV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-DV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-DV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
 
 struct TcArgs {
   int M, N, K, S, Kc, nchunks;
@@ -249,7 +160,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int kk = 0; kk < kSlab / 16; ++kk) {
               const uint64_t ad = sw128_desc(abase + (uint32_t)(i * a_plane_bytes() + kk * 32));
               const uint64_t bd = sw128_desc(bbase + (uint32_t)(j * b_plane_bytes() + kk * 32));
-              umma(acc, ad, bd, (slab > 0 || i > 0 || kk > 0) ? 1u : 0u);
+              umma(acc, ad, bd, kIdesc, (slab > 0 || i > 0 || kk > 0) ? 1u : 0u);
             }
           }
         }
@@ -551,41 +462,6 @@ __global__ void reduce_parts_kernel(const cplx* part, int M, int N, int nz, long
   cplx r = mk(alpha * s.x, alpha * s.y);
   if (accumulate) r = cadd(*p, r);
   *p = r;
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no
-// link-time dependency on libcuda).
-using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeFn encode_fn() {
-  static EncodeFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, []() {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(p);
-  });
-  return fn;
-}
-
-// 3-D map over digit planes [planes][rows][ldk] BF16 with a box of
-// kSlab x box_rows x 1 and the 128-byte swizzle; rows beyond `rows` and K
-// beyond `K` read as zero.
-cudaError_t plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int K, long long ldk, int rows, int nplanes,
-                      int box_rows) {
-  EncodeFn fn = encode_fn();
-  if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
-  const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)ldk * 2 * (cuuint64_t)rows};
-  const cuuint32_t box[3] = {(cuuint32_t)kSlab, (cuuint32_t)box_rows, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(planes), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
