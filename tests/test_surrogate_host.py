@@ -46,26 +46,29 @@ def test_param_count_matches_layout(lib):
 
 
 def test_dataset_pairs_rates_with_initial_moments(monkeypatch):
-    """dataset(): one pair per (solve, snapshot > 0), input [params(T), y0],
-    target (y(T) - y0) / T; the solver is replaced by a known table."""
+    """dataset(): one pair per (solve, snapshot > 0), input [params(T), y0,
+    ydot0], target (y(T) - y0 - T ydot0) / T, base y0 + T ydot0; the solver
+    is replaced by known tables."""
     from paper_2403_04946_gb300 import surrogate as S
     members = [synthetic.surrogate_member(s) for s in (1, 2)]
     table = np.arange(2 * 3 * 14, dtype=float).reshape(2, 3, 14) ** 1.5
+    rates = -np.arange(2 * 14, dtype=float).reshape(2, 14) ** 0.5
 
-    def fake_solve(ms, steps, **kw):
-        assert steps == [0, 2, 5]
-        return table[: len(ms)]
+    def fake_solve(ms, steps, rate0=False, **kw):
+        assert steps == [0, 2, 5] and rate0
+        return table[: len(ms)], rates[: len(ms)]
 
     monkeypatch.setattr(S, "solve", fake_solve)
-    X, R, Y0, YT, T = S.dataset(members, [5, 2])
-    assert X.shape == (4, S.n_in(4)) and R.shape == (4, 14)
+    X, R, BASE, YT, T = S.dataset(members, [5, 2])
+    assert X.shape == (4, S.n_in(4)) == (4, 12 + 28) and R.shape == (4, 14)
     dt = members[0].dt
     np.testing.assert_allclose(T, [2 * dt, 5 * dt, 2 * dt, 5 * dt])
     np.testing.assert_array_equal(X[1, :S.N_PARAMS], S.params(members[0], 5 * dt))
-    np.testing.assert_array_equal(X[3, S.N_PARAMS:], table[1, 0])
-    np.testing.assert_allclose(R[2], (table[1, 1] - table[1, 0]) / (2 * dt))
+    np.testing.assert_array_equal(X[3, S.N_PARAMS:S.N_PARAMS + 14], table[1, 0])
+    np.testing.assert_array_equal(X[3, S.N_PARAMS + 14:], rates[1])
+    np.testing.assert_allclose(R[2], (table[1, 1] - table[1, 0] - 2 * dt * rates[1]) / (2 * dt))
     np.testing.assert_array_equal(YT[3], table[1, 2])
-    np.testing.assert_array_equal(Y0[0], table[0, 0])
+    np.testing.assert_allclose(BASE[0], table[0, 0] + 2 * dt * rates[0])
 
 
 def test_answer_routes_rejected_queries_to_the_solver(monkeypatch):
@@ -76,10 +79,11 @@ def test_answer_routes_rejected_queries_to_the_solver(monkeypatch):
     steps = [4, 7, 4, 7]
     calls = []
 
-    def fake_solve(ms, st, **kw):
+    def fake_solve(ms, st, rate0=False, **kw):
         calls.append((len(ms), tuple(st)))
         if st == [0]:
-            return np.zeros((len(ms), 1, 14))
+            assert rate0
+            return np.zeros((len(ms), 1, 14)), np.zeros((len(ms), 14))
         return np.full((len(ms), 1, 14), 100.0 + st[0])
 
     class FakeNet:
