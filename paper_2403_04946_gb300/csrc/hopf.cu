@@ -75,6 +75,7 @@ struct hopf_ctx {
   // operator tables
   cplx* d_coef = nullptr;             // kNumOps ops x 3 x n
   unsigned char* d_blocks = nullptr;  // 3 site kinds x 36
+  unsigned long long op_forms = 0;    // hk::OpTable::forms of d_coef (0: apply untiled)
   double* d_agrid = nullptr;          // n
   std::vector<double> agrid;
   // cooperative-kernel workspace
@@ -257,6 +258,24 @@ inline void dfree(void* p) { hk::dev_free(p); }
 // slot 0 with zero row and column for A, D, S (and so for P, Q, Z).
 hopf_status build_ops_cdf(hopf_ctx* ctx);
 
+// hk::OpTable::forms of a coefficient table of three-point operators.
+unsigned long long op_forms(const std::vector<cplx>& coef, int n) {
+  unsigned long long f = 1ull << 63;
+  for (int op = 0; op < hk::kNumOps; ++op) {
+    unsigned b = 0;
+    bool ident = true;
+    for (int w = 0; w < 3; ++w)
+      for (int i = 0; i < n; ++i) {
+        const cplx c = coef[(size_t)op * 3 * n + (size_t)w * n + i];
+        if (c.x != 0.0) b |= 1u << (2 * w);
+        if (c.y != 0.0) b |= 2u << (2 * w);
+        if (c.y != 0.0 || c.x != (w == 1 ? 1.0 : 0.0)) ident = false;
+      }
+    f |= (unsigned long long)(ident ? 0x40u : b) << (8 * op);
+  }
+  return f;
+}
+
 hopf_status build_ops(hopf_ctx* ctx) {
   if (ctx->equation == HOPF_EQ_CDF) return build_ops_cdf(ctx);
   const int n = ctx->p.n, d = ctx->p.d;
@@ -293,6 +312,7 @@ hopf_status build_ops(hopf_ctx* ctx) {
     set(hk::OP_Z, 0, i, cplx{-2.0 * e * a * dlo, 0.0});
     set(hk::OP_Z, 2, i, cplx{-2.0 * e * a * dup, 0.0});
   }
+  ctx->op_forms = op_forms(coef, n);  // the Phi equation's operators are all three-point
   CK(cudaMemcpyAsync(ctx->d_coef, coef.data(), coef.size() * sizeof(cplx), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_agrid, ctx->agrid.data(), n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -314,6 +334,7 @@ hopf_status build_ops_cdf(hopf_ctx* ctx) {
   const double h = 2.0 * M_PI / d;
   ctx->agrid.assign(n, 0.0);
   for (int k = 0; k < n; ++k) ctx->agrid[k] = -U + k * du;
+  ctx->op_forms = 0;  // K integrates along the grid: the untiled apply
   std::vector<cplx> coef((size_t)hk::kNumOps * 3 * n, cplx{0.0, 0.0});
   auto set = [&](int op, int which, int i, double v) { coef[(size_t)op * 3 * n + (size_t)which * n + i] = cplx{v, 0.0}; };
   const double c = ctx->p.nonlinear ? 1.0 / (2.0 * h) : 0.0;
@@ -962,7 +983,7 @@ hopf_status orth_sweep_apply(hopf_ctx* ctx, const hopf_tt* X, std::vector<int>& 
   RoundWs& w = ctx->rw;
   const int d = X->d, n = X->n;
   const std::vector<int>& r = X->ranks;
-  const hk::OpTable ops{ctx->d_coef, n};
+  const hk::OpTable ops{ctx->d_coef, n, ctx->op_forms};
   p.assign(d + 1, 1);
   nbv.assign(d, 32);
   {

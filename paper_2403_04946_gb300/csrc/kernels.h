@@ -155,6 +155,11 @@ struct OpTable {
   // I, A, P, Q, Z, K (index op*3*n + {0,n,2n} + i), complex (op_apply).
   cplx* coef;
   int n;
+  // Per slot (8 bits at 8 * op): which coefficient parts are nonzero
+  // anywhere (bits 0-5: lo re, lo im, di re, di im, up re, up im), bit 6 the
+  // identity.  Bit 63 set: the table holds only such three-point operators
+  // and the tiled apply may use these forms; 0: not computed.
+  unsigned long long forms = 0;
 };
 enum { OP_I = 0, OP_A = 1, OP_P = 2, OP_Q = 3, OP_Z = 4, OP_K = 5, OP_NONE = 7 };
 constexpr int kNumOps = 6;  // slots of the coefficient table

@@ -270,40 +270,37 @@ struct SplitView {
   int tri_mode, tri;
 };
 
-DV cplx view_at(const SplitView& v, int r, int k) {
-  if (v.tri_mode == 1 && r > k + v.tri) return mk(0, 0);
-  if (v.tri_mode == 2) {
-    // reflector s = r (rows of the view are reflector indices), entry i = k:
-    // zero above the unit diagonal k < r + tri, one on it
-    if (k < r + v.tri) return mk(0, 0);
-    if (k == r + v.tri) return mk(1, 0);
-  }
-  if (v.tri_mode == 3) {
-    // same reflector block, view with rows = entry index i, columns = s
-    if (r < k + v.tri) return mk(0, 0);
-    if (r == k + v.tri) return mk(1, 0);
-  }
-  cplx x = v.X[(long long)r * v.rs + (long long)k * v.ks];
-  if (v.conj) x.y = -x.y;
-  return x;
+// What the view holds at an in-range (r, k): 0 the stored value, 1 zero
+// (outside the triangle), 2 one (the unit diagonal of a reflector block).
+DV int view_kind(const SplitView& v, int r, int k) {
+  if (v.tri_mode == 1) return r > k + v.tri ? 1 : 0;
+  // reflector s = r (rows of the view are reflector indices), entry i = k:
+  // zero above the unit diagonal k < r + tri, one on it
+  if (v.tri_mode == 2) return k < r + v.tri ? 1 : (k == r + v.tri ? 2 : 0);
+  // same reflector block, view with rows = entry index i, columns = s
+  if (v.tri_mode == 3) return r < k + v.tri ? 1 : (r == k + v.tri ? 2 : 0);
+  return 0;
 }
 
-DV void comps(cplx x, double (&c)[3]) {
-  c[0] = x.x;
-  c[1] = x.y;
-  c[2] = x.x + x.y;
-}
-
-// Splitting, one CTA per (32 rows, K-chunk): pass 1 finds each row's
-// per-component exponent e (max |x| 2^-e < 1) over the chunk, pass 2 cuts
-// the digits.  Each 32 x 64 slab of the operand goes through shared memory,
-// read along whichever index is contiguous in memory and written as 64
-// consecutive BF16 digits per row and plane.  No FP64 arithmetic beyond one
-// addition (re + im): the magnitudes are compared as integers and the digits
-// cut from the IEEE bit pattern (on this GPU the FP64 pipe retires two
-// multiply-adds per clock per SM).
-constexpr int kSplitRows = 32;
+// Splitting, one CTA per (16 rows, K-chunk): the chunk (16 x at most 192
+// values, 48 KB) is staged once into shared memory by cp.async along
+// whichever index is contiguous in memory (entries outside the view's
+// triangle are written as their constants instead of read); pass 1 finds
+// each row's per-component exponent e (max |x| 2^-e < 1) over the chunk,
+// pass 2 cuts the digits, written as consecutive BF16 digits per row and
+// plane.  Four CTAs per SM keep about 190 KB of loads in flight.  No FP64
+// arithmetic beyond one addition (re + im): the magnitudes are compared as
+// integers and the digits cut from the IEEE bit pattern (on this GPU the
+// FP64 pipe retires two multiply-adds per clock per SM).
+constexpr int kSplitRows = 16;
 constexpr int kSplitThreads = 256;
+constexpr int kSplitLd = 3 * kSlab + 1;  // one K-chunk and a zero pad per shared-memory row
+size_t split_smem_bytes() { return (size_t)kSplitRows * kSplitLd * sizeof(cplx); }
+
+DV void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+DV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // |x| as an ordered integer key (the IEEE bits without the sign).
 DV long long mag_key(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll; }
@@ -370,83 +367,78 @@ DV void digit_pair(long long X0, long long X1, int S, unsigned int* dst, size_t 
   dst[0] = bf16_bits(y0) | (bf16_bits(y1) << 16);
 }
 
-DV void split_load(const SplitView& v, int r0, int k0, int k1, cplx (*tile)[kSlab + 1]) {
-  if (v.rs == 1 && v.ks != 1) {  // rows contiguous: consecutive threads along r
-    for (int idx = threadIdx.x; idx < kSplitRows * kSlab; idx += kSplitThreads) {
-      const int r = idx % kSplitRows, k = idx / kSplitRows;
-      tile[r][k] = (r0 + r < v.R && k0 + k < k1) ? view_at(v, r0 + r, k0 + k) : mk(0, 0);
-    }
-  } else {  // K contiguous (or neither): consecutive threads along k
-    for (int idx = threadIdx.x; idx < kSplitRows * kSlab; idx += kSplitThreads) {
-      const int k = idx % kSlab, r = idx / kSlab;
-      tile[r][k] = (r0 + r < v.R && k0 + k < k1) ? view_at(v, r0 + r, k0 + k) : mk(0, 0);
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kSplitThreads)
     split_kernel(SplitView v, int Kc, int nchunks, int S, int* e, __nv_bfloat16* planes, long long ldk) {
-  __shared__ cplx tile[kSplitRows][kSlab + 1];
-  __shared__ long long mx[3][kSplitThreads / kSplitRows][kSplitRows];
+  extern __shared__ cplx tile[];  // [kSplitRows][kSplitLd]
   __shared__ int esh[3][kSplitRows];
   const int r0 = blockIdx.x * kSplitRows, z = blockIdx.y;
-  const int kb = z * Kc, ke = min(v.K, kb + Kc);
+  const int kb = z * Kc, klen = min(v.K - kb, Kc);
   const int tid = threadIdx.x;
-  // pass 1: largest magnitude per row and component
-  const int pr = tid % kSplitRows, pg = tid / kSplitRows;
-  long long k0m = 0, k1m = 0, k2m = 0;
-  for (int k0 = kb; k0 < ke; k0 += kSlab) {
-    split_load(v, r0, k0, ke, tile);
-    __syncthreads();
-    for (int k = pg; k < kSlab; k += kSplitThreads / kSplitRows) {
-      const cplx x = tile[pr][k];
-      k0m = max(k0m, mag_key(x.x));
-      k1m = max(k1m, mag_key(x.y));
-      k2m = max(k2m, mag_key(x.x + x.y));
+  const int nval = kSplitRows * klen;
+  const bool rows_contiguous = v.rs == 1 && v.ks != 1;
+  for (int idx = tid; idx < nval; idx += kSplitThreads) {
+    int r, k;
+    if (rows_contiguous) {
+      r = idx % kSplitRows;
+      k = idx / kSplitRows;
+    } else {
+      k = idx % klen;
+      r = idx / klen;
     }
-    __syncthreads();
+    cplx* dst = tile + r * kSplitLd + k;
+    const int kind = (r0 + r < v.R) ? view_kind(v, r0 + r, kb + k) : 1;
+    if (kind == 0) cp_async16(dst, v.X + (long long)(r0 + r) * v.rs + (long long)(kb + k) * v.ks);
+    else *dst = mk(kind == 2 ? 1.0 : 0.0, 0.0);
   }
-  mx[0][pg][pr] = k0m;
-  mx[1][pg][pr] = k1m;
-  mx[2][pg][pr] = k2m;
+  if ((klen & 1) && tid < kSplitRows) tile[tid * kSplitLd + klen] = mk(0, 0);  // second value of the last pair
+  cp_async_wait_all();
   __syncthreads();
-  if (tid < 3 * kSplitRows) {
-    const int q = tid / kSplitRows, r = tid % kSplitRows;
-    long long g = 0;
-    for (int j = 0; j < kSplitThreads / kSplitRows; ++j) g = max(g, mx[q][j][r]);
-    const int ex = key_exponent(g);
-    esh[q][r] = ex;
-    if (r0 + r < v.R) e[((size_t)q * nchunks + z) * v.R + r0 + r] = ex;
+  const double sgn = v.conj ? -1.0 : 1.0;
+  // pass 1: largest magnitude per row and component, a half-warp per row
+  {
+    const int r = tid >> 4, j = tid & 15;
+    long long k0m = 0, k1m = 0, k2m = 0;
+    for (int k = j; k < klen; k += 16) {
+      const cplx x = tile[r * kSplitLd + k];
+      const double im = sgn * x.y;
+      k0m = max(k0m, mag_key(x.x));
+      k1m = max(k1m, mag_key(im));
+      k2m = max(k2m, mag_key(x.x + im));
+    }
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+      k0m = max(k0m, __shfl_xor_sync(0xffffffffu, k0m, o));
+      k1m = max(k1m, __shfl_xor_sync(0xffffffffu, k1m, o));
+      k2m = max(k2m, __shfl_xor_sync(0xffffffffu, k2m, o));
+    }
+    if (j < 3) {
+      const int ex = key_exponent(j == 0 ? k0m : (j == 1 ? k1m : k2m));
+      esh[j][r] = ex;
+      if (r0 + r < v.R) e[((size_t)j * nchunks + z) * v.R + r0 + r] = ex;
+    }
   }
   __syncthreads();
   // pass 2: balanced base-256 digits of round(x 2^(8S-1)), |x| = |v| 2^-e < 1:
   // x ~ sum_j q_j 2^(-7-8j) with |q_j| <= 128.  Each thread cuts two
   // consecutive K-values of a row and stores each digit pair as one 32-bit
-  // word (K-chunks and slabs start at even K, ldk is even).
+  // word (K-chunks start at even K, ldk is even).
   const size_t plane = (size_t)v.R * ldk;
   const int nbits = 8 * S - 1;
-  const int kp = tid % (kSlab / 2), rg = tid / (kSlab / 2);
-  constexpr int kRowStep = kSplitThreads / (kSlab / 2);
-  for (int k0 = kb; k0 < ke; k0 += kSlab) {
-    split_load(v, r0, k0, ke, tile);
-    __syncthreads();
-    const int kk = 2 * kp;
-    if (k0 + kk < ke)
-      for (int r = rg; r < kSplitRows; r += kRowStep) {
-        if (r0 + r >= v.R) break;
-        // the second value of the pair is zero beyond ke (the loader's fill)
-        const cplx x0 = tile[r][kk], x1 = tile[r][kk + 1];
-        const double c0[3] = {x0.x, x0.y, x0.x + x0.y};
-        const double c1[3] = {x1.x, x1.y, x1.x + x1.y};
-        unsigned int* dst = reinterpret_cast<unsigned int*>(planes + (size_t)(r0 + r) * ldk + k0 + kk);
+  const int nph = (klen + 1) >> 1;
+  for (int pi = tid; pi < kSplitRows * nph; pi += kSplitThreads) {
+    const int r = pi / nph, kk = 2 * (pi - r * nph);
+    if (r0 + r >= v.R) break;
+    const cplx x0 = tile[r * kSplitLd + kk], x1 = tile[r * kSplitLd + kk + 1];
+    const double i0 = sgn * x0.y, i1 = sgn * x1.y;
+    const double c0[3] = {x0.x, i0, x0.x + i0};
+    const double c1[3] = {x1.x, i1, x1.x + i1};
+    unsigned int* dst = reinterpret_cast<unsigned int*>(planes + (size_t)(r0 + r) * ldk + kb + kk);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int e = esh[q][r];
-          digit_pair(fixed_point(c0[q], e, nbits), fixed_point(c1[q], e, nbits), S, dst + (size_t)(q * S) * (plane / 2),
-                     plane / 2);
-        }
-      }
-    __syncthreads();
+    for (int q = 0; q < 3; ++q) {
+      const int ex = esh[q][r];
+      digit_pair(fixed_point(c0[q], ex, nbits), fixed_point(c1[q], ex, nbits), S, dst + (size_t)(q * S) * (plane / 2),
+                 plane / 2);
+    }
   }
 }
 
@@ -494,7 +486,9 @@ cudaError_t tc_split(const TcOperandView& ov, int S, TcOperand* out, void* buf, 
   out->nchunks = nchunks;
   SplitView v{ov.X, ov.rs, ov.ks, ov.R, ov.K, ov.conj, ov.tri_mode, ov.tri};
   const dim3 grid((ov.R + kSplitRows - 1) / kSplitRows, nchunks);
-  split_kernel<<<grid, kSplitThreads, 0, s>>>(v, Kc, nchunks, S, out->e, reinterpret_cast<__nv_bfloat16*>(buf), ldk);
+  cudaError_t e = allow_smem((const void*)split_kernel, split_smem_bytes());
+  if (e != cudaSuccess) return e;
+  split_kernel<<<grid, kSplitThreads, split_smem_bytes(), s>>>(v, Kc, nchunks, S, out->e, reinterpret_cast<__nv_bfloat16*>(buf), ldk);
   return cudaGetLastError();
 }
 

@@ -674,11 +674,119 @@ __global__ void stencil_combine_kernel(const cplx* __restrict__ T, int r, int n,
   }
 }
 
+// Tiled form of the same sum for the conj-transposed layout (mode 1) and
+// three-point operators.  One CTA per (q, 32 left-rank indices i, 16 grid
+// points m): the T_beta[i, m - 1 .. m + 16, q] rows of every beta are staged
+// in shared memory by cp.async (zero beyond the grid's edges), each thread
+// forms all Al outputs of one (i, m) from the three taps of every beta with
+// only the coefficient parts that are nonzero (the identity is an addition,
+// a real diagonal two multiply-adds), and a warp writes 16 consecutive m of
+// two output rows: 256-byte segments of the H^H layout.
+constexpr int kStTM = 16;
+constexpr int kStTI = 32;
+constexpr int kStThreads = 256;
+constexpr int kStLd = kStTI + 1;  // odd row stride: conflict-free reads along m
+
+size_t stencil_tile_smem(int Bn) { return (size_t)Bn * (kStTM + 2) * kStLd * sizeof(cplx); }
+
+DV void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// acc += (op x)[m] from the taps xl = x[m-1], x0 = x[m], xu = x[m+1]
+// (zero beyond the edges), using the parts of the coefficients that f marks.
+DV void op_acc(const cplx* __restrict__ cf, int n, int m, unsigned f, const cplx& xl, const cplx& x0,
+               const cplx& xu, cplx& acc) {
+  if (f & 0x40) {
+    acc.x += x0.x;
+    acc.y += x0.y;
+    return;
+  }
+  if (f & 0x03) {
+    const cplx c = cf[m];
+    if (f & 0x01) { acc.x = fma(c.x, xl.x, acc.x); acc.y = fma(c.x, xl.y, acc.y); }
+    if (f & 0x02) { acc.x = fma(-c.y, xl.y, acc.x); acc.y = fma(c.y, xl.x, acc.y); }
+  }
+  if (f & 0x0C) {
+    const cplx c = cf[n + m];
+    if (f & 0x04) { acc.x = fma(c.x, x0.x, acc.x); acc.y = fma(c.x, x0.y, acc.y); }
+    if (f & 0x08) { acc.x = fma(-c.y, x0.y, acc.x); acc.y = fma(c.y, x0.x, acc.y); }
+  }
+  if (f & 0x30) {
+    const cplx c = cf[2 * n + m];
+    if (f & 0x10) { acc.x = fma(c.x, xu.x, acc.x); acc.y = fma(c.x, xu.y, acc.y); }
+    if (f & 0x20) { acc.x = fma(-c.y, xu.y, acc.x); acc.y = fma(c.y, xu.x, acc.y); }
+  }
+}
+
+__global__ void __launch_bounds__(kStThreads, 3)
+    stencil_tile_kernel(const cplx* __restrict__ T, int r, int n, int p, int Bn, int Al, int Ar,
+                        const unsigned char* __restrict__ blocks, const cplx* __restrict__ coef,
+                        unsigned long long forms, cplx* __restrict__ out, int ldo) {
+  extern __shared__ cplx xs[];  // [Bn][kStTM + 2][kStLd]: T_beta[i0 + i, m0 - 1 + mm, q]
+  __shared__ unsigned char blk[36];
+  constexpr int rows = kStTM + 2;
+  const int mt = (n + kStTM - 1) / kStTM, it = (r + kStTI - 1) / kStTI;
+  int b = blockIdx.x;
+  const int m0 = (b % mt) * kStTM;
+  b /= mt;
+  const int i0 = (b % it) * kStTI;
+  const int q = b / it;
+  const int ti = min(kStTI, r - i0);
+  const size_t bstride = (size_t)r * n * p;
+  if (threadIdx.x < Al * Ar) blk[threadIdx.x] = blocks[threadIdx.x];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int row = w; row < Bn * rows; row += kStThreads / 32) {
+    const int be = row / rows, mm = row - be * rows;
+    const int m = m0 - 1 + mm;
+    if (lane < ti) {
+      cplx* dst = xs + row * kStLd + lane;
+      if (m >= 0 && m < n) cp_async16(dst, T + bstride * be + (size_t)(i0 + lane) + (size_t)r * ((size_t)m + (size_t)n * q));
+      else *dst = mk(0, 0);
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int mi = lane & 15, m = m0 + mi;
+  if (m >= n) return;
+  const size_t col = (size_t)m + (size_t)n * q;
+  for (int i = 2 * w + (lane >> 4); i < ti; i += kStThreads / 16) {
+    cplx acc[6];
+#pragma unroll
+    for (int al = 0; al < 6; ++al) acc[al] = mk(0, 0);
+    for (int be = 0; be < Bn; ++be) {
+      const cplx* x = xs + (be * rows + mi) * kStLd + i;  // row mi holds m - 1
+      const cplx xl = x[0], x0 = x[kStLd], xu = x[2 * kStLd];
+#pragma unroll
+      for (int al = 0; al < 6; ++al) {
+        if (al < Al) {
+          const int op = blk[al * Ar + be];
+          if (op != OP_NONE)
+            op_acc(coef + (size_t)op * 3 * n, n, m, (unsigned)(forms >> (8 * op)) & 0xFFu, xl, x0, xu, acc[al]);
+        }
+      }
+    }
+#pragma unroll
+    for (int al = 0; al < 6; ++al)
+      if (al < Al) out[col + (size_t)ldo * (size_t)(al * r + i0 + i)] = cconj(acc[al]);
+  }
+}
+
 cudaError_t stencil_combine(const cplx* T, int r, int n, int p, int Bn, int Al, int Ar,
                             const unsigned char* blocks_dev, const OpTable& ops, cplx* out,
                             int mode, int ldo, cudaStream_t s) {
   const size_t total = (size_t)Al * r * n * p;
   if (total == 0) return cudaSuccess;
+  if (mode == 1 && (ops.forms >> 63) && Bn <= 6 && Al <= 6 && Al * Ar <= 36) {
+    const size_t smem = stencil_tile_smem(Bn);
+    cudaError_t e = allow_smem((const void*)stencil_tile_kernel, smem);
+    if (e != cudaSuccess) return e;
+    const size_t tiles = (size_t)((n + kStTM - 1) / kStTM) * ((r + kStTI - 1) / kStTI) * p;
+    stencil_tile_kernel<<<(unsigned)tiles, kStThreads, smem, s>>>(T, r, n, p, Bn, Al, Ar, blocks_dev, ops.coef,
+                                                                   ops.forms, out, ldo);
+    return cudaGetLastError();
+  }
   const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
   stencil_combine_kernel<<<grid, 256, 0, s>>>(T, r, n, p, Bn, Al, Ar, blocks_dev, ops.coef, out,
                                               mode, ldo);
