@@ -542,6 +542,21 @@ void reset_barrier(hopf_ctx* ctx) {
   cudaMemcpyAsync(ctx->coop.bar, &hb, sizeof hb, cudaMemcpyHostToDevice, ctx->stream);
 }
 
+// read_small and check_barrier with one synchronisation: the barrier record
+// comes back in the last four ints of the pinned int buffer.
+static_assert(sizeof(GridBar) == 4 * sizeof(int), "barrier record size");
+hopf_status read_small_checked(hopf_ctx* ctx, int nint, int ndbl) {
+  CK(cudaMemcpyAsync(ctx->h_int + 12, ctx->coop.bar, sizeof(GridBar), cudaMemcpyDeviceToHost, ctx->stream));
+  TRY(read_small(ctx, nint, ndbl));
+  GridBar hb;
+  std::memcpy(&hb, ctx->h_int + 12, sizeof hb);
+  if (hb.err) {
+    reset_barrier(ctx);
+    return fail(ctx, HOPF_ETIMEOUT, "a grid barrier wait expired");
+  }
+  return HOPF_OK;
+}
+
 hopf_status check_barrier(hopf_ctx* ctx) {
   GridBar hb;
   CK(cudaMemcpyAsync(&hb, ctx->coop.bar, sizeof(GridBar), cudaMemcpyDeviceToHost, ctx->stream));
@@ -829,8 +844,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
                    double tol, int cap, const int* forced, double* disc_out, bool* capped) {
   const int d = t->d, n = t->n;
   RoundWs& w = ctx->rw;
-  TRY(read_small(ctx, 0, 1));
-  TRY(check_barrier(ctx));
+  TRY(read_small_checked(ctx, 0, 1));
   const double nrm2 = ctx->h_dbl[0];
   if (!std::isfinite(nrm2)) return fail(ctx, HOPF_ENUMERIC, "non-finite norm in rounding");
   const double eps_hat = tol * std::sqrt(nrm2) / std::sqrt((double)(d - 1));
@@ -882,8 +896,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
       LAUNCH(HOPF_K_SVD, gebrd_flops(pp), 0, 1, hk::gebrd(w.Mb, pp, pp, w.bd_d, w.bd_e, w.bd_tauq, w.bd_taup, ctx->coop, ctx->stream, w.bd_rows));
       LAUNCH(HOPF_K_SVD, 0, 0, 2, hk::bd_sigma(w.bd_d, w.bd_e, pp, w.bd_a2, w.bd_info, w.sig, ctx->stream));
       LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::bd_rank(w.sig, pp, ctx->d_dbl + 1, cap, forced_c, ctx->d_int, ctx->d_dbl + 2, w.sig + pp, ctx->stream));
-      TRY(read_small(ctx, 3, 5));
-      TRY(check_barrier(ctx));
+      TRY(read_small_checked(ctx, 3, 5));
       ctx->prof.svd_count += 1;
     }
     // Jacobi leaves out pairs far below the truncation tolerance (theta);
@@ -903,8 +916,7 @@ hopf_status phase2(hopf_ctx* ctx, hopf_tt* t, const std::vector<int>& p, const s
         LAUNCH(HOPF_K_SMALL, 0, 0, 1, hk::rank_select(w.Mb, cols, cols, pp, ctx->d_dbl + 1, cap, forced_c, w.sig, w.perm, ctx->d_int, ctx->d_dbl + 2, ctx->stream));
       }
       CK(cudaMemcpyAsync(ctx->d_int + 2, ctx->coop.counters + 63, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
-      TRY(read_small(ctx, 3, 5));
-      TRY(check_barrier(ctx));
+      TRY(read_small_checked(ctx, 3, 5));
       if (ctx->h_int[2] < 0) return fail(ctx, HOPF_ENUMERIC, "Jacobi SVD did not converge at bond %d", c + 1);
       ctx->prof.svd_count += 1;
       ctx->prof.svd_sweeps += ctx->h_int[2];
@@ -1780,8 +1792,7 @@ hopf_status tt_norm(hopf_ctx* ctx, const hopf_tt* t, double* norm) {
   TRY(round_reserve(ctx, t));
   std::vector<int> p, nbv;
   TRY(orth_sweep(ctx, t, p, nbv));
-  TRY(read_small(ctx, 0, 1));
-  TRY(check_barrier(ctx));
+  TRY(read_small_checked(ctx, 0, 1));
   *norm = std::sqrt(ctx->h_dbl[0]);
   return HOPF_OK;
 }
