@@ -308,11 +308,14 @@ size_t gebrd_rows_elems(int n, int sms) {
   return (size_t)(n + G) * (size_t)n;
 }
 
+size_t bd_vectors_smem(int n);
+
 bool gebrd_fits(int n, const CoopWs& ws, bool have_rows_ws) {
   int nloc;
   size_t smem;
   bool glob;
-  return n >= 1 && gebrd_grid(n, coop_sms(ws), &nloc, &smem, have_rows_ws, &glob) > 0;
+  return n >= 1 && gebrd_grid(n, coop_sms(ws), &nloc, &smem, have_rows_ws, &glob) > 0 &&
+         bd_vectors_smem(n) <= (size_t)dev_info().max_smem_optin;
 }
 
 cudaError_t gebrd(cplx* A, int lda, int n, double* d, double* e, cplx* tauq, cplx* taup,
@@ -543,45 +546,50 @@ DV double hash_unit(unsigned a, unsigned b) {
   return (double)(h & 0xFFFFFFu) * (1.0 / 16777216.0) - 0.5;
 }
 
-// Solver arrays of T_GK - lam I (length N each) in shared memory.
-enum { L_DINV = 0, L_DU = 1, L_DU2 = 2, L_DL = 3, L_PV = 4, L_B = 5 };
-constexpr int kSolveArrays = 6;
+// Solver arrays of T_GK - lam I (length N each) in shared memory, and the
+// scaled off-diagonals (staged once per launch).
+enum { L_DINV = 0, L_C1 = 1, L_C2 = 2, L_DL = 3, L_PV = 4, L_B = 5, L_OFF = 6 };
+constexpr int kSolveArrays = 7;
+size_t bd_vectors_smem(int n) { return sizeof(double) * kSolveArrays * 2 * (size_t)n; }
 
-// LU with partial pivoting of T_GK - lam I (scaled: off-diagonals a_k / amax);
-// one thread.  Row i of U holds (1 / pivot, super, second super).
-DV void gk_factor(const double* d, const double* e, int n, double inv, double lam, double* w) {
-  const int N = 2 * n;
+// LU with partial pivoting of T_GK - lam I (off-diagonals at L_OFF, scaled
+// by 1 / amax); one thread.  Row i of U is stored as (1 / pivot, super /
+// pivot, second super / pivot), so that the back substitution has one
+// dependent multiply-add per row, and the multiplier uses the reciprocal of
+// the pivot: one reciprocal and one multiply-add on the serial chain.
+DV void gk_factor(int N, double lam, double* w) {
   double* Dinv = w + L_DINV * N;
-  double* DU = w + L_DU * N;
-  double* DU2 = w + L_DU2 * N;
+  double* C1 = w + L_C1 * N;
+  double* C2 = w + L_C2 * N;
   double* DL = w + L_DL * N;
   double* PV = w + L_PV * N;
+  const double* off = w + L_OFF * N;
   const double tiny = 4.0 * DBL_EPSILON;
-  auto off = [&](int k) { return ((k & 1) ? e[k >> 1] : d[k >> 1]) * inv; };
   auto guard = [&](double p) { return fabs(p) < tiny ? (p < 0.0 ? -tiny : tiny) : p; };
-  double di = -lam, dui = (N > 1) ? off(0) : 0.0;
-  double sub = (N > 1) ? off(0) : 0.0;
+  double di = -lam, dui = (N > 1) ? off[0] : 0.0;
+  double sub = dui;
   for (int i = 0; i < N - 1; ++i) {
-    const double dn = -lam, un = (i + 1 < N - 1) ? off(i + 1) : 0.0;
+    const double un = (i + 1 < N - 1) ? off[i + 1] : 0.0;
     if (fabs(di) >= fabs(sub)) {
-      const double piv = guard(di);
-      const double f = sub / piv;
-      Dinv[i] = 1.0 / piv;
-      DU[i] = dui;
-      DU2[i] = 0.0;
+      const double rp = 1.0 / guard(di);
+      const double f = sub * rp;
+      Dinv[i] = rp;
+      C1[i] = dui * rp;
+      C2[i] = 0.0;
       DL[i] = f;
       PV[i] = 0.0;
-      di = dn - f * dui;
+      di = fma(-f, dui, -lam);
       dui = un;
     } else {
-      // rows i and i+1 swapped: new row i = (sub, dn, un)
-      const double f = di / sub;
-      Dinv[i] = 1.0 / sub;
-      DU[i] = dn;
-      DU2[i] = un;
+      // rows i and i+1 swapped: new row i = (sub, -lam, un)
+      const double rs = 1.0 / sub;
+      const double f = di * rs;
+      Dinv[i] = rs;
+      C1[i] = -lam * rs;
+      C2[i] = un * rs;
       DL[i] = f;
       PV[i] = 1.0;
-      di = dui - f * dn;
+      di = fma(f, lam, dui);
       dui = -f * un;
     }
     sub = un;  // the sub-diagonal of row i+2 equals the super-diagonal off(i+1)
@@ -592,8 +600,8 @@ DV void gk_factor(const double* d, const double* e, int n, double inv, double la
 // Solve with the factors, in place on B; one thread.
 DV void gk_solve(int N, double* w) {
   const double* Dinv = w + L_DINV * N;
-  const double* DU = w + L_DU * N;
-  const double* DU2 = w + L_DU2 * N;
+  const double* C1 = w + L_C1 * N;
+  const double* C2 = w + L_C2 * N;
   const double* DL = w + L_DL * N;
   const double* PV = w + L_PV * N;
   double* B = w + L_B * N;
@@ -602,16 +610,18 @@ DV void gk_solve(int N, double* w) {
     const double bn = B[i + 1], f = DL[i];
     if (PV[i] != 0.0) {
       B[i] = bn;
-      cur = cur - f * bn;
+      cur = fma(-f, bn, cur);
     } else {
       B[i] = cur;
-      cur = bn - f * cur;
+      cur = fma(-f, cur, bn);
     }
   }
   double x2 = 0.0, x1 = cur * Dinv[N - 1];
   B[N - 1] = x1;
   for (int i = N - 2; i >= 0; --i) {
-    const double x = (B[i] - DU[i] * x1 - DU2[i] * x2) * Dinv[i];
+    // x2 is known one row earlier than x1: only the last multiply-add waits on x1
+    const double t = fma(-C2[i], x2, B[i] * Dinv[i]);
+    const double x = fma(-C1[i], x1, t);
     B[i] = x;
     x2 = x1;
     x1 = x;
@@ -639,8 +649,11 @@ __global__ void bd_vectors_kernel(const double* __restrict__ d, const double* __
   while (k1 < nvec && sig[k1 - 1] - sig[k1] < gap_tol) ++k1;
   const double inv = 1.0 / amax;
   double* B = vsm + L_B * N;
+  double* off = vsm + L_OFF * N;
+  for (int i = lane; i < N - 1; i += 32) off[i] = ((i & 1) ? e[i >> 1] : d[i >> 1]) * inv;
+  __syncwarp();
   for (int k = k0; k < k1; ++k) {
-    if (lane == 0) gk_factor(d, e, n, inv, sig[k] * inv, vsm);
+    if (lane == 0) gk_factor(N, sig[k] * inv, vsm);
     for (int i = lane; i < N; i += 32) B[i] = 1.0 + 0.25 * hash_unit((unsigned)i, (unsigned)k);
     __syncwarp();
     for (int it = 0; it < 3; ++it) {
@@ -716,7 +729,7 @@ cudaError_t bd_vectors(const double* d, const double* e, int n, const double* in
                        int kt, int nvec, double* X, int ldx, double* Zs, cudaStream_t s) {
   if (nvec <= 0) return cudaSuccess;
   if (kt > 0) {
-    const size_t smem = sizeof(double) * kSolveArrays * 2 * (size_t)n;
+    const size_t smem = bd_vectors_smem(n);
     cudaError_t err = allow_smem((const void*)bd_vectors_kernel, smem);
     if (err != cudaSuccess) return err;
     bd_vectors_kernel<<<kt, 32, smem, s>>>(d, e, n, info, sig, kt, X, ldx, Zs);

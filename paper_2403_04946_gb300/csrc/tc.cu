@@ -61,7 +61,6 @@ __host__ __device__ constexpr int b_plane_bytes() { return kTcN * kSlab * 2; }  
 __host__ __device__ int stage_bytes(int S) { return S * (a_plane_bytes() + b_plane_bytes()); }
 size_t tc_smem_bytes(int S) { return (size_t)kStages * stage_bytes(S) + 1024; }
 
-constexpr uint32_t kIdesc = umma_idesc_bf16(kTcM, kTcN);
 
 
 struct TcArgs {
@@ -81,6 +80,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], acc_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ int eb_sh[3][kTcN];
   // 1024-byte aligned stage ring (the swizzle atoms need it)
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -151,18 +151,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         const int c = st % 3, slab = st / 3;
         const uint32_t abase = smem_u32(smem + (size_t)slot * sbytes);
-        const uint32_t bbase = abase + (uint32_t)(S * a_plane_bytes());
-        for (int L = 0; L < S; ++L) {
-          const uint32_t acc = tmem + (uint32_t)((c * S + L) * kTcN);
-          for (int i = 0; i <= L; ++i) {
-            const int j = L - i;
+        const uint64_t a0 = sw128_desc(abase), b0 = sw128_desc(abase + (uint32_t)(S * a_plane_bytes()));
+        // A digit plane i against B planes 0 .. S-1-i in one product: the B
+        // planes lie one after another (32 rows each), so together they are
+        // one (S - i) x 32-row operand whose output columns are the level
+        // accumulators L = i .. S-1, contiguous in tensor memory.  The
+        // descriptors advance by adding the offset / 16 to their address
+        // field (shared-memory addresses stay below 2^18).
+        for (int i = 0; i < S; ++i) {
+          const uint32_t acc = tmem + (uint32_t)((c * S + i) * kTcN);
+          const uint32_t idesc = umma_idesc_bf16(kTcM, kTcN * (S - i));
 #pragma unroll
-            for (int kk = 0; kk < kSlab / 16; ++kk) {
-              const uint64_t ad = sw128_desc(abase + (uint32_t)(i * a_plane_bytes() + kk * 32));
-              const uint64_t bd = sw128_desc(bbase + (uint32_t)(j * b_plane_bytes() + kk * 32));
-              umma(acc, ad, bd, kIdesc, (slab > 0 || i > 0 || kk > 0) ? 1u : 0u);
-            }
-          }
+          for (int kk = 0; kk < kSlab / 16; ++kk)
+            umma(acc, a0 + (uint64_t)((i * a_plane_bytes() + kk * 32) >> 4), b0 + (uint64_t)(kk * 2), idesc,
+                 (slab > 0 || i > 0 || kk > 0) ? 1u : 0u);
         }
         umma_commit(&empty_bar[slot]);  // the stage is free once these MMAs have read it
       }
@@ -177,14 +179,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // the FP64 pipe is 1/64 of the FP32 one).
     const int m = m0 + 32 * warp + lane;
     cplx* out = a.out + (size_t)z * a.zstride;
-    // the values an accumulating product adds to, 16 columns at a time,
-    // loaded ahead (independent loads in flight together): the first half
-    // while the MMAs run, the second before its accumulators are read
-    cplx pre[16];
+    // the tile's column exponents of B, staged while the MMAs run (named
+    // barrier 1: the four epilogue warps only)
+    {
+      const int t = threadIdx.x;
+      if (t < 3 * kTcN) {
+        const int c = t / kTcN, n = n0 + t % kTcN;
+        eb_sh[c][t % kTcN] = (n < a.N) ? a.eB[(size_t)c * a.nchunks * a.N + (size_t)z * a.N + n] : 0;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+    // the values an accumulating product adds to, 8 columns at a time,
+    // loaded ahead (independent loads in flight together): the first
+    // quarter while the MMAs run, each next one before its accumulators are
+    // read
+    cplx pre[8];
     auto prefetch = [&](int h) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int n = n0 + 16 * h + q;
+      for (int q = 0; q < 8; ++q) {
+        const int n = n0 + 8 * h + q;
         pre[q] = (a.accumulate && m < a.M && n < a.N) ? out[m + (size_t)a.ldo * n] : mk(0, 0);
       }
     };
@@ -192,42 +205,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const bool ok = mbar_wait(&acc_bar, 0, vabort, a.err);
     tc_fence_after();
     if (ok && !*vabort) {
-      const int* eA = a.eA + (size_t)z * a.M;
-      const int* eB = a.eB + (size_t)z * a.N;
-      const size_t eAs = (size_t)a.nchunks * a.M, eBs = (size_t)a.nchunks * a.N;
+      const size_t eAs = (size_t)a.nchunks * a.M;
       int ea[3] = {0, 0, 0};
       if (m < a.M)
-        for (int c = 0; c < 3; ++c) ea[c] = eA[c * eAs + m];
+        for (int c = 0; c < 3; ++c) ea[c] = a.eA[c * eAs + (size_t)z * a.M + m];
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll 1
-      for (int h = 0; h < kTcN / 16; ++h) {
+      for (int h = 0; h < kTcN / 8; ++h) {
         if (h > 0) prefetch(h);
-        float th[3][16], tl[3][16];
+        float th[3][8], tl[3][8];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-#pragma unroll 1
-          for (int L = 0; L < S; ++L) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((c * S + L) * kTcN + 16 * h), v);
+          // all five level accumulators of product c (levels >= S are not
+          // written by the MMAs and are skipped)
+          float v[kMaxDigits][8];
+          tmem_ld_levels8(lane_base + (uint32_t)(c * S * kTcN + 8 * h), v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            th[c][q] = v[0][q] * pow2f(-14);  // exact: an integer below 2^24 times a power of two
+            tl[c][q] = 0.f;
+          }
+#pragma unroll
+          for (int L = 1; L < kMaxDigits; ++L) {
+            if (L >= S) break;
             const float w = pow2f(-14 - 8 * L);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const float x = v[q] * w;  // exact: an integer below 2^24 times a power of two
-              if (L == 0) {
-                th[c][q] = x;
-                tl[c][q] = 0.f;
-              } else {
-                df_add_part(th[c][q], tl[c][q], x, 0.f);
-              }
-            }
+            for (int q = 0; q < 8; ++q) df_add_part(th[c][q], tl[c][q], v[L][q] * w, 0.f);
           }
         }
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int n = n0 + 16 * h + q;
+        for (int q = 0; q < 8; ++q) {
+          const int n = n0 + 8 * h + q;
           if (m >= a.M || n >= a.N) continue;
           int ex[3];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) ex[c] = ea[c] + eB[c * eBs + n];
+          for (int c = 0; c < 3; ++c) ex[c] = ea[c] + eb_sh[c][8 * h + q];
           const int E0 = max(ex[0], max(ex[1], ex[2]));
           // component values relative to 2^E0 (factors <= 1: exact scaling,
           // or below the double-float precision of the largest one)
