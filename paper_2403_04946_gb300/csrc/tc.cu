@@ -19,14 +19,16 @@
 //     C = (T1 - T2) + i (T3 - T1 - T2),
 // each of Ar, Ai, Ar + Ai (and the same for B) split with its own scales.
 //
-// The product kernel: one CTA per 128 x 32 output tile and K-chunk.  Warp 4
+// The product kernel: one CTA per 128 x 32 output tile and K-chunk.  Warp 8
 // streams digit slabs (64 K-values, 128 B per row, 128-byte swizzle) into a
-// two-stage shared-memory ring with TMA (cp.async.bulk.tensor); warp 5 issues
+// two-stage shared-memory ring with TMA (cp.async.bulk.tensor); warp 9 issues
 // tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) into 15 accumulators
-// (3 products x 5 levels x 32 columns) in tensor memory; warps 0-3 read the
-// accumulators back (tcgen05.ld), combine levels, scales and the 3M terms in
-// FP64, and write the complex result (overwritten, added, or as a per-chunk
-// partial that a reduction kernel sums in a fixed order).
+// (3 products x 5 levels x 32 columns) in tensor memory, one MMA per A digit
+// plane covering all its levels; warps 0-7 (two per tensor-memory lane
+// quadrant, 16 columns each) read the accumulators back (tcgen05.ld),
+// combine levels, scales and the 3M terms in double-float, and write the
+// complex result (overwritten, added, or as a per-chunk partial that a
+// reduction kernel sums in a fixed order).
 //
 // Every wait is bounded (2 s of wall time): on expiry the kernel records
 // the error in the grid-barrier record the host checks (HOPF_ETIMEOUT),
@@ -52,7 +54,7 @@ constexpr int kSlab = 64;        // K-values per digit slab (128 bytes of BF16)
 constexpr int kMaxDigits = 5;    // 3 products x 5 levels x 32 columns = 480 TMEM columns
 constexpr int kTmemCols = 512;
 constexpr int kStages = 2;
-constexpr int kTcThreads = 192;  // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr int kTcThreads = 320;  // warps 0-7 epilogue, 8 producer, 9 MMA
 constexpr uint64_t kWaitNs = kTcWaitNs;
 static_assert(kTmaSlab == 64, "digit slabs are one 128-byte TMA box row");
 
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = tmem_slot;
   volatile int* vabort = &abort_flag;
 
-  if (warp == 4) {
+  if (warp == 8) {
     // ---- producer: one (slab, product) stage at a time ------------------
     if (lane == 0) {
       int issued = 0;
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (global_ns() - t0 > kWaitNs) break;
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ---- MMA issuer -------------------------------------------------------
     if (lane == 0) {
       for (int st = 0; st < nstage; ++st) {
@@ -171,23 +173,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       umma_commit(&acc_bar);  // all accumulators final (also after an abort)
     }
   } else {
-    // ---- epilogue: warps 0-3, thread = output row ------------------------
+    // ---- epilogue: warps 0-7, thread = output row of its lane quadrant ----
     // Every level accumulator is an exact FP32 integer; the levels, the
     // per-component scales and the 3M combination are summed in
     // double-float arithmetic on the FP32 pipe (error-free TwoSum steps),
     // and only the final value is converted to FP64 and scaled (on this GPU
     // the FP64 pipe is 1/64 of the FP32 one).
-    const int m = m0 + 32 * warp + lane;
+    // warp w reads tensor-memory lanes 32 (w % 4) .. +31 (its quadrant) and
+    // columns 16 (w / 4) .. +15: two warps per quadrant share the rows
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = m0 + 32 * quad + lane;
     cplx* out = a.out + (size_t)z * a.zstride;
     // the tile's column exponents of B, staged while the MMAs run (named
-    // barrier 1: the four epilogue warps only)
+    // barrier 1: the eight epilogue warps only)
     {
       const int t = threadIdx.x;
       if (t < 3 * kTcN) {
         const int c = t / kTcN, n = n0 + t % kTcN;
         eb_sh[c][t % kTcN] = (n < a.N) ? a.eB[(size_t)c * a.nchunks * a.N + (size_t)z * a.N + n] : 0;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, 256;" ::: "memory");
     }
     // the values an accumulating product adds to, 8 columns at a time,
     // loaded ahead (independent loads in flight together): the first
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         pre[q] = (a.accumulate && m < a.M && n < a.N) ? out[m + (size_t)a.ldo * n] : mk(0, 0);
       }
     };
-    prefetch(0);
+    prefetch(2 * half);
     const bool ok = mbar_wait(&acc_bar, 0, vabort, a.err);
     tc_fence_after();
     if (ok && !*vabort) {
@@ -209,10 +214,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       int ea[3] = {0, 0, 0};
       if (m < a.M)
         for (int c = 0; c < 3; ++c) ea[c] = a.eA[c * eAs + (size_t)z * a.M + m];
-      const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
 #pragma unroll 1
-      for (int h = 0; h < kTcN / 8; ++h) {
-        if (h > 0) prefetch(h);
+      for (int h = 2 * half; h < 2 * half + 2; ++h) {
+        if (h > 2 * half) prefetch(h);
         float th[3][8], tl[3][8];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
