@@ -53,3 +53,27 @@ def test_reference_arm_runs_on_rank_zero_only():
     import bench
     args = types.SimpleNamespace(steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args, 1) is None
+
+
+def test_reference_line_reports_the_sample_and_the_extrapolated_rate(monkeypatch):
+    """ms_per_step is the wall time of one bench step (the measured oracle
+    sample), value the full-workload rate extrapolated from it by bonds."""
+    sys.path.insert(0, ROOT)
+    import bench
+    calls = []
+
+    def fake_sample(d_sample: int = 4):
+        calls.append(d_sample)
+        return 2.0, 2.0 * (32 - 1) / (d_sample - 1)
+
+    monkeypatch.setattr(bench, "oracle_sample_seconds", fake_sample)
+    args = types.SimpleNamespace(steps=2, warmup=3, gpus=1)
+    line = bench.run_reference(args, 0)
+    assert len(calls) == 5  # three untimed warm-up samples, two timed
+    assert line["impl"] == "reference"
+    assert line["ms_per_step"] == pytest.approx(2000.0)
+    assert line["extrapolated_ms_per_step"] == pytest.approx(2000.0 * 31 / 3)
+    assert line["value"] == pytest.approx(1.0 / (2.0 * 31 / 3))
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert "d=4" in line["cpu_baseline"]["sample"] and line["cpu_baseline"]["kind"] == "oracle"
