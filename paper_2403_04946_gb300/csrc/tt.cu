@@ -51,32 +51,38 @@ static inline int nblk(size_t n, int t) { return (int)((n + t - 1) / t); }
 // every W block one of the per-mode operators (op_apply): tridiagonal in
 // (m, m'), or the CDF equation's cumulative K.  One thread per
 // output element, consecutive threads along the fastest (left-rank) index, so
-// loads of X and stores of Y are both coalesced 16-byte accesses.
+// loads of X and stores of Y are both coalesced 16-byte accesses.  The grid's
+// y index walks the right-rank index q = (beta, j) and x the (alpha, i, m)
+// plane, so that every index comes from 32-bit arithmetic (the plane is
+// below 2^31 elements, checked by the launcher).
 __global__ void apply_core_kernel(const cplx* __restrict__ X, int a, int n, int c,
                                   cplx* __restrict__ Y, int Al, int Ar,
                                   const unsigned char* __restrict__ blocks,
                                   const cplx* __restrict__ coef) {
-  const size_t rows = (size_t)Al * a;
-  const size_t total = rows * n * (size_t)(Ar * c);
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = e % rows;
-    const size_t rest = e / rows;
-    const int m = (int)(rest % n);
-    const size_t q = rest / n;
-    const int al = (int)(p / a), i = (int)(p % a);
-    const int be = (int)(q / c), j = (int)(q % c);
-    const int op = blocks[al * Ar + be];
-    cplx v = mk(0, 0);
-    if (op != OP_NONE) v = op_apply(coef, op, n, X + i + (size_t)a * n * j, (size_t)a, m);  // X[i, :, j], stride a
-    Y[e] = v;
+  const int rows = Al * a;
+  const int plane = rows * n;
+  for (int q = blockIdx.y; q < Ar * c; q += gridDim.y) {
+    const int be = q / c, j = q - be * c;
+    const cplx* Xj = X + (size_t)a * n * j;
+    cplx* Yq = Y + (size_t)plane * q;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < plane; idx += gridDim.x * blockDim.x) {
+      const int m = idx / rows, p = idx - m * rows;
+      const int al = p / a, i = p - al * a;
+      const int op = blocks[al * Ar + be];
+      cplx v = mk(0, 0);
+      if (op != OP_NONE) v = op_apply(coef, op, n, Xj + i, (size_t)a, m);  // X[i, :, j], stride a
+      Yq[idx] = v;
+    }
   }
 }
 
 cudaError_t apply_core(const cplx* in, int a, int n, int c, cplx* out, int Al, int Ar,
                        const unsigned char* blocks_dev, const OpTable& ops, cudaStream_t s) {
-  const size_t total = (size_t)Al * a * n * Ar * c;
-  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
+  const size_t plane = (size_t)Al * a * n;
+  const size_t nq = (size_t)Ar * c;
+  if (plane == 0 || nq == 0) return cudaSuccess;
+  if (plane >= (1u << 31) || nq >= (1u << 31)) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)std::min<size_t>(nblk(plane, 256), 1024), (unsigned)std::min<size_t>(nq, 65535));
   apply_core_kernel<<<grid, 256, 0, s>>>(in, a, n, c, out, Al, Ar, blocks_dev, ops.coef);
   return cudaGetLastError();
 }
@@ -653,24 +659,24 @@ __global__ void stencil_combine_kernel(const cplx* __restrict__ T, int r, int n,
                                        int Al, int Ar, const unsigned char* __restrict__ blocks,
                                        const cplx* __restrict__ coef, cplx* __restrict__ out,
                                        int mode, int ldo) {
-  const size_t rows = (size_t)Al * r;
-  const size_t total = rows * n * (size_t)p;
+  // grid y walks q, x the (alpha, i, m) plane: 32-bit index arithmetic
+  const int rows = Al * r;
+  const int plane = rows * n;
   const size_t blk = (size_t)r * n * p;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t pr = e % rows;
-    const size_t rest = e / rows;
-    const int m = (int)(rest % n);
-    const int q = (int)(rest / n);
-    const int al = (int)(pr / r), i = (int)(pr % r);
-    cplx v = mk(0, 0);
-    for (int be = 0; be < Bn; ++be) {
-      const int op = blocks[al * Ar + be];
-      if (op == OP_NONE) continue;
-      v = cadd(v, op_apply(coef, op, n, T + blk * be + i + (size_t)r * n * q, (size_t)r, m));  // T_beta[i, :, q]
+  for (int q = blockIdx.y; q < p; q += gridDim.y) {
+    const cplx* Tq = T + (size_t)r * n * q;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < plane; idx += gridDim.x * blockDim.x) {
+      const int m = idx / rows, pr = idx - m * rows;
+      const int al = pr / r, i = pr - al * r;
+      cplx v = mk(0, 0);
+      for (int be = 0; be < Bn; ++be) {
+        const int op = blocks[al * Ar + be];
+        if (op == OP_NONE) continue;
+        v = cadd(v, op_apply(coef, op, n, Tq + blk * be + i, (size_t)r, m));  // T_beta[i, :, q]
+      }
+      if (mode == 0) out[(size_t)idx + (size_t)plane * q] = v;
+      else out[(size_t)(m + (size_t)n * q) + (size_t)ldo * pr] = cconj(v);
     }
-    if (mode == 0) out[e] = v;
-    else out[(size_t)(m + (size_t)n * q) + (size_t)ldo * pr] = cconj(v);
   }
 }
 
@@ -787,7 +793,9 @@ cudaError_t stencil_combine(const cplx* T, int r, int n, int p, int Bn, int Al, 
                                                                    ops.forms, out, ldo);
     return cudaGetLastError();
   }
-  const int grid = std::min<size_t>(nblk(total, 256), (size_t)dev_info().sm_count * 16);
+  const size_t plane = (size_t)Al * r * n;
+  if (plane >= (1u << 31)) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)std::min<size_t>(nblk(plane, 256), 1024), (unsigned)std::min(p, 65535));
   stencil_combine_kernel<<<grid, 256, 0, s>>>(T, r, n, p, Bn, Al, Ar, blocks_dev, ops.coef, out,
                                               mode, ldo);
   return cudaGetLastError();
